@@ -1,0 +1,198 @@
+/*
+ * fm.h -- C ABI of the GB300 (sm_103a) implicit time step for the hydrodynamic
+ * freezing models of Baskaran, Guan and Lowengrub, "Energy Stable Multigrid
+ * Method for Local and Non-local Hydrodynamic Models for Freezing".
+ *
+ * One call of fm_step advances (rho^k, u^k) by one step of the fully discrete
+ * convex-splitting scheme, Sec. 5, Eqs. (discrete_a)-(discrete_d):
+ *
+ *   rho^{k+1} - rho^k = -s div_h(rho^k u^{k+1/2}),
+ *   rho^k (u^{k+1} - u^k) = s [ -rho^k omega^k x u^{k+1/2}
+ *        - (rho^k/2) grad_h |u^{k+1}|^2 - rho^k grad_h mu^{k+1}
+ *        + gamma Lap_h u^{k+1/2} ],
+ *   mu^{k+1} = dF_c[rho^{k+1}] - dF_e[rho^k],   omega^k = curl_h u^k,
+ *
+ * with the PFC functional (Sec. 5.3, Lemma 5.4) or the non-local CDFT
+ * functional (Sec. 5.2, Lemma 5.2, kernel J of Sec. 6, convolution of
+ * Eq. (discrete_convolution) evaluated by a hand-written FFT).  The implicit
+ * system N(g) = S of App. G is solved by FAS multigrid (Sec. 6) with a
+ * red-black point-block Gauss-Seidel smoother (App. G.1, G.2), damping
+ * (App. G.3) and the positive projection of Sec. 6.
+ *
+ * Conventions shared by every entry point:
+ *  - Return 0 (FM_OK) on success or a negative FM_E* code; nothing throws.
+ *  - Grids are periodic with cubic cells of side h.  Fields are stored
+ *    row-major with x fastest: index (k*ny + j)*nx + i.  Velocities are passed
+ *    as `dim` separate arrays (structure of arrays), all float64.
+ *  - `where` says whether caller pointers are host (FM_HOST) or device
+ *    (FM_DEVICE) memory; device pointers must be on the current CUDA device.
+ *  - The caller owns the handle and its own arrays; the library allocates
+ *    (cudaMalloc at fm_create) and owns every device buffer of the solver and
+ *    frees them in fm_destroy.
+ *  - All work is issued on the stream given to fm_set_stream (default: the
+ *    legacy default stream).  Calls that return values to the host (fm_step's
+ *    convergence test, fm_energy, fm_mass) synchronise that stream.
+ *  - On a nonzero return from fm_step the state is left at time level k,
+ *    unchanged.
+ */
+#ifndef FM_H
+#define FM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FM_OK        0
+#define FM_EINVAL   (-1)  /* invalid argument (sizes, parameters, null pointers) */
+#define FM_ENOMEM   (-2)  /* device allocation failed */
+#define FM_ECUDA    (-3)  /* a CUDA runtime call failed */
+#define FM_ENOCONV  (-4)  /* residual above tol after max_cycles V-cycles */
+#define FM_ENONPOS  (-5)  /* non-positive density reached ln (CDFT, delta = 0) */
+#define FM_ENAN     (-6)  /* non-finite residual */
+
+#define FM_PFC   1        /* local phase-field-crystal functional, Sec. 2.2 / 5.3 */
+#define FM_CDFT  2        /* non-local CDFT functional, Sec. 2.1 / 5.2 */
+
+#define FM_FP64  0        /* every sweep in float64 */
+#define FM_MIXED 1        /* float32 smoothing and transfers inside a float64
+                             outer residual / defect-correction loop */
+
+#define FM_HOST   0
+#define FM_DEVICE 1
+
+/* Periodic grid: dim = 2 or 3; n[d] points along x, y, z (n[2] ignored in
+ * 2-D); spacing h.  Every n[d] must be even (red-black ordering). */
+typedef struct {
+    int dim;
+    int n[3];
+    double h;
+} fm_grid;
+
+/* kind = FM_PFC: alpha = 1 - eps (App. B).  kind = FM_CDFT: nu is the spatial
+ * scale of the kernel J(x) = sqrt(2) exp(-pi^2 |x|^2/(2 nu^2))
+ * - exp(-pi^2 |x|^2/(4 nu^2)) (Sec. 6). */
+typedef struct {
+    int kind;
+    double alpha;
+    double nu;
+} fm_functional;
+
+/* Solver parameters (fm_default_params fills the defaults in brackets). */
+typedef struct {
+    double gamma;   /* viscosity [2], Sec. 6 */
+    double w_damp;  /* damping weight of the point block [0.5], App. G.3 */
+    double delta;   /* projection rho <- sqrt(rho^2 + delta^2) [0], Sec. 6 */
+    double tol;     /* stop when max_c sqrt(h^d sum r_c^2) <= tol [1e-10] */
+    double sigma;   /* sign of the vorticity term [+1 = vector form of Eq.
+                       (discrete_b)]; -1 reproduces the App. G printing */
+    int nu1, nu2;   /* pre- and post-smoothing iterations [2, 2] */
+    int max_cycles; /* [50] */
+    int coarsest;   /* coarsen while every n[d]/2 >= coarsest and is even [4] */
+    int ncoarse;    /* smoothing iterations on the coarsest grid [16] */
+    int precision;  /* FM_FP64 or FM_MIXED [FM_FP64] */
+} fm_params;
+
+typedef struct {
+    int cycles;     /* V-cycles taken */
+    double res0;    /* residual norm of the initial iterate */
+    double res;     /* final residual norm (float64) */
+} fm_step_info;
+
+typedef struct fm_state fm_state;
+
+/* Fill *p with the defaults listed in fm_params. */
+void fm_default_params(fm_params* p);
+
+/* Create a solver for one grid.  Validates the sizes and parameters
+ * (FM_EINVAL), builds the multigrid hierarchy, and for CDFT samples J,
+ * computes c_e = (J_e * 1) = h^d sum J_e (Lemma 5.2) and the transform of J
+ * on the device.  The state starts at rho = 0, u = 0: call fm_set_fields. */
+int fm_create(const fm_grid* grid, const fm_params* prm,
+              const fm_functional* fn, fm_state** out);
+
+/* Free every device buffer and the handle (null is accepted). */
+void fm_destroy(fm_state* st);
+
+/* Issue all further work on `stream` (a cudaStream_t). */
+int fm_set_stream(fm_state* st, void* stream);
+
+/* Copy rho and the dim velocity components (vel[0..dim-1]) into the state.
+ * Each array holds nx*ny*nz float64 values. */
+int fm_set_fields(fm_state* st, const double* rho, const double* const* vel, int where);
+
+/* Copy the current rho and velocity out of the state. */
+int fm_get_fields(fm_state* st, double* rho, double* const* vel, int where);
+
+/* Advance one time step of size dt (the paper's s) with FAS V(nu1, nu2)
+ * cycles until the float64 residual norm is <= tol, then re-evaluate
+ * rho^{k+1} from the continuity equation with the final velocity (mass exact
+ * to round-off) and project.  info may be null.  FM_ENOCONV / FM_ENAN leave
+ * the state unchanged. */
+int fm_step(fm_state* st, double dt, fm_step_info* info);
+
+/* Total energy E = 1/2 (rho u || u) + F[rho] (Thm 5.1) of the current state,
+ * with F the discrete PFC energy (Eq. CS_PFC_discrete) or the CDFT energy
+ * (Eq. CS_DFT_discrete); F and KE separately.  Float64 deterministic
+ * reductions.  Any output pointer may be null. */
+int fm_energy(fm_state* st, double* E, double* F, double* KE);
+
+/* Mass (rho || 1) = h^d sum rho (Thm 5.1). */
+int fm_mass(fm_state* st, double* M);
+
+/* Human-readable message for a return code. */
+const char* fm_strerror(int code);
+
+/* ---- Row-level entry points (each is one step of fm_step, exposed so that
+ * every part of the hot path can be checked on its own). ---- */
+
+/* What fm_get_aux reads (all float64, nx*ny*nz values per component). */
+#define FM_AUX_OMEGA   1  /* omega^k components (1 in 2-D, 3 in 3-D), Eq. (discrete_d) */
+#define FM_AUX_SOURCE  2  /* S components of App. G (1+dim, +2 for PFC) */
+#define FM_AUX_CONV    3  /* J * rho^k (CDFT), Eq. (discrete_convolution) */
+#define FM_AUX_ITERATE 4  /* the current iterate g (rho, u.., mu, kappa) */
+
+/* Compute omega^k, J*rho^k (CDFT), the source S and the initial iterate g^0
+ * for a step of size dt from the current fields (the first stage of
+ * fm_step). */
+int fm_prepare(fm_state* st, double dt);
+
+/* Read component `comp` of an auxiliary field after fm_prepare or fm_step. */
+int fm_get_aux(fm_state* st, int what, int comp, double* out, int where);
+
+/* Float64 residual r = S - N(g) of App. G for a caller-supplied iterate g
+ * (g[0..nu-1] with nu = 1 + dim (+2 for PFC)) against the source of the last
+ * fm_prepare; writes r (r may be null) and its norm max_c sqrt(h^d sum r_c^2). */
+int fm_residual(fm_state* st, const double* const* g, double* const* r,
+                double* norm, int where);
+
+/* Periodic convolution out = J * rho (Eq. (discrete_convolution)) with the
+ * state's kernel J (CDFT states only), by FFT. */
+int fm_convolve(fm_state* st, const double* rho, double* out, int where);
+
+/* Nodal full-weighting restriction of one float64 field from the state's
+ * finest grid to the next coarser grid (coarse sizes n[d]/2). */
+int fm_restrict(fm_state* st, const double* fine, double* coarse, int where);
+
+/* fine += bilinear (trilinear) prolongation of one float64 coarse field. */
+int fm_prolong_add(fm_state* st, const double* coarse, double* fine, int where);
+
+/* Number of multigrid levels of the state. */
+int fm_levels(const fm_state* st);
+
+/* ---- Measurement (no counterpart in the paper). ---- */
+
+/* Enable (1) or disable (0) CUDA-event timing of every finest-level smoother
+ * launch issued by fm_step, and reset the accumulated totals. */
+int fm_profile(fm_state* st, int enable);
+
+/* Accumulated finest-level smoother time (ms) and launch count since the last
+ * fm_profile call, and the total number of kernels this state has launched
+ * since fm_create.  Any output pointer may be null. */
+int fm_profile_read(const fm_state* st, double* smoother_ms, long long* smoother_launches,
+                    long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FM_H */

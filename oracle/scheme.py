@@ -484,7 +484,9 @@ class SolverOpts:
 
 
 def can_coarsen(shape, opts):
-    return all(n % 2 == 0 and n // 2 >= opts.coarsest for n in shape)
+    """Coarsen while every size halves to an even size >= ``coarsest``
+    (red-black ordering needs even periodic sizes on every level)."""
+    return all(n % 2 == 0 and n // 2 >= opts.coarsest and (n // 2) % 2 == 0 for n in shape)
 
 
 def vcycle(g, f, c, P, opts):

@@ -1,0 +1,75 @@
+// Host-side state of one solver instance (shared by the libfm translation
+// units).  All device buffers live in one arena allocated at fm_create.
+#pragma once
+
+#include <cuda_runtime.h>
+#include "../../include/fm.h"
+#include "fm_internal.cuh"
+
+namespace fm {
+
+constexpr int MAXLEV = 16;
+constexpr int MAXEV = 64;     // profiling events (pairs) per outer iteration
+
+struct LevelBufs {
+  Geo g;
+  double h;
+  void* e[MAXU];
+  void* f[MAXU];
+  void* r[MAXU];
+  void* eh[MAXU];
+  void* rk;        // precision-T rho^k (level 0 of the FP64 path: aliases st.rho)
+  void* om[3];
+  void* cr;        // precision-T coefficient iterate (level 0 FP64: aliases st.g)
+  void* cv[3];
+};
+
+struct FFTBufs {
+  double2* Jhat;       // transform of h^d J / N (scaled so that the inverse needs no scale)
+  double2* work;       // complex work array, N values
+  double2* tw[3];      // twiddles exp(-2 pi i k / n_d), k < n_d / 2
+};
+
+}  // namespace fm
+
+struct fm_state {
+  fm_grid grid;
+  fm_params prm;
+  fm_functional fn;
+  int kind, dim, nu, nom, nlev;
+  int elem;                       // sizeof(T) of the hierarchy
+  fm::LevelBufs lv[fm::MAXLEV];
+  // float64 finest-level fields
+  double* rho;
+  double* vel[3];
+  double* g[fm::MAXU];
+  double* S[fm::MAXU];
+  double* om[3];
+  double* conv;                   // J * rho^k (CDFT)
+  double* tmp;                    // float64 scratch of N values
+  double* r64[fm::MAXU];          // float64 residual scratch (row-level entry points)
+  double* partials;               // per-block partial sums (deterministic reductions)
+  int nblk;                       // blocks of the reduction kernels
+  double* dscal;                  // device scalars
+  double* hscal;                  // pinned host mirror of dscal
+  double ce;                      // (J_e * 1) (CDFT)
+  fm::FFTBufs fft;
+  double dt;                      // step of the last fm_prepare
+  bool prepared;
+  cudaStream_t stream;
+  long long launches;             // kernels launched by this state
+  bool prof;                      // time the finest-level smoother launches
+  bool pev_ready;
+  cudaEvent_t pev[fm::MAXEV];
+  int npev;
+  double prof_ms;
+  long long prof_count;
+  void* arena;
+  size_t arena_bytes;
+};
+
+namespace fm {
+// fm_fft.cu
+int fft_init(fm_state* st);                                    // twiddles, J, c_e, Jhat
+int fft_convolve(fm_state* st, const double* rho, double* out);  // out = J * rho
+}  // namespace fm

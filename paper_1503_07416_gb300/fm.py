@@ -1,0 +1,306 @@
+"""ctypes binding of libfm (include/fm.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Arrays may be
+numpy float64 arrays (host memory) or torch float64 CUDA tensors (device
+memory); every step of the computation runs in the CUDA library.  Loading
+fails loudly when libfm.so is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_PKG, "libfm.so")
+
+FM_OK = 0
+FM_EINVAL = -1
+FM_ENOMEM = -2
+FM_ECUDA = -3
+FM_ENOCONV = -4
+FM_ENONPOS = -5
+FM_ENAN = -6
+FM_PFC = 1
+FM_CDFT = 2
+FM_FP64 = 0
+FM_MIXED = 1
+FM_HOST = 0
+FM_DEVICE = 1
+FM_AUX_OMEGA = 1
+FM_AUX_SOURCE = 2
+FM_AUX_CONV = 3
+FM_AUX_ITERATE = 4
+
+
+class fm_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("h", C.c_double)]
+
+
+class fm_functional(C.Structure):
+    _fields_ = [("kind", C.c_int), ("alpha", C.c_double), ("nu", C.c_double)]
+
+
+class fm_params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("w_damp", C.c_double), ("delta", C.c_double),
+                ("tol", C.c_double), ("sigma", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
+                ("max_cycles", C.c_int), ("coarsest", C.c_int), ("ncoarse", C.c_int),
+                ("precision", C.c_int)]
+
+
+class fm_step_info(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("res0", C.c_double), ("res", C.c_double)]
+
+
+class FMError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+_SIGS = {
+    "fm_default_params": (None, [C.POINTER(fm_params)]),
+    "fm_create": (C.c_int, [C.POINTER(fm_grid), C.POINTER(fm_params), C.POINTER(fm_functional),
+                            C.POINTER(C.c_void_p)]),
+    "fm_destroy": (None, [C.c_void_p]),
+    "fm_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fm_set_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
+    "fm_get_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
+    "fm_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(fm_step_info)]),
+    "fm_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                            C.POINTER(C.c_double)]),
+    "fm_mass": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "fm_strerror": (C.c_char_p, [C.c_int]),
+    "fm_prepare": (C.c_int, [C.c_void_p, C.c_double]),
+    "fm_get_aux": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]),
+    "fm_residual": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                              C.POINTER(C.c_double), C.c_int]),
+    "fm_convolve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "fm_restrict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "fm_prolong_add": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "fm_levels": (C.c_int, [C.c_void_p]),
+    "fm_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "fm_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                  C.POINTER(C.c_longlong)]),
+}
+
+
+def lib():
+    """Load libfm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError(f"libfm.so not found at {LIBPATH}: build it with "
+                               "python -m paper_1503_07416_gb300.build")
+        L = C.CDLL(LIBPATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def fm_strerror(code):
+    return lib().fm_strerror(code).decode()
+
+
+strerror = fm_strerror
+
+
+def _check(code, what):
+    if code != FM_OK:
+        raise FMError(code, what)
+
+
+def _ptr(a):
+    """(address, where) of a float64 numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous float64")
+        return a.ctypes.data, FM_HOST
+    import torch  # noqa: F401  (device arrays are torch tensors)
+    if a.dtype != torch.float64 or not a.is_contiguous():
+        raise ValueError("device tensors must be contiguous float64")
+    return a.data_ptr(), (FM_DEVICE if a.is_cuda else FM_HOST)
+
+
+def _where(arrs):
+    ws = {_ptr(a)[1] for a in arrs if a is not None}
+    if len(ws) != 1:
+        raise ValueError("mix of host and device arrays")
+    return ws.pop()
+
+
+def _vec(arrs):
+    return (C.c_void_p * len(arrs))(*[(_ptr(a)[0] if a is not None else None) for a in arrs])
+
+
+def fm_default_params():
+    p = fm_params()
+    lib().fm_default_params(C.byref(p))
+    return p
+
+
+def fm_create(grid: fm_grid, prm: fm_params, fn: fm_functional):
+    h = C.c_void_p()
+    _check(lib().fm_create(C.byref(grid), C.byref(prm), C.byref(fn), C.byref(h)), "fm_create")
+    return h
+
+
+def fm_destroy(st):
+    lib().fm_destroy(st)
+
+
+def fm_set_stream(st, stream_handle: int):
+    _check(lib().fm_set_stream(st, C.c_void_p(stream_handle)), "fm_set_stream")
+
+
+def fm_set_fields(st, rho, vel):
+    w = _where([rho, *vel])
+    _check(lib().fm_set_fields(st, C.c_void_p(_ptr(rho)[0]), _vec(vel), w), "fm_set_fields")
+
+
+def fm_get_fields(st, rho, vel):
+    w = _where([rho, *vel])
+    _check(lib().fm_get_fields(st, C.c_void_p(_ptr(rho)[0]), _vec(vel), w), "fm_get_fields")
+
+
+def fm_step(st, dt):
+    info = fm_step_info()
+    _check(lib().fm_step(st, C.c_double(dt), C.byref(info)), "fm_step")
+    return info
+
+
+def fm_step_raw(st, dt):
+    """fm_step returning (code, info) without raising."""
+    info = fm_step_info()
+    code = lib().fm_step(st, C.c_double(dt), C.byref(info))
+    return code, info
+
+
+def fm_energy(st):
+    E, F, K = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().fm_energy(st, C.byref(E), C.byref(F), C.byref(K)), "fm_energy")
+    return E.value, F.value, K.value
+
+
+def fm_mass(st):
+    M = C.c_double()
+    _check(lib().fm_mass(st, C.byref(M)), "fm_mass")
+    return M.value
+
+
+def fm_prepare(st, dt):
+    _check(lib().fm_prepare(st, C.c_double(dt)), "fm_prepare")
+
+
+def fm_get_aux(st, what, comp, out):
+    p, w = _ptr(out)
+    _check(lib().fm_get_aux(st, what, comp, C.c_void_p(p), w), "fm_get_aux")
+
+
+def fm_residual(st, g, r=None):
+    w = _where(list(g) + (list(r) if r is not None else []))
+    nrm = C.c_double()
+    rv = _vec(r) if r is not None else None
+    _check(lib().fm_residual(st, _vec(g), rv, C.byref(nrm), w), "fm_residual")
+    return nrm.value
+
+
+def fm_convolve(st, rho, out):
+    w = _where([rho, out])
+    _check(lib().fm_convolve(st, C.c_void_p(_ptr(rho)[0]), C.c_void_p(_ptr(out)[0]), w), "fm_convolve")
+
+
+def fm_restrict(st, fine, coarse):
+    w = _where([fine, coarse])
+    _check(lib().fm_restrict(st, C.c_void_p(_ptr(fine)[0]), C.c_void_p(_ptr(coarse)[0]), w), "fm_restrict")
+
+
+def fm_prolong_add(st, coarse, fine):
+    w = _where([fine, coarse])
+    _check(lib().fm_prolong_add(st, C.c_void_p(_ptr(coarse)[0]), C.c_void_p(_ptr(fine)[0]), w),
+           "fm_prolong_add")
+
+
+def fm_levels(st):
+    return lib().fm_levels(st)
+
+
+def fm_profile(st, enable):
+    _check(lib().fm_profile(st, 1 if enable else 0), "fm_profile")
+
+
+def fm_profile_read(st):
+    """(smoother_ms, smoother_launches, total_launches)."""
+    ms, n, tot = C.c_double(), C.c_longlong(), C.c_longlong()
+    _check(lib().fm_profile_read(st, C.byref(ms), C.byref(n), C.byref(tot)), "fm_profile_read")
+    return ms.value, n.value, tot.value
+
+
+# ---------------------------------------------------------------------------
+# A small object wrapper over the same calls.
+# ---------------------------------------------------------------------------
+class Solver:
+    """One periodic grid and its FAS solver (owns an fm_state handle)."""
+
+    def __init__(self, kind, n, h, dim=2, alpha=0.0, nu=0.0, precision=FM_FP64, stream=None, **params):
+        g = fm_grid()
+        g.dim = dim
+        ns = list(n) if hasattr(n, "__len__") else [n] * dim
+        for d in range(3):
+            g.n[d] = ns[d] if d < dim else 1
+        g.h = h
+        f = fm_functional()
+        f.kind = {"pfc": FM_PFC, "cdft": FM_CDFT}.get(kind, kind)
+        f.alpha = alpha
+        f.nu = nu
+        p = fm_default_params()
+        p.precision = precision
+        for k, v in params.items():
+            setattr(p, k, v)
+        self.dim = dim
+        self.shape = tuple(reversed(ns[:dim]))
+        self.nu = 1 + dim + (2 if f.kind == FM_PFC else 0)
+        self.handle = fm_create(g, p, f)
+        if stream is not None:
+            fm_set_stream(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            fm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_fields(self, rho, vel):
+        fm_set_fields(self.handle, rho, vel)
+
+    def get_fields(self, rho=None, vel=None):
+        if rho is None:
+            rho = np.empty(self.shape)
+            vel = [np.empty(self.shape) for _ in range(self.dim)]
+        fm_get_fields(self.handle, rho, vel)
+        return rho, vel
+
+    def step(self, dt):
+        return fm_step(self.handle, dt)
+
+    def energy(self):
+        return fm_energy(self.handle)
+
+    def mass(self):
+        return fm_mass(self.handle)
+
+    def aux(self, what, comp):
+        out = np.empty(self.shape)
+        fm_get_aux(self.handle, what, comp, out)
+        return out

@@ -1,0 +1,279 @@
+"""CUDA path (through the C ABI) against the FP64 CPU oracle, element by
+element on the same seeded inputs.
+
+Tolerances (relative 2-norm per field, ||x_gpu - x_oracle|| / ||x_oracle||):
+float64 path 1e-10 per step, mixed path (float32 smoothing inside the float64
+outer residual loop) 1e-8, with both solvers converged to the same float64
+residual tolerance (1e-12 unless stated).  Both solve the same discrete
+system; the two solvers' iterates differ, the fixed point does not.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import scheme as S
+from paper_1503_07416_gb300 import fm, inputs
+from tests.helpers import gpu_solver, oracle_setup, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOLMIX = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_07416_gb300 import build
+    build.build_library()
+    fm.lib()
+
+
+def _compare_step(rho, vel, prm, precision, tol=1e-12, w_damp=None, steps=1, bound=None, **kw):
+    P, opts, J = oracle_setup(rho, prm, w_damp=w_damp, tol=tol)
+    sol = gpu_solver(rho, prm, precision=precision, w_damp=w_damp, tol=tol, **kw)
+    bound = bound or (TOL64 if precision == fm.FM_FP64 else TOLMIX)
+    worst = 0.0
+    for _ in range(steps):
+        sol.set_fields(rho, vel)
+        info = sol.step(prm["dt"])
+        rg, vg = sol.get_fields()
+        ro, vo, oinfo = S.step(rho, vel, P, opts, J=J)
+        assert info.res <= tol
+        errs = [rel(rg, ro)] + [rel(a, b) for a, b in zip(vg, vo)]
+        worst = max(worst, max(errs))
+        assert max(errs) <= bound, (errs, info.cycles, oinfo["cycles"])
+        rho, vel = ro, vo
+    sol.close()
+    return worst
+
+
+# --------------------------------------------------------------- full steps
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_pfc64_steps(precision):
+    """2-D PFC 64x64 (L = 32, eps = 0.025, s = 0.01), 3 steps, per-step parity."""
+    rho, vel, prm = inputs.pfc64()
+    _compare_step(rho, vel, prm, precision, steps=3)
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_pfc_supercooled_with_velocity(precision):
+    """PFC eps = 0.4 supercooled liquid with nuclei, non-zero velocity and
+    vorticity, 128x128, undamped smoother."""
+    rho, vel, prm = inputs.pfc_supercooled(128, seed=21)
+    rng = np.random.default_rng(5)
+    vel = [0.05 * rng.standard_normal(rho.shape) for _ in range(2)]
+    _compare_step(rho, vel, prm, precision, w_damp=0.0, steps=2)
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_cdft_steps(precision):
+    """2-D CDFT, the 256^2 physics (h = 17/128, nu = 2.362) on a 64x64 box,
+    2 steps; the convolution runs through the hand-written FFT."""
+    rho, vel, prm = inputs.cdft256(n=64)
+    prm = dict(prm, h=17.0 / 128)
+    rng = np.random.default_rng(8)
+    vel = [0.02 * rng.standard_normal(rho.shape) for _ in range(2)]
+    _compare_step(rho, vel, prm, precision, steps=2)
+
+
+def test_ragged_nonsquare_grid():
+    """48 x 40 grid (levels 48x40 -> 24x20 -> 12x10; coarsest stops at an odd
+    half) with the PFC functional."""
+    rng = np.random.default_rng(3)
+    rho = 0.8 + 0.05 * rng.uniform(-1, 1, (40, 48))
+    vel = [0.03 * rng.standard_normal((40, 48)) for _ in range(2)]
+    prm = dict(kind="pfc", dim=2, h=0.9, dt=0.02, alpha=0.6, delta=0.0, tol=1e-12)
+    _compare_step(rho, vel, prm, fm.FM_FP64, w_damp=0.0, steps=2)
+    _compare_step(rho, vel, prm, fm.FM_MIXED, w_damp=0.0, steps=1)
+
+
+def test_smallest_grid():
+    """4 x 4 grid: a single level, solved by the coarsest-grid kernel alone."""
+    rng = np.random.default_rng(4)
+    rho = 0.8 + 0.05 * rng.uniform(-1, 1, (4, 4))
+    vel = [0.03 * rng.standard_normal((4, 4)) for _ in range(2)]
+    prm = dict(kind="pfc", dim=2, h=0.9, dt=0.02, alpha=0.6, tol=1e-12)
+    _compare_step(rho, vel, prm, fm.FM_FP64, w_damp=0.0, ncoarse=40)
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_3d_pfc(precision):
+    """3-D PFC 16^3 with random velocity (three vorticity components)."""
+    rng = np.random.default_rng(6)
+    n = 16
+    rho = 0.8 + 0.05 * rng.uniform(-1, 1, (n, n, n))
+    vel = [0.03 * rng.standard_normal((n, n, n)) for _ in range(3)]
+    prm = dict(kind="pfc", dim=3, h=0.9, dt=0.02, alpha=0.6, tol=1e-12)
+    _compare_step(rho, vel, prm, precision, w_damp=0.0, steps=2)
+
+
+def test_uniform_state_is_a_fixed_point():
+    n = 32
+    rho = np.full((n, n), 0.8)
+    vel = [np.zeros((n, n)), np.zeros((n, n))]
+    prm = dict(kind="pfc", dim=2, h=0.9, dt=0.02, alpha=0.6, tol=1e-12)
+    sol = gpu_solver(rho, prm)
+    sol.set_fields(rho, vel)
+    info = sol.step(0.02)
+    rg, vg = sol.get_fields()
+    assert info.cycles == 0
+    assert np.array_equal(rg, rho) and all(np.array_equal(a, b) for a, b in zip(vg, vel))
+
+
+# --------------------------------------------------------------- rows of the path
+def test_prepare_rows_vorticity_source_iterate():
+    """omega^k, S and g^0 (PFC) after fm_prepare against the oracle."""
+    rng = np.random.default_rng(12)
+    n, h, s = 32, 0.7, 0.03
+    rho = 0.9 + 0.05 * rng.uniform(-1, 1, (n, n))
+    vel = [0.1 * rng.standard_normal((n, n)) for _ in range(2)]
+    prm = dict(kind="pfc", dim=2, h=h, dt=s, alpha=0.6)
+    P, _, _ = oracle_setup(rho, prm)
+    sol = gpu_solver(rho, prm)
+    sol.set_fields(rho, vel)
+    fm.fm_prepare(sol.handle, s)
+    om = S.vorticity(vel, h)
+    Sx = S.source(rho, vel, om, P)
+    g0 = S.initial_iterate(rho, vel, P)
+    assert rel(sol.aux(fm.FM_AUX_OMEGA, 0), om[0]) < 1e-14
+    for c in range(5):
+        assert rel(sol.aux(fm.FM_AUX_SOURCE, c), Sx[c]) < 1e-13, c
+        assert rel(sol.aux(fm.FM_AUX_ITERATE, c), g0[c]) < 1e-13, c
+
+
+@pytest.mark.parametrize("kind", ["pfc", "cdft"])
+def test_residual_row(kind):
+    """r = S - N(g) for an arbitrary g against the oracle's N and S."""
+    rng = np.random.default_rng(13)
+    n = 32
+    if kind == "pfc":
+        h, prm = 0.7, dict(kind="pfc", dim=2, h=0.7, dt=0.03, alpha=0.6)
+        rho = 0.9 + 0.05 * rng.uniform(-1, 1, (n, n))
+    else:
+        h, prm = 17.0 / 32, dict(kind="cdft", dim=2, h=17.0 / 32, dt=0.02, nu=2.362, delta=1e-10)
+        rho = 0.3 + 0.05 * rng.uniform(0, 1, (n, n))
+    vel = [0.1 * rng.standard_normal((n, n)) for _ in range(2)]
+    P, _, J = oracle_setup(rho, prm)
+    sol = gpu_solver(rho, prm)
+    sol.set_fields(rho, vel)
+    fm.fm_prepare(sol.handle, prm["dt"])
+    g = [rho + 0.01 * rng.standard_normal((n, n))] + [v + 0.01 * rng.standard_normal((n, n)) for v in vel]
+    if kind == "pfc":
+        g += [rng.standard_normal((n, n)), rng.standard_normal((n, n))]
+    r_gpu = [np.empty((n, n)) for _ in g]
+    nrm = fm.fm_residual(sol.handle, g, r_gpu)
+    om = S.vorticity(vel, h)
+    C = S.conv_fft(J, rho, h) if kind == "cdft" else None
+    Sx = S.source(rho, vel, om, P, C)
+    r_or = S.residual(g, Sx, S.Coeffs(rho, om), P)
+    for a, b in zip(r_gpu, r_or):
+        assert np.max(np.abs(a - b)) <= 1e-12 * max(1.0, np.max(np.abs(b)))
+    assert abs(nrm - S.res_norm(r_or, h)) <= 1e-12 * S.res_norm(r_or, h)
+
+
+@pytest.mark.parametrize("n", [8, 32, 256])
+def test_convolution_row(n):
+    """J * rho by the CUDA FFT against the oracle's DFT, and against the direct
+    O(N^2) sum of Eq. (discrete_convolution) on the small grid."""
+    h = 34.0 / n
+    rng = np.random.default_rng(n)
+    rho = 0.3 + 0.05 * rng.uniform(0, 1, (n, n))
+    prm = dict(kind="cdft", dim=2, h=h, dt=0.02, nu=2.362, delta=1e-10)
+    sol = gpu_solver(rho, prm)
+    out = np.empty((n, n))
+    fm.fm_convolve(sol.handle, rho, out)
+    J, _, _ = S.sample_kernel((n, n), h, 2.362)
+    ref = S.conv_fft(J, rho, h)
+    assert np.max(np.abs(out - ref)) <= 1e-13 * np.max(np.abs(ref))
+    if n <= 32:
+        assert np.max(np.abs(out - S.conv_direct(J, rho, h))) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_transfer_rows():
+    """Full-weighting restriction and bilinear prolongation (2-D and 3-D)."""
+    rng = np.random.default_rng(14)
+    for shape in [(16, 24), (8, 8, 8)]:
+        dim = len(shape)
+        prm = dict(kind="pfc", dim=dim, h=0.5, dt=0.01, alpha=0.6)
+        sol = gpu_solver(np.zeros(shape), prm)
+        fine = rng.standard_normal(shape)
+        coarse = np.empty(tuple(x // 2 for x in shape))
+        fm.fm_restrict(sol.handle, fine, coarse)
+        assert np.max(np.abs(coarse - S.restrict_fw(fine))) < 1e-14
+        E = rng.standard_normal(coarse.shape)
+        f2 = fine.copy()
+        fm.fm_prolong_add(sol.handle, E, f2)
+        assert np.max(np.abs(f2 - (fine + S.prolong(E)))) < 1e-14
+
+
+@pytest.mark.parametrize("kind", ["pfc", "cdft"])
+def test_energy_and_mass_rows(kind):
+    rng = np.random.default_rng(15)
+    n = 64
+    if kind == "pfc":
+        prm = dict(kind="pfc", dim=2, h=0.7, dt=0.03, alpha=0.6)
+        rho = 0.9 + 0.05 * rng.uniform(-1, 1, (n, n))
+    else:
+        prm = dict(kind="cdft", dim=2, h=17.0 / 64, dt=0.02, nu=2.362, delta=1e-10)
+        rho = 0.3 + 0.05 * rng.uniform(0, 1, (n, n))
+    vel = [0.1 * rng.standard_normal((n, n)) for _ in range(2)]
+    P, _, J = oracle_setup(rho, prm)
+    sol = gpu_solver(rho, prm)
+    sol.set_fields(rho, vel)
+    E, F, K = sol.energy()
+    Eo, Fo, Ko = S.energy(rho, vel, P, J)
+    assert abs(E - Eo) <= 1e-12 * abs(Eo) and abs(F - Fo) <= 1e-12 * abs(Fo) and abs(K - Ko) <= 1e-12 * abs(Ko)
+    assert abs(sol.mass() - S.mass(rho, P.h)) <= 1e-14 * S.mass(rho, P.h)
+
+
+# --------------------------------------------------------------- invariants
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_mass_and_energy_over_steps(precision):
+    """Thm 5.1 on the device: mass to round-off and energy non-increasing
+    over 20 steps of the 64^2 PFC workload."""
+    rho, vel, prm = inputs.pfc64()
+    sol = gpu_solver(rho, prm, precision=precision, w_damp=0.0)
+    sol.set_fields(rho, vel)
+    M0 = sol.mass()
+    E0 = sol.energy()[0]
+    for _ in range(20):
+        sol.step(prm["dt"])
+        M = sol.mass()
+        E = sol.energy()[0]
+        assert abs(M - M0) <= 1e-13 * abs(M0)
+        assert E <= E0 + 1e-9
+        E0 = E
+
+
+# --------------------------------------------------------------- full size
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_full_size_pfc512_one_step(precision):
+    """The 512^2 PFC workload at full size, in the configuration the benchmark
+    times (undamped, tol 1e-10): one step against the oracle, whole fields."""
+    rho, vel, prm = inputs.pfc512()
+    _compare_step(rho, vel, prm, precision, tol=1e-11, w_damp=0.0, steps=1)
+
+
+# --------------------------------------------------------------- failure paths
+def test_no_convergence_leaves_state_unchanged():
+    rho, vel, prm = inputs.pfc64()
+    sol = gpu_solver(rho, prm, tol=1e-30, max_cycles=1)
+    sol.set_fields(rho, vel)
+    code, info = fm.fm_step_raw(sol.handle, prm["dt"])
+    assert code == fm.FM_ENOCONV
+    rg, vg = sol.get_fields()
+    assert np.array_equal(rg, rho) and all(np.array_equal(a, b) for a, b in zip(vg, vel))
+
+
+def test_nan_input_reports_enan():
+    rho, vel, prm = inputs.pfc64()
+    rho = rho.copy()
+    rho[3, 5] = math.nan
+    sol = gpu_solver(rho, prm)
+    sol.set_fields(rho, vel)
+    code, _ = fm.fm_step_raw(sol.handle, prm["dt"])
+    assert code == fm.FM_ENAN
