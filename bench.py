@@ -173,7 +173,10 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
 
     results = {}
-    for name, prec in (("mixed", fm.FM_MIXED), ("fp64", fm.FM_FP64)):
+    arms = (("mixed", fm.FM_MIXED), ("fp64", fm.FM_FP64))
+    if args.only:
+        arms = tuple(a for a in arms if a[0] == args.only)
+    for name, prec in arms:
         sol = make_solver(fm, rho.shape, prm, prec, stream)
         if world > 1:
             dist.barrier()
@@ -188,6 +191,15 @@ def run_ours(args):
             total_ms = float(t.item())
         results[name] = dict(total_ms=total_ms, cycles=cycles, launches=launches, prof=prof,
                              clocks=clk.summary(), sol=sol, prec=prec)
+
+    if args.no_e2e or args.only:
+        for r in results.values():
+            r["sol"].close()
+        if rank == 0:
+            print(json.dumps({k: {"ms_per_step": v["total_ms"] / args.steps, "cycles": v["cycles"][:5],
+                                  "launches": v["launches"], "smoother": v["prof"]}
+                              for k, v in results.items()}))
+        return
 
     # end to end through the C ABI with host buffers (mixed path)
     sol = results["mixed"]["sol"]
@@ -356,6 +368,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
+                    help="time one arm only and print a short diagnostic line (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
