@@ -191,6 +191,25 @@ int fm_profile(fm_state* st, int enable);
 int fm_profile_read(const fm_state* st, double* smoother_ms, long long* smoother_launches,
                     long long* launches);
 
+/* ---- Allocation-free entry point (the paper has no counterpart). ---- */
+
+/* Largest grid fm_mass_noalloc accepts: 4096 blocks x 1024 points. */
+#define FM_NOALLOC_MAX_POINTS (4096LL * 1024LL)
+
+/* Mass h^d sum rho of the caller's float64 device array `rho` (dim = 2 or 3,
+ * n[0..dim-1] points, spacing h), written to the caller's device double
+ * `out`, issued on `stream` (a cudaStream_t; null = legacy default stream).
+ * It allocates no device memory: for callers that cannot call cudaMalloc
+ * (a host application whose device memory is reserved by its own allocator,
+ * or a time-critical loop that must not take cudaMalloc's implicit
+ * synchronisation).  Its 32 KiB reduction scratch is a static device array
+ * that every GPU loading libfm holds until exit; all calls share it, so calls
+ * that overlap on the GPU race.  The first call on each device looks up the
+ * scratch address (cudaGetSymbolAddress) and must come before any stream
+ * capture.  Returns FM_EINVAL for null pointers, bad dim/h or more than
+ * FM_NOALLOC_MAX_POINTS points; asynchronous (read `out` after the stream). */
+int fm_mass_noalloc(const double* rho, int dim, const int* n, double h, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,8 @@ _SIGS = {
     "fm_restrict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "fm_prolong_add": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "fm_levels": (C.c_int, [C.c_void_p]),
+    "fm_mass_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_double, C.c_void_p,
+                                  C.c_void_p]),
     "fm_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "fm_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                   C.POINTER(C.c_longlong)]),
@@ -229,6 +231,16 @@ def fm_prolong_add(st, coarse, fine):
 
 def fm_levels(st):
     return lib().fm_levels(st)
+
+
+def fm_mass_noalloc(rho, h, out, stream=0):
+    """Mass of a float64 CUDA tensor into a 1-element float64 CUDA tensor,
+    without any device allocation by the library (see include/fm.h)."""
+    dims = list(reversed(rho.shape))
+    n = (C.c_int * 3)(*(dims + [1] * (3 - len(dims))))
+    code = lib().fm_mass_noalloc(C.c_void_p(rho.data_ptr()), len(dims), n, C.c_double(h),
+                                 C.c_void_p(out.data_ptr()), C.c_void_p(stream))
+    _check(code, "fm_mass_noalloc")
 
 
 def fm_profile(st, enable):
