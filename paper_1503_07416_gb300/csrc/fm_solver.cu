@@ -106,38 +106,13 @@ __device__ __forceinline__ void smooth_point(const Lvl<T>& L, const Phys<T>& P, 
   for (int q = 0; q < LY::NU; ++q) E[q][c] = (T(1) - w) * eg[q] + w * eo[q];
 }
 
+// --------------------------------------------------------------------------
+// Point operations of one level (shared by the per-level kernels and the
+// single-block small-level V-cycle)
+// --------------------------------------------------------------------------
 template <typename T, int KIND, int DIM>
-__global__ void __launch_bounds__(TPB) k_smooth(Lvl<T> L, Phys<T> P, int color) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int i, j, k;
-  if (!colour_point(t, color, L.g, i, j, k)) return;
-  const Nb n = neighbours(i, j, k, L.g);
-  smooth_point<T, KIND, DIM>(L, P, n);
-}
-
-// Coarsest grid: one block, `iters` red-black iterations.
-template <typename T, int KIND, int DIM>
-__global__ void __launch_bounds__(TPB) k_coarsest(Lvl<T> L, Phys<T> P, int iters) {
-  const int half = L.g.N / 2;
-  for (int it = 0; it < iters; ++it) {
-    for (int color = 0; color < 2; ++color) {
-      for (int t = threadIdx.x; t < half; t += blockDim.x) {
-        int i, j, k;
-        colour_point(t, color, L.g, i, j, k);
-        const Nb n = neighbours(i, j, k, L.g);
-        smooth_point<T, KIND, DIM>(L, P, n);
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// r = f - M(e)
-template <typename T, int KIND, int DIM>
-__global__ void __launch_bounds__(TPB) k_resid(Lvl<T> L, Phys<T> P) {
+__device__ __forceinline__ void resid_point(const Lvl<T>& L, const Phys<T>& P, int idx) {
   using LY = Layout<KIND, DIM>;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= L.g.N) return;
   int i, j, k;
   coords(idx, L.g, i, j, k);
   const Nb n = neighbours(i, j, k, L.g);
@@ -147,11 +122,9 @@ __global__ void __launch_bounds__(TPB) k_resid(Lvl<T> L, Phys<T> P) {
   for (int q = 0; q < LY::NU; ++q) L.r[q][idx] = L.f[q][idx] - M[q];
 }
 
-// Coarse level C from fine level F: f_C = FW(r_F); e_C = eh_C = inject(e_F).
+// coarse point idx: f_C = FW(r_F); e_C = eh_C = inject(e_F)
 template <typename T, int NU, int DIM>
-__global__ void __launch_bounds__(TPB) k_restrict(Lvl<T> F, Lvl<T> C) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= C.g.N) return;
+__device__ __forceinline__ void restrict_point(const Lvl<T>& F, const Lvl<T>& C, int idx) {
   int I, J, K;
   coords(idx, C.g, I, J, K);
   const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
@@ -164,18 +137,19 @@ __global__ void __launch_bounds__(TPB) k_restrict(Lvl<T> F, Lvl<T> C) {
   } else {
     zs[0] = zs[1] = zs[2] = 0;
   }
-  const T wt[3] = {T(1), T(2), T(1)};
   constexpr int KZ = (DIM == 3) ? 3 : 1;
   const T norm = (DIM == 3) ? T(1.0 / 64.0) : T(1.0 / 16.0);
 #pragma unroll
   for (int q = 0; q < NU; ++q) {
     T acc = 0;
+#pragma unroll
     for (int c = 0; c < KZ; ++c) {
       const int zz = (DIM == 3) ? zs[c] : 0;
-      const T wz = (DIM == 3) ? wt[c] : T(1);
+      const T wz = (DIM == 3) ? (c == 1 ? T(2) : T(1)) : T(1);
+#pragma unroll
       for (int b = 0; b < 3; ++b) {
         const int rowb = (zz * F.g.ny + ys[b]) * F.g.nx;
-        const T wy = wz * wt[b];
+        const T wy = wz * (b == 1 ? T(2) : T(1));
         acc += wy * (F.r[q][rowb + xs[0]] + T(2) * F.r[q][rowb + xs[1]] + F.r[q][rowb + xs[2]]);
       }
     }
@@ -188,10 +162,8 @@ __global__ void __launch_bounds__(TPB) k_restrict(Lvl<T> F, Lvl<T> C) {
 
 // f_C += M_C(eh_C)
 template <typename T, int KIND, int DIM>
-__global__ void __launch_bounds__(TPB) k_coarse_rhs(Lvl<T> L, Phys<T> P) {
+__device__ __forceinline__ void coarse_rhs_point(const Lvl<T>& L, const Phys<T>& P, int idx) {
   using LY = Layout<KIND, DIM>;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= L.g.N) return;
   int i, j, k;
   coords(idx, L.g, i, j, k);
   const Nb n = neighbours(i, j, k, L.g);
@@ -201,34 +173,28 @@ __global__ void __launch_bounds__(TPB) k_coarse_rhs(Lvl<T> L, Phys<T> P) {
   for (int q = 0; q < LY::NU; ++q) L.f[q][idx] += M[q];
 }
 
-// e_F += P(e_C - eh_C)  (bilinear / trilinear)
+// fine point idx: e_F += P(e_C - eh_C)  (bilinear / trilinear)
 template <typename T, int NU, int DIM>
-__global__ void __launch_bounds__(TPB) k_prolong(Lvl<T> F, Lvl<T> C) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= F.g.N) return;
+__device__ __forceinline__ void prolong_point(const Lvl<T>& F, const Lvl<T>& C, int idx) {
   int i, j, k;
   coords(idx, F.g, i, j, k);
   int xi[2], yi[2], zi[2];
-  T xw[2], yw[2], zw[2];
-  int nxp, nyp, nzp;
-  {
-    const int X = i >> 1;
-    xi[0] = X; xw[0] = (i & 1) ? T(0.5) : T(1);
-    xi[1] = (X + 1 == C.g.nx) ? 0 : X + 1; xw[1] = T(0.5);
-    nxp = (i & 1) ? 2 : 1;
-    const int Y = j >> 1;
-    yi[0] = Y; yw[0] = (j & 1) ? T(0.5) : T(1);
-    yi[1] = (Y + 1 == C.g.ny) ? 0 : Y + 1; yw[1] = T(0.5);
-    nyp = (j & 1) ? 2 : 1;
-    if (DIM == 3) {
-      const int Z = k >> 1;
-      zi[0] = Z; zw[0] = (k & 1) ? T(0.5) : T(1);
-      zi[1] = (Z + 1 == C.g.nz) ? 0 : Z + 1; zw[1] = T(0.5);
-      nzp = (k & 1) ? 2 : 1;
-    } else {
-      zi[0] = zi[1] = 0; zw[0] = T(1); zw[1] = T(0); nzp = 1;
-    }
+  T xw, yw, zw;
+  const int X = i >> 1, Y = j >> 1, Z = k >> 1;
+  xi[0] = X; xi[1] = (X + 1 == C.g.nx) ? 0 : X + 1;
+  yi[0] = Y; yi[1] = (Y + 1 == C.g.ny) ? 0 : Y + 1;
+  const int nxp = (i & 1) ? 2 : 1, nyp = (j & 1) ? 2 : 1;
+  xw = (i & 1) ? T(0.5) : T(1);
+  yw = (j & 1) ? T(0.5) : T(1);
+  int nzp = 1;
+  zi[0] = zi[1] = 0;
+  zw = T(1);
+  if constexpr (DIM == 3) {
+    zi[0] = Z; zi[1] = (Z + 1 == C.g.nz) ? 0 : Z + 1;
+    nzp = (k & 1) ? 2 : 1;
+    zw = (k & 1) ? T(0.5) : T(1);
   }
+  const T w = xw * yw * zw;
 #pragma unroll
   for (int q = 0; q < NU; ++q) {
     T acc = 0;
@@ -236,33 +202,136 @@ __global__ void __launch_bounds__(TPB) k_prolong(Lvl<T> F, Lvl<T> C) {
       for (int b = 0; b < nyp; ++b)
         for (int a = 0; a < nxp; ++a) {
           const int ci = (zi[c] * C.g.ny + yi[b]) * C.g.nx + xi[a];
-          acc += zw[c] * yw[b] * xw[a] * (C.e[q][ci] - C.eh[q][ci]);
+          acc += C.e[q][ci] - C.eh[q][ci];
         }
-    F.e[q][idx] += acc;
+    F.e[q][idx] += w * acc;
   }
 }
 
-// Injection of up to 8 coefficient fields from a fine to a coarse grid.
+template <typename T, int KIND, int DIM>
+__global__ void __launch_bounds__(TPB) k_smooth(Lvl<T> L, Phys<T> P, int color) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (!colour_point(t, color, L.g, i, j, k)) return;
+  const Nb n = neighbours(i, j, k, L.g);
+  smooth_point<T, KIND, DIM>(L, P, n);
+}
+
+template <typename T, int KIND, int DIM>
+__global__ void __launch_bounds__(TPB) k_resid(Lvl<T> L, Phys<T> P) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < L.g.N) resid_point<T, KIND, DIM>(L, P, idx);
+}
+
+template <typename T, int NU, int DIM>
+__global__ void __launch_bounds__(TPB) k_restrict(Lvl<T> F, Lvl<T> C) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < C.g.N) restrict_point<T, NU, DIM>(F, C, idx);
+}
+
+template <typename T, int KIND, int DIM>
+__global__ void __launch_bounds__(TPB) k_coarse_rhs(Lvl<T> L, Phys<T> P) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < L.g.N) coarse_rhs_point<T, KIND, DIM>(L, P, idx);
+}
+
+template <typename T, int NU, int DIM>
+__global__ void __launch_bounds__(TPB) k_prolong(Lvl<T> F, Lvl<T> C) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < F.g.N) prolong_point<T, NU, DIM>(F, C, idx);
+}
+
+// The whole V-cycle of the small levels (each at most SMALL_N points) in one
+// thread block: phases separated by __syncthreads, data in L1/L2.
+constexpr int SMALL_N = 4096;
+constexpr int SMALL_TPB = 512;
+constexpr int MAXSMALL = 8;
+
 template <typename T>
-struct InjList {
-  const T* src[8];
-  T* dst[8];
+struct SmallLv {
+  Lvl<T> lv[MAXSMALL];
   int count;
 };
 
+template <typename T, int KIND, int DIM>
+__device__ __forceinline__ void block_smooth(const Lvl<T>& L, const Phys<T>& P, int iters) {
+  const int half = L.g.N / 2;
+  for (int it = 0; it < iters; ++it)
+    for (int color = 0; color < 2; ++color) {
+      for (int t = threadIdx.x; t < half; t += blockDim.x) {
+        int i, j, k;
+        colour_point(t, color, L.g, i, j, k);
+        const Nb n = neighbours(i, j, k, L.g);
+        smooth_point<T, KIND, DIM>(L, P, n);
+      }
+      __syncthreads();
+    }
+}
+
+template <typename T, int KIND, int DIM>
+__global__ void __launch_bounds__(SMALL_TPB) k_vcycle_small(SmallLv<T> S, Phys<T> P, int nu1, int nu2,
+                                                            int ncoarse) {
+  using LY = Layout<KIND, DIM>;
+  const int nl = S.count;
+  for (int l = 0; l + 1 < nl; ++l) {
+    const Lvl<T>& F = S.lv[l];
+    const Lvl<T>& C = S.lv[l + 1];
+    block_smooth<T, KIND, DIM>(F, P, nu1);
+    for (int idx = threadIdx.x; idx < F.g.N; idx += blockDim.x) resid_point<T, KIND, DIM>(F, P, idx);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < C.g.N; idx += blockDim.x) restrict_point<T, LY::NU, DIM>(F, C, idx);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < C.g.N; idx += blockDim.x) coarse_rhs_point<T, KIND, DIM>(C, P, idx);
+    __syncthreads();
+  }
+  block_smooth<T, KIND, DIM>(S.lv[nl - 1], P, ncoarse);
+  for (int l = nl - 2; l >= 0; --l) {
+    const Lvl<T>& F = S.lv[l];
+    const Lvl<T>& C = S.lv[l + 1];
+    for (int idx = threadIdx.x; idx < F.g.N; idx += blockDim.x) prolong_point<T, LY::NU, DIM>(F, C, idx);
+    __syncthreads();
+    block_smooth<T, KIND, DIM>(F, P, nu2);
+  }
+}
+
+// Injection of up to 6 coefficient fields from the finest grid to every
+// coarser level at once (injection of an injection samples every 2^l-th
+// point of the finest grid).
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_inject(InjList<T> L, Geo F, Geo C) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= C.N) return;
+struct InjAll {
+  const T* src[6];
+  T* dst[MAXLEV][6];
+  Geo g[MAXLEV];
+  int off[MAXLEV + 1];
+  int nsrc;
+  int nl;      // levels 1..nl-1 are written
+  Geo g0;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_inject_all(InjAll<T> A) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= A.off[A.nl]) return;
+  int l = 1;
+  while (t >= A.off[l + 1]) ++l;
+  const int idx = t - A.off[l];
   int I, J, K;
-  coords(idx, C, I, J, K);
-  const int fidx = ((2 * K) * F.ny + 2 * J) * F.nx + 2 * I;
-  for (int q = 0; q < L.count; ++q) L.dst[q][idx] = L.src[q][fidx];
+  coords(idx, A.g[l], I, J, K);
+  const int sc = 1 << l;
+  const int fidx = ((K * sc) * A.g0.ny + J * sc) * A.g0.nx + I * sc;
+  for (int q = 0; q < A.nsrc; ++q) A.dst[l][q][idx] = A.src[q][fidx];
 }
 
 // --------------------------------------------------------------------------
 // float64 kernels of the finest level
 // --------------------------------------------------------------------------
+struct Vel3 {
+  const double* p[3];
+};
+struct Vel3W {
+  double* p[3];
+};
+
 struct Fields64 {
   const double* rho;          // rho^k
   const double* vel[3];       // u^k
@@ -525,9 +594,67 @@ __global__ void __launch_bounds__(TPB) k_update64(Fields64 F, Resid64Out O, int 
   F.g[0][idx] = (delta > 0.0) ? sqrt(r * r + delta * delta) : fabs(r);
 }
 
-// rho^{k+1} = S1 - (s/4h) sum_d [rho^k u_d]_{+} - [rho^k u_d]_{-}, projected.
+// Device-side control block of one step: residual norms, cycle count and
+// status; read by the host once per step (graph mode) or per cycle.
+struct Ctl {
+  double norm;
+  double norm0;
+  int cycles;
+  int status;
+  int pad[2];
+};
+
+// Finishes the residual norm max_q sqrt(w * sum_q), updates the control
+// block (cycles += in_body) and, in graph mode, sets the WHILE condition:
+// continue while the norm is finite, above tol and cycles < max_cycles.
+template <int NQ>
+__global__ void k_norm_ctl(const double* partials, int nblk, double w, Ctl* ctl, double tol, int max_cycles,
+                           int in_body, cudaGraphConditionalHandle handle, int use_handle) {
+  double v[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) v[q] = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += TPB)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] += partials[b * NQ + q];
+  __shared__ double sm[NQ][TPB / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+    for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sm[q][warp] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    bool finite = true;
+    for (int q = 0; q < NQ; ++q) {
+      double x = 0.0;
+      for (int ww = 0; ww < TPB / 32; ++ww) x += sm[q][ww];
+      const double nq = sqrt(w * x);
+      if (!(nq == nq) || isinf(nq)) finite = false;
+      mx = fmax(mx, nq);
+    }
+    const double nrm = finite ? mx : NAN;
+    int cycles = in_body ? ctl->cycles + 1 : 0;
+    ctl->cycles = cycles;
+    ctl->norm = nrm;
+    if (!in_body) ctl->norm0 = nrm;
+    int status = FM_OK;
+    if (!finite) status = FM_ENAN;
+    else if (nrm > tol && cycles >= max_cycles) status = FM_ENOCONV;
+    ctl->status = status;
+    const bool cont = status == FM_OK && nrm > tol;
+    if (use_handle) cudaGraphSetConditional(handle, cont ? 1u : 0u);
+  }
+}
+
+// rho^{k+1} = S1 - (s/4h) sum_d ([rho^k u_d]_{+d} - [rho^k u_d]_{-d}), projected,
+// into `out`; skipped unless the solve succeeded.
 template <int DIM>
-__global__ void __launch_bounds__(TPB) k_closure(Fields64 F, Geo G, double h, Phys<double> P, double* out) {
+__global__ void __launch_bounds__(TPB) k_closure(Fields64 F, Geo G, double h, Phys<double> P, double* out,
+                                                 const Ctl* ctl) {
+  if (ctl->status != FM_OK) return;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= G.N) return;
   int i, j, k;
@@ -541,12 +668,21 @@ __global__ void __launch_bounds__(TPB) k_closure(Fields64 F, Geo G, double h, Ph
   out[idx] = (P.delta > 0.0) ? sqrt(r * r + P.delta * P.delta) : fabs(r);
 }
 
+// New time level: rho <- closure result, u <- converged velocity (if the
+// solve succeeded).
+template <int DIM>
+__global__ void __launch_bounds__(TPB) k_commit(double* rho, Vel3W vel, const double* rnew, Vel3 gvel, int N,
+                                                const Ctl* ctl) {
+  if (ctl->status != FM_OK) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N) return;
+  rho[idx] = rnew[idx];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) vel.p[d][idx] = gvel.p[d][idx];
+}
+
 // Energy densities: q0 = KE, then PFC: psi^4/12, alpha psi^2/2, (Lap rho)^2/2,
 // rho Lap rho; CDFT: rho (ln rho - 1), -rho (J*rho)/2.
-struct Vel3 {
-  const double* p[3];
-};
-
 template <int KIND, int DIM>
 __global__ void __launch_bounds__(TPB) k_energy(const double* rho, Vel3 vel3,
                                                 const double* conv, Geo G, double h, double alpha,
@@ -719,11 +855,57 @@ static int harvest_profile(fm_state* st) {
   return FM_OK;
 }
 
+// The step is issued in three parts:
+//   pre  : omega^k, (J * rho^k), S, g^0, coefficients rho^k/omega^k down the
+//          hierarchy, the float64 residual of g^0 and its norm;
+//   body : coefficients g down the hierarchy, one FAS V-cycle on the
+//          correction equation, g += e, the float64 residual and its norm;
+//   post : closure and commit of the new time level (skipped on failure),
+//          the control block copied to pinned host memory.
+// Graph mode captures pre, a WHILE conditional node around body, and post
+// into one CUDA graph (one launch and one host synchronisation per step);
+// host-loop mode (used while profiling) launches the parts directly and
+// reads the control block after each norm.
 template <typename T, int KIND, int DIM>
 struct Solver {
   using LY = Layout<KIND, DIM>;
 
-  static int prepare(fm_state* st) {
+  static int inject_all(fm_state* st, bool coefficients_only) {
+    if (st->nlev < 2) return FM_OK;
+    InjAll<T> A;
+    memset(&A, 0, sizeof(A));
+    A.nl = st->nlev;
+    A.g0 = st->lv[0].g;
+    A.off[0] = A.off[1] = 0;
+    for (int l = 1; l < st->nlev; ++l) {
+      A.g[l] = st->lv[l].g;
+      A.off[l + 1] = A.off[l] + st->lv[l].g.N;
+    }
+    int q = 0;
+    if (coefficients_only) {
+      A.src[q] = (const T*)st->lv[0].cr;
+      for (int l = 1; l < st->nlev; ++l) A.dst[l][q] = (T*)st->lv[l].cr;
+      ++q;
+      for (int d = 0; d < DIM; ++d, ++q) {
+        A.src[q] = (const T*)st->lv[0].cv[d];
+        for (int l = 1; l < st->nlev; ++l) A.dst[l][q] = (T*)st->lv[l].cv[d];
+      }
+    } else {
+      A.src[q] = (const T*)st->lv[0].rk;
+      for (int l = 1; l < st->nlev; ++l) A.dst[l][q] = (T*)st->lv[l].rk;
+      ++q;
+      for (int d = 0; d < LY::NOM; ++d, ++q) {
+        A.src[q] = (const T*)st->lv[0].om[d];
+        for (int l = 1; l < st->nlev; ++l) A.dst[l][q] = (T*)st->lv[l].om[d];
+      }
+    }
+    A.nsrc = q;
+    k_inject_all<T><<<nblocks(A.off[st->nlev]), TPB, 0, st->stream>>>(A);
+    FM_LAUNCHED();
+    return FM_OK;
+  }
+
+  static int enqueue_prepare(fm_state* st) {
     const Geo G = st->lv[0].g;
     const double h = st->lv[0].h;
     Phys<double> P = make_phys<double>(st);
@@ -739,30 +921,18 @@ struct Solver {
       k_prepare_mu<DIM><<<nblocks(G.N), TPB, 0, s>>>(F, G, h, P);
       FM_LAUNCHED();
     }
-    // coefficients rho^k, omega^k down the hierarchy (once per step)
-    for (int l = 0; l + 1 < st->nlev; ++l) {
-      InjList<T> L;
-      L.count = 1 + LY::NOM;
-      L.src[0] = (const T*)st->lv[l].rk;
-      L.dst[0] = (T*)st->lv[l + 1].rk;
-      for (int d = 0; d < LY::NOM; ++d) {
-        L.src[1 + d] = (const T*)st->lv[l].om[d];
-        L.dst[1 + d] = (T*)st->lv[l + 1].om[d];
-      }
-      k_inject<T><<<nblocks(st->lv[l + 1].g.N), TPB, 0, s>>>(L, st->lv[l].g, st->lv[l + 1].g);
-      FM_LAUNCHED();
-    }
+    return inject_all(st, false);
+  }
+
+  static int prepare(fm_state* st) {
+    int rc = enqueue_prepare(st);
+    if (rc) return rc;
+    FM_CUDA(cudaStreamSynchronize(st->stream));
     st->prepared = true;
     return FM_OK;
   }
 
-  // Float64 residual (+ level-0 set-up for a cycle when `cycle` is true).
-  static int residual64(fm_state* st, bool cycle, double* const* r64, double* norm_host) {
-    const Geo G = st->lv[0].g;
-    const double h = st->lv[0].h;
-    Phys<double> P = make_phys<double>(st);
-    cudaStream_t s = st->stream;
-    Fields64 F = make_fields(st);
+  static Resid64Out resid_out(fm_state* st, bool cycle, double* const* r64) {
     Resid64Out O;
     for (int q = 0; q < MAXU; ++q) {
       O.f0[q] = (cycle && q < LY::NU) ? st->lv[0].f[q] : nullptr;
@@ -775,6 +945,35 @@ struct Solver {
       O.cr32 = (float*)st->lv[0].cr;
       for (int d = 0; d < DIM; ++d) O.cv32[d] = (float*)st->lv[0].cv[d];
     }
+    return O;
+  }
+
+  // float64 residual of the current iterate, the level-0 set-up of a cycle
+  // and the control-block update (in_body: this follows a cycle).
+  static int enqueue_resid_norm(fm_state* st, int in_body, cudaGraphConditionalHandle hdl, int use_handle) {
+    const Geo G = st->lv[0].g;
+    const double h = st->lv[0].h;
+    Phys<double> P = make_phys<double>(st);
+    cudaStream_t s = st->stream;
+    Fields64 F = make_fields(st);
+    Resid64Out O = resid_out(st, true, nullptr);
+    k_resid64<KIND, DIM, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
+    FM_LAUNCHED();
+    const double w = (DIM == 3) ? h * h * h : h * h;
+    k_norm_ctl<LY::NU><<<1, TPB, 0, s>>>(st->partials, st->nblk, w, (Ctl*)st->ctl, st->prm.tol,
+                                         st->prm.max_cycles, in_body, hdl, use_handle);
+    FM_LAUNCHED();
+    return FM_OK;
+  }
+
+  // Standalone float64 residual for fm_residual (synchronous).
+  static int residual64(fm_state* st, double* const* r64, double* norm_host) {
+    const Geo G = st->lv[0].g;
+    const double h = st->lv[0].h;
+    Phys<double> P = make_phys<double>(st);
+    cudaStream_t s = st->stream;
+    Fields64 F = make_fields(st);
+    Resid64Out O = resid_out(st, false, r64);
     k_resid64<KIND, DIM, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
     FM_LAUNCHED();
     const double w = (DIM == 3) ? h * h * h : h * h;
@@ -783,23 +982,6 @@ struct Solver {
     FM_CUDA(cudaMemcpyAsync(st->hscal, st->dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
     FM_CUDA(cudaStreamSynchronize(s));
     *norm_host = st->hscal[0];
-    return harvest_profile(st);
-  }
-
-  static int inject_coefficients(fm_state* st) {
-    cudaStream_t s = st->stream;
-    for (int l = 0; l + 1 < st->nlev; ++l) {
-      InjList<T> L;
-      L.count = 1 + DIM;
-      L.src[0] = (const T*)st->lv[l].cr;
-      L.dst[0] = (T*)st->lv[l + 1].cr;
-      for (int d = 0; d < DIM; ++d) {
-        L.src[1 + d] = (const T*)st->lv[l].cv[d];
-        L.dst[1 + d] = (T*)st->lv[l + 1].cv[d];
-      }
-      k_inject<T><<<nblocks(st->lv[l + 1].g.N), TPB, 0, s>>>(L, st->lv[l].g, st->lv[l + 1].g);
-      FM_LAUNCHED();
-    }
     return FM_OK;
   }
 
@@ -807,7 +989,7 @@ struct Solver {
     cudaStream_t s = st->stream;
     Lvl<T> L = make_lvl<T>(st, l);
     const int half = L.g.N / 2;
-    const bool prof = st->prof && l == 0;
+    const bool prof = st->prof && !st->capturing && l == 0;
     for (int it = 0; it < iters; ++it)
       for (int color = 0; color < 2; ++color) {
         if (prof && st->npev + 2 <= MAXEV) FM_CUDA(cudaEventRecord(st->pev[st->npev], s));
@@ -823,9 +1005,11 @@ struct Solver {
 
   static int vcycle(fm_state* st, int l, const Phys<T>& P) {
     cudaStream_t s = st->stream;
-    if (l == st->nlev - 1) {
-      Lvl<T> L = make_lvl<T>(st, l);
-      k_coarsest<T, KIND, DIM><<<1, TPB, 0, s>>>(L, P, st->prm.ncoarse);
+    if (l >= st->small_from) {
+      SmallLv<T> S;
+      S.count = st->nlev - l;
+      for (int q = 0; q < S.count; ++q) S.lv[q] = make_lvl<T>(st, l + q);
+      k_vcycle_small<T, KIND, DIM><<<1, SMALL_TPB, 0, s>>>(S, P, st->prm.nu1, st->prm.nu2, st->prm.ncoarse);
       FM_LAUNCHED();
       return FM_OK;
     }
@@ -846,63 +1030,157 @@ struct Solver {
     return smooth(st, l, P, st->prm.nu2);
   }
 
-  static int update(fm_state* st) {
+  static int enqueue_body(fm_state* st, cudaGraphConditionalHandle hdl, int use_handle) {
+    int rc = inject_all(st, true);
+    if (rc) return rc;
+    Phys<T> P = make_phys<T>(st);
+    rc = vcycle(st, 0, P);
+    if (rc) return rc;
     const Geo G = st->lv[0].g;
     Fields64 F = make_fields(st);
-    Resid64Out O;
-    for (int q = 0; q < MAXU; ++q) O.e0[q] = (q < LY::NU) ? st->lv[0].e[q] : nullptr;
+    Resid64Out O = resid_out(st, true, nullptr);
     k_update64<LY::NU, T><<<nblocks(G.N), TPB, 0, st->stream>>>(F, O, G.N, st->prm.delta);
     FM_LAUNCHED();
+    return enqueue_resid_norm(st, 1, hdl, use_handle);
+  }
+
+  static int enqueue_post(fm_state* st) {
+    const Geo G = st->lv[0].g;
+    Fields64 F = make_fields(st);
+    Phys<double> P64 = make_phys<double>(st);
+    const Ctl* ctl = (const Ctl*)st->ctl;
+    k_closure<DIM><<<nblocks(G.N), TPB, 0, st->stream>>>(F, G, st->lv[0].h, P64, st->tmp, ctl);
+    FM_LAUNCHED();
+    Vel3W vw{{st->vel[0], st->vel[1], st->vel[2]}};
+    Vel3 gv{{st->g[1], st->g[2], DIM == 3 ? st->g[3] : nullptr}};
+    k_commit<DIM><<<nblocks(G.N), TPB, 0, st->stream>>>(st->rho, vw, st->tmp, gv, G.N, ctl);
+    FM_LAUNCHED();
+    FM_CUDA(cudaMemcpyAsync(st->hscal + 32, st->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st->stream));
+    return FM_OK;
+  }
+
+  static int read_ctl(fm_state* st, Ctl* out) {
+    FM_CUDA(cudaMemcpyAsync(st->hscal + 32, st->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st->stream));
+    FM_CUDA(cudaStreamSynchronize(st->stream));
+    memcpy(out, st->hscal + 32, sizeof(Ctl));
+    return harvest_profile(st);
+  }
+
+  static int finish(fm_state* st, fm_step_info* info) {
+    Ctl c;
+    memcpy(&c, st->hscal + 32, sizeof(Ctl));
+    st->prepared = false;
+    if (info) {
+      info->cycles = c.cycles;
+      info->res0 = c.norm0;
+      info->res = c.norm;
+    }
+    return c.status;
+  }
+
+  static int step_hostloop(fm_state* st, fm_step_info* info) {
+    int rc = enqueue_prepare(st);
+    if (rc) return rc;
+    rc = enqueue_resid_norm(st, 0, 0, 0);
+    if (rc) return rc;
+    Ctl c;
+    for (;;) {
+      rc = read_ctl(st, &c);
+      if (rc) return rc;
+      if (c.status != FM_OK || !(c.norm > st->prm.tol)) break;
+      rc = enqueue_body(st, 0, 0);
+      if (rc) return rc;
+    }
+    rc = enqueue_post(st);
+    if (rc) return rc;
+    FM_CUDA(cudaStreamSynchronize(st->stream));
+    return finish(st, info);
+  }
+
+  static int build_graph(fm_state* st) {
+    if (st->gexec) {
+      cudaGraphExecDestroy(st->gexec);
+      st->gexec = nullptr;
+    }
+    if (st->graph) {
+      cudaGraphDestroy(st->graph);
+      st->graph = nullptr;
+    }
+    cudaStream_t saved = st->stream;
+    cudaStream_t s0 = st->cap[0], s1 = st->cap[1];
+    st->capturing = true;
+    st->stream = s0;
+    int rc = FM_OK;
+    cudaGraph_t g = nullptr;
+    do {
+      if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = FM_ECUDA; break; }
+      const long long l0 = st->launches;
+      rc = enqueue_prepare(st);
+      if (rc) break;
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      cudaGraph_t cg = nullptr;
+      if (cudaStreamGetCaptureInfo(s0, &cs, nullptr, &cg, nullptr, nullptr, nullptr) != cudaSuccess) { rc = FM_ECUDA; break; }
+      cudaGraphConditionalHandle hdl;
+      if (cudaGraphConditionalHandleCreate(&hdl, cg, 0, cudaGraphCondAssignDefault) != cudaSuccess) { rc = FM_ECUDA; break; }
+      rc = enqueue_resid_norm(st, 0, hdl, 1);
+      if (rc) break;
+      st->cnt_pre = st->launches - l0;
+      if (cudaStreamGetCaptureInfo(s0, &cs, nullptr, &cg, &deps, nullptr, &nd) != cudaSuccess) { rc = FM_ECUDA; break; }
+      cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+      cp.conditional.handle = hdl;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t wnode;
+      if (cudaGraphAddNode(&wnode, cg, deps, nullptr, nd, &cp) != cudaSuccess) { rc = FM_ECUDA; break; }
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      if (cudaStreamUpdateCaptureDependencies(s0, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess) { rc = FM_ECUDA; break; }
+      st->stream = s1;
+      if (cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = FM_ECUDA; break; }
+      const long long l1 = st->launches;
+      rc = enqueue_body(st, hdl, 1);
+      st->cnt_body = st->launches - l1;
+      cudaGraph_t bodyout = nullptr;
+      if (cudaStreamEndCapture(s1, &bodyout) != cudaSuccess && rc == FM_OK) rc = FM_ECUDA;
+      if (rc) break;
+      st->stream = s0;
+      const long long l2 = st->launches;
+      rc = enqueue_post(st);
+      st->cnt_post = st->launches - l2;
+      st->launches = l0;
+    } while (0);
+    st->stream = s0;
+    if (cudaStreamEndCapture(s0, &g) != cudaSuccess && rc == FM_OK) rc = FM_ECUDA;
+    st->stream = saved;
+    st->capturing = false;
+    if (rc) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (cudaGraphInstantiate(&st->gexec, g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphDestroy(g);
+      return FM_ECUDA;
+    }
+    st->graph = g;
+    st->graph_dt = st->dt;
     return FM_OK;
   }
 
   static int step(fm_state* st, fm_step_info* info) {
-    int rc = prepare(st);
-    if (rc) return rc;
-    Phys<T> P = make_phys<T>(st);
-    double nr = 0.0, nr0 = 0.0;
-    int cycles = 0;
-    for (;;) {
-      rc = residual64(st, true, nullptr, &nr);
+    if (st->prof || !st->use_graph) return step_hostloop(st, info);
+    if (!st->gexec || st->graph_dt != st->dt) {
+      int rc = build_graph(st);
       if (rc) return rc;
-      if (cycles == 0) nr0 = nr;
-      if (!(nr == nr) || std::isinf(nr)) return FM_ENAN;
-      if (nr <= st->prm.tol) break;
-      if (cycles >= st->prm.max_cycles) return FM_ENOCONV;
-      rc = inject_coefficients(st);
-      if (rc) return rc;
-      rc = vcycle(st, 0, P);
-      if (rc) return rc;
-      rc = update(st);
-      if (rc) return rc;
-      ++cycles;
     }
-    // closure into the iterate's rho buffer, then swap time levels
-    const Geo G = st->lv[0].g;
-    Fields64 F = make_fields(st);
-    Phys<double> P64 = make_phys<double>(st);
-    k_closure<DIM><<<nblocks(G.N), TPB, 0, st->stream>>>(F, G, st->lv[0].h, P64, st->g[0]);
-    FM_LAUNCHED();
-    double* t = st->rho;
-    st->rho = st->g[0];
-    st->g[0] = t;
-    for (int d = 0; d < DIM; ++d) {
-      t = st->vel[d];
-      st->vel[d] = st->g[1 + d];
-      st->g[1 + d] = t;
-    }
-    if (st->prm.precision == FM_FP64) {
-      st->lv[0].rk = st->rho;
-      st->lv[0].cr = st->g[0];
-      for (int d = 0; d < DIM; ++d) st->lv[0].cv[d] = st->g[1 + d];
-    }
-    st->prepared = false;
-    if (info) {
-      info->cycles = cycles;
-      info->res0 = nr0;
-      info->res = nr;
-    }
-    return FM_OK;
+    FM_CUDA(cudaGraphLaunch(st->gexec, st->stream));
+    FM_CUDA(cudaStreamSynchronize(st->stream));
+    Ctl c;
+    memcpy(&c, st->hscal + 32, sizeof(Ctl));
+    st->launches += st->cnt_pre + (long long)c.cycles * st->cnt_body + st->cnt_post;
+    return finish(st, info);
   }
 };
 
@@ -924,10 +1202,8 @@ static int dispatch_prepare(fm_state* st) {
 template <typename T>
 static int dispatch_resid(fm_state* st, double* const* r, double* nr) {
   if (st->kind == FM_PFC)
-    return st->dim == 2 ? Solver<T, KPFC, 2>::residual64(st, false, r, nr)
-                        : Solver<T, KPFC, 3>::residual64(st, false, r, nr);
-  return st->dim == 2 ? Solver<T, KCDFT, 2>::residual64(st, false, r, nr)
-                      : Solver<T, KCDFT, 3>::residual64(st, false, r, nr);
+    return st->dim == 2 ? Solver<T, KPFC, 2>::residual64(st, r, nr) : Solver<T, KPFC, 3>::residual64(st, r, nr);
+  return st->dim == 2 ? Solver<T, KCDFT, 2>::residual64(st, r, nr) : Solver<T, KCDFT, 3>::residual64(st, r, nr);
 }
 
 // --------------------------------------------------------------------------
@@ -963,6 +1239,7 @@ static size_t carve(fm_state* st, char* base) {
   for (int q = 0; q < MAXU; ++q) st->r64[q] = q < st->nu ? (double*)C.take(N0 * d8) : nullptr;
   st->partials = (double*)C.take((size_t)st->nblk * 8 * d8);
   st->dscal = (double*)C.take(64 * d8);
+  st->ctl = C.take(64);
   for (int l = 0; l < st->nlev; ++l) {
     LevelBufs& B = st->lv[l];
     const size_t N = B.g.N;
@@ -1092,6 +1369,16 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
     h *= 2.0;
   }
   st->nlev = nlev;
+  st->small_from = nlev - 1;
+  for (int l = 0; l < nlev; ++l)
+    if (st->lv[l].g.N <= SMALL_N && nlev - l <= MAXSMALL) {
+      st->small_from = l;
+      break;
+    }
+  {
+    const char* eg = getenv("FM_GRAPH");
+    st->use_graph = !(eg && eg[0] == '0');
+  }
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -1122,6 +1409,12 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
     fm_destroy(st);
     return FM_ECUDA;
   }
+  if (cudaStreamCreateWithFlags(&st->cap[0], cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&st->cap[1], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    fm_destroy(st);
+    return FM_ECUDA;
+  }
   st->ce = 0.0;
   if (st->kind == FM_CDFT) {
     const int rc = fft_init(st);
@@ -1143,6 +1436,10 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
 
 void fm_destroy(fm_state* st) {
   if (!st) return;
+  if (st->gexec) cudaGraphExecDestroy(st->gexec);
+  if (st->graph) cudaGraphDestroy(st->graph);
+  for (int i = 0; i < 2; ++i)
+    if (st->cap[i]) cudaStreamDestroy(st->cap[i]);
   if (st->pev_ready)
     for (int i = 0; i < MAXEV; ++i) cudaEventDestroy(st->pev[i]);
   if (st->arena) cudaFree(st->arena);

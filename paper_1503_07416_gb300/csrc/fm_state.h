@@ -57,6 +57,15 @@ struct fm_state {
   double dt;                      // step of the last fm_prepare
   bool prepared;
   cudaStream_t stream;
+  cudaStream_t cap[2];            // private streams used to capture the step graph
+  bool capturing;
+  bool use_graph;                 // run fm_step as one CUDA graph launch
+  int small_from;                 // first level handled by the single-block V-cycle
+  void* ctl;                      // device control block of the step
+  cudaGraph_t graph;
+  cudaGraphExec_t gexec;
+  double graph_dt;                // step size the graph was captured with
+  long long cnt_pre, cnt_body, cnt_post;  // kernels per graph part (launch accounting)
   long long launches;             // kernels launched by this state
   bool prof;                      // time the finest-level smoother launches
   bool pev_ready;
