@@ -255,11 +255,12 @@ def run_ours(args):
     value = world * steps / (mix["total_ms"] / 1e3)
     ms_per_step = mix["total_ms"] / steps
     peak, peak_kind = load_peaks()
-    # smoother roofline: algorithmic bytes of one colour half-sweep of the
-    # finest level = 20 words/point x N/2 points (float32)
+    # smoother roofline: one launch of the fused 2-D kernel is one red-black
+    # sweep of the finest level: algorithmic bytes = 20 words/point x N points
+    # (float32): read e (5), f (5), rho^k, omega^k, rho, u, v (5); write e (5)
     sm_ms, sm_n = mix["prof"]
     words = 20
-    bytes_launch = words * 4 * (N // 2)
+    bytes_launch = words * 4 * N
     avg_ms = sm_ms / max(1, sm_n)
     achieved = bytes_launch / (avg_ms * 1e-3) / 1e9 if sm_n else None
     traffic = None
@@ -296,11 +297,12 @@ def run_ours(args):
                 "ms_per_step": round(f64["total_ms"] / steps, 5),
                 "cycles_per_step_mean": round(statistics.mean(f64["cycles"]), 3),
                 "smoother_launch_ms": round(f64_avg, 6),
+                "smoother_gbs": round(words * 8 * N / (f64_avg * 1e-3) / 1e9, 1) if f64_sm_n else None,
             },
             "speedup_mixed_over_fp64": round(f64["total_ms"] / mix["total_ms"], 3),
         },
         "roofline": {
-            "kernel": "k_smooth<float,PFC,2> (finest level, one colour)",
+            "kernel": "k_smooth_rb2d<float,PFC> (finest level, one red-black sweep)",
             "bound": "hbm",
             "achieved": round(achieved, 1) if achieved else None,
             "peak": peak,

@@ -241,9 +241,106 @@ __global__ void __launch_bounds__(TPB) k_prolong(Lvl<T> F, Lvl<T> C) {
   if (idx < F.g.N) prolong_point<T, NU, DIM>(F, C, idx);
 }
 
+// Fused red-black sweep of a 2-D level: one thread block per RB_TX x RB_TY
+// tile.  The tile and a halo of two points of every array the point update
+// reads are staged in shared memory; red points are updated on the tile and
+// its first halo ring (their black neighbours are all staged), then black
+// points on the tile, and the tile's corrections are written back.  Red
+// values on the ring are recomputed identically by the neighbouring tiles, so
+// the result equals a red launch followed by a black launch.
+constexpr int RB_TX = 32, RB_TY = 16, RB_H = 2;
+constexpr int RB_SW = RB_TX + 2 * RB_H;
+constexpr int RB_SN = RB_SW * (RB_TY + 2 * RB_H);
+constexpr int RB_THREADS = 256;
+
+template <int KIND>
+constexpr int rb_arrays() {
+  return 2 * Layout<KIND, 2>::NU + 5;  // e, f, rk, om, cr, cv0, cv1
+}
+
+__device__ __forceinline__ int wrapi(int x, int n) {
+  x %= n;
+  return x < 0 ? x + n : x;
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(RB_THREADS) k_smooth_rb2d(Lvl<T> G, Phys<T> P) {
+  using LY = Layout<KIND, 2>;
+  constexpr int NU = LY::NU;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  const int nx = G.g.nx, ny = G.g.ny;
+  const int x0 = blockIdx.x * RB_TX, y0 = blockIdx.y * RB_TY;
+  for (int t = threadIdx.x; t < RB_SN; t += blockDim.x) {
+    const int ly = t / RB_SW, lx = t - ly * RB_SW;
+    const int gidx = wrapi(y0 + ly - RB_H, ny) * nx + wrapi(x0 + lx - RB_H, nx);
+#pragma unroll
+    for (int q = 0; q < NU; ++q) {
+      sm[q * RB_SN + t] = G.e[q][gidx];
+      sm[(NU + q) * RB_SN + t] = G.f[q][gidx];
+    }
+    sm[(2 * NU) * RB_SN + t] = G.rk[gidx];
+    sm[(2 * NU + 1) * RB_SN + t] = G.om[0][gidx];
+    sm[(2 * NU + 2) * RB_SN + t] = G.cr[gidx];
+    sm[(2 * NU + 3) * RB_SN + t] = G.cv[0][gidx];
+    sm[(2 * NU + 4) * RB_SN + t] = G.cv[1][gidx];
+  }
+  Lvl<T> L;
+  L.g = G.g;
+  L.h = G.h;
+#pragma unroll
+  for (int q = 0; q < MAXU; ++q) {
+    L.e[q] = q < NU ? sm + q * RB_SN : nullptr;
+    L.f[q] = q < NU ? sm + (NU + q) * RB_SN : nullptr;
+    L.r[q] = L.eh[q] = nullptr;
+  }
+  L.rk = sm + (2 * NU) * RB_SN;
+  L.om[0] = sm + (2 * NU + 1) * RB_SN;
+  L.om[1] = L.om[2] = nullptr;
+  L.cr = sm + (2 * NU + 2) * RB_SN;
+  L.cv[0] = sm + (2 * NU + 3) * RB_SN;
+  L.cv[1] = sm + (2 * NU + 4) * RB_SN;
+  L.cv[2] = nullptr;
+  __syncthreads();
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int color = pass;              // red (i + j even) first, then black
+    const int ring = pass == 0 ? 1 : 0;  // red also on the first halo ring
+    const int w = RB_TX + 2 * ring;      // even
+    const int hw = w >> 1;
+    const int npts = hw * (RB_TY + 2 * ring);
+    for (int t = threadIdx.x; t < npts; t += blockDim.x) {
+      const int ry = t / hw;
+      const int gy = y0 - ring + ry;
+      const int rx = 2 * (t - ry * hw) + ((color + x0 + ring + gy) & 1);
+      const int lx = RB_H - ring + rx, ly = RB_H - ring + ry;
+      Nb n;
+      n.c = ly * RB_SW + lx;
+      n.m[0] = n.c - 1;
+      n.p[0] = n.c + 1;
+      n.m[1] = n.c - RB_SW;
+      n.p[1] = n.c + RB_SW;
+      n.m[2] = n.p[2] = n.c;
+      smooth_point<T, KIND, 2>(L, P, n);
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < RB_TX * RB_TY; t += blockDim.x) {
+    const int ty = t / RB_TX, tx = t - ty * RB_TX;
+    const int gx = x0 + tx, gy = y0 + ty;
+    if (gx < nx && gy < ny) {
+      const int sidx = (ty + RB_H) * RB_SW + tx + RB_H;
+#pragma unroll
+      for (int q = 0; q < NU; ++q) G.e[q][gy * nx + gx] = L.e[q][sidx];
+    }
+  }
+}
+
 // The whole V-cycle of the small levels (each at most SMALL_N points) in one
 // thread block: phases separated by __syncthreads, data in L1/L2.
-constexpr int SMALL_N = 4096;
+constexpr int SMALL_N = 1024;           // levels of at most this many points run in one block
+constexpr int SMALL_SMEM_N = 1024;
+constexpr size_t SMALL_SMEM_MAX = 200 * 1024;
 constexpr int SMALL_TPB = 512;
 constexpr int MAXSMALL = 8;
 
@@ -291,6 +388,75 @@ __global__ void __launch_bounds__(SMALL_TPB) k_vcycle_small(SmallLv<T> S, Phys<T
     for (int idx = threadIdx.x; idx < F.g.N; idx += blockDim.x) prolong_point<T, LY::NU, DIM>(F, C, idx);
     __syncthreads();
     block_smooth<T, KIND, DIM>(F, P, nu2);
+  }
+}
+
+// Same V-cycle with the corrections, right-hand sides and residuals of the
+// small levels held in shared memory (coefficients are read through L1).
+// On entry the first small level's e and f are in global memory; on exit its
+// e is written back.  `layout` gives each level's shared-memory offsets.
+template <typename T>
+struct SmallSmem {
+  int off_e[MAXSMALL][MAXU];
+  int off_f[MAXSMALL][MAXU];
+  int off_r[MAXSMALL][MAXU];
+  int off_eh[MAXSMALL][MAXU];
+};
+
+template <typename T, int KIND, int DIM>
+__global__ void __launch_bounds__(SMALL_TPB) k_vcycle_small_smem(SmallLv<T> S, SmallSmem<T> M, Phys<T> P,
+                                                                 int nu1, int nu2, int ncoarse) {
+  using LY = Layout<KIND, DIM>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  __shared__ Lvl<T> SL[MAXSMALL];
+  const int nl = S.count;
+  if (threadIdx.x == 0) {
+    for (int l = 0; l < nl; ++l) {
+      SL[l] = S.lv[l];
+      for (int q = 0; q < MAXU; ++q) {
+        SL[l].e[q] = q < LY::NU ? sm + M.off_e[l][q] : nullptr;
+        SL[l].f[q] = q < LY::NU ? sm + M.off_f[l][q] : nullptr;
+        SL[l].r[q] = (q < LY::NU && l + 1 < nl) ? sm + M.off_r[l][q] : nullptr;
+        SL[l].eh[q] = (q < LY::NU && l > 0) ? sm + M.off_eh[l][q] : nullptr;
+      }
+    }
+  }
+  __syncthreads();
+  {
+    const Lvl<T>& G = S.lv[0];
+    for (int idx = threadIdx.x; idx < G.g.N; idx += blockDim.x)
+#pragma unroll
+      for (int q = 0; q < LY::NU; ++q) {
+        SL[0].e[q][idx] = G.e[q][idx];
+        SL[0].f[q][idx] = G.f[q][idx];
+      }
+  }
+  __syncthreads();
+  for (int l = 0; l + 1 < nl; ++l) {
+    const Lvl<T>& F = SL[l];
+    const Lvl<T>& C = SL[l + 1];
+    block_smooth<T, KIND, DIM>(F, P, nu1);
+    for (int idx = threadIdx.x; idx < F.g.N; idx += blockDim.x) resid_point<T, KIND, DIM>(F, P, idx);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < C.g.N; idx += blockDim.x) restrict_point<T, LY::NU, DIM>(F, C, idx);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < C.g.N; idx += blockDim.x) coarse_rhs_point<T, KIND, DIM>(C, P, idx);
+    __syncthreads();
+  }
+  block_smooth<T, KIND, DIM>(SL[nl - 1], P, ncoarse);
+  for (int l = nl - 2; l >= 0; --l) {
+    const Lvl<T>& F = SL[l];
+    const Lvl<T>& C = SL[l + 1];
+    for (int idx = threadIdx.x; idx < F.g.N; idx += blockDim.x) prolong_point<T, LY::NU, DIM>(F, C, idx);
+    __syncthreads();
+    block_smooth<T, KIND, DIM>(F, P, nu2);
+  }
+  {
+    const Lvl<T>& G = S.lv[0];
+    for (int idx = threadIdx.x; idx < G.g.N; idx += blockDim.x)
+#pragma unroll
+      for (int q = 0; q < LY::NU; ++q) G.e[q][idx] = SL[0].e[q][idx];
   }
 }
 
@@ -990,16 +1156,32 @@ struct Solver {
     Lvl<T> L = make_lvl<T>(st, l);
     const int half = L.g.N / 2;
     const bool prof = st->prof && !st->capturing && l == 0;
-    for (int it = 0; it < iters; ++it)
-      for (int color = 0; color < 2; ++color) {
+    const bool fused = DIM == 2 && st->fused_rb;
+    const size_t smem = (size_t)rb_arrays<KIND>() * RB_SN * sizeof(T);
+    if (fused) {
+      static bool attr = false;
+      if (!attr) {
+        FM_CUDA(cudaFuncSetAttribute(k_smooth_rb2d<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        attr = true;
+      }
+    }
+    const dim3 tiles((L.g.nx + RB_TX - 1) / RB_TX, (L.g.ny + RB_TY - 1) / RB_TY);
+    for (int it = 0; it < iters; ++it) {
+      const int nlaunch = fused ? 1 : 2;
+      for (int color = 0; color < nlaunch; ++color) {
         if (prof && st->npev + 2 <= MAXEV) FM_CUDA(cudaEventRecord(st->pev[st->npev], s));
-        k_smooth<T, KIND, DIM><<<nblocks(half), TPB, 0, s>>>(L, P, color);
+        if (fused)
+          k_smooth_rb2d<T, KIND><<<tiles, RB_THREADS, smem, s>>>(L, P);
+        else
+          k_smooth<T, KIND, DIM><<<nblocks(half), TPB, 0, s>>>(L, P, color);
         FM_LAUNCHED();
         if (prof && st->npev + 2 <= MAXEV) {
           FM_CUDA(cudaEventRecord(st->pev[st->npev + 1], s));
           st->npev += 2;
         }
       }
+    }
     return FM_OK;
   }
 
@@ -1009,7 +1191,32 @@ struct Solver {
       SmallLv<T> S;
       S.count = st->nlev - l;
       for (int q = 0; q < S.count; ++q) S.lv[q] = make_lvl<T>(st, l + q);
-      k_vcycle_small<T, KIND, DIM><<<1, SMALL_TPB, 0, s>>>(S, P, st->prm.nu1, st->prm.nu2, st->prm.ncoarse);
+      // shared-memory layout of the small levels' e, f, r, eh
+      SmallSmem<T> M;
+      memset(&M, 0, sizeof(M));
+      int off = 0;
+      for (int q = 0; q < S.count; ++q) {
+        const int N = S.lv[q].g.N;
+        for (int u = 0; u < LY::NU; ++u) {
+          M.off_e[q][u] = off; off += N;
+          M.off_f[q][u] = off; off += N;
+          if (q + 1 < S.count) { M.off_r[q][u] = off; off += N; }
+          if (q > 0) { M.off_eh[q][u] = off; off += N; }
+        }
+      }
+      const size_t smem = (size_t)off * sizeof(T);
+      if (smem <= SMALL_SMEM_MAX && S.lv[0].g.N <= SMALL_SMEM_N) {
+        static bool attr = false;
+        if (!attr) {
+          FM_CUDA(cudaFuncSetAttribute(k_vcycle_small_smem<T, KIND, DIM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_SMEM_MAX));
+          attr = true;
+        }
+        k_vcycle_small_smem<T, KIND, DIM><<<1, SMALL_TPB, smem, s>>>(S, M, P, st->prm.nu1, st->prm.nu2,
+                                                                      st->prm.ncoarse);
+      } else {
+        k_vcycle_small<T, KIND, DIM><<<1, SMALL_TPB, 0, s>>>(S, P, st->prm.nu1, st->prm.nu2, st->prm.ncoarse);
+      }
       FM_LAUNCHED();
       return FM_OK;
     }
@@ -1378,6 +1585,8 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
   {
     const char* eg = getenv("FM_GRAPH");
     st->use_graph = !(eg && eg[0] == '0');
+    const char* ef = getenv("FM_FUSED_RB");
+    st->fused_rb = !(ef && ef[0] == '0');
   }
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);

@@ -60,6 +60,7 @@ struct fm_state {
   cudaStream_t cap[2];            // private streams used to capture the step graph
   bool capturing;
   bool use_graph;                 // run fm_step as one CUDA graph launch
+  bool fused_rb;                  // 2-D: one tiled launch per red-black sweep
   int small_from;                 // first level handled by the single-block V-cycle
   void* ctl;                      // device control block of the step
   cudaGraph_t graph;
