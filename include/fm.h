@@ -179,6 +179,39 @@ int fm_prolong_add(fm_state* st, const double* coarse, double* fine, int where);
 /* Number of multigrid levels of the state. */
 int fm_levels(const fm_state* st);
 
+/* ---- Batched ensembles (2-D) ---- */
+
+/* A set of independent 2-D instances (uneven grid sizes allowed) stepped
+ * together: every stage of the step -- including each multigrid level of the
+ * V-cycle -- is one kernel launch over all instances, and the whole step is
+ * one CUDA graph whose WHILE loop runs until every instance has converged
+ * (each instance stops iterating at its own convergence).  Same scheme and
+ * solver as fm_step, per instance. */
+typedef struct fm_batch fm_batch;
+
+/* count instances with grids[0..count-1] (all dim = 2), shared parameters
+ * and functional.  FM_EINVAL for 3-D grids or invalid sizes. */
+int fm_create_batch(int count, const fm_grid* grids, const fm_params* prm,
+                    const fm_functional* fn, fm_batch** out);
+
+/* Free the batch and all its instances (null accepted). */
+void fm_destroy_batch(fm_batch* b);
+
+/* Issue all further work on `stream`. */
+int fm_batch_set_stream(fm_batch* b, void* stream);
+
+/* Instance i as an fm_state, owned by the batch: use fm_set_fields,
+ * fm_get_fields, fm_energy, fm_mass on it (not fm_destroy). */
+fm_state* fm_batch_instance(fm_batch* b, int i);
+
+/* One time step of every instance, instance i with step dt[i] > 0; info
+ * (nullable) receives count records.  Returns the first non-zero instance
+ * status (instances that failed are left at their time level k). */
+int fm_step_batch(fm_batch* b, const double* dt, fm_step_info* info);
+
+/* Kernels launched by the batch since creation. */
+long long fm_batch_launches(const fm_batch* b);
+
 /* ---- Measurement (no counterpart in the paper). ---- */
 
 /* Enable (1) or disable (0) CUDA-event timing of every finest-level smoother

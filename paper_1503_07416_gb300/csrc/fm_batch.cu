@@ -1,0 +1,762 @@
+// Batched ensembles: many independent 2-D instances of uneven grid sizes and
+// per-instance time steps advance together.  Every stage of the step is one
+// launch over all instances (one launch per multigrid level for the level
+// work): each launch carries a static work list of (instance, first block)
+// items, a block finds its instance by binary search, reads that instance's
+// level descriptor, and returns at once if the instance has already
+// converged.  The whole step is one CUDA graph with a WHILE node whose
+// condition is "some instance is still iterating"; time steps are read from a
+// device array, so the graph does not depend on them.
+//
+// Each instance is a full fm_state (its own arena, hierarchy and, for CDFT,
+// kernel transform), so fields, energy and mass are read per instance with
+// the single-instance entry points.
+#include <cuda_runtime.h>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fm_state.h"
+#include "fm_device.cuh"
+
+namespace fm {
+
+struct WorkItem {
+  int inst;
+  int blk0;
+  int aux;   // tiles per row (tile kernels)
+  int pad;
+};
+
+struct WList {
+  int off;      // first item in the item array
+  int n;        // items
+  int nblocks;  // total blocks
+};
+
+template <typename T>
+struct InstDev {
+  Lvl<T> lv[MAXLEV];
+  SmallLv<T> S;
+  SmallSmem<T> M;
+  InjAll<T> inj_rk;
+  InjAll<T> inj_cf;
+  Fields64 F;
+  Resid64Out O;
+  Vel3W velw;
+  Vel3 gvel;
+  Geo g0;
+  double h0;
+  double* partials;
+  double* tmp;
+  double* rho;
+  int nblk64;
+  int small_from;
+  int nlev;
+  int pad;
+};
+
+__device__ __forceinline__ int find_item(const WorkItem* it, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (it[mid].blk0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool inst_active(const Ctl* ctl, int inst) { return ctl[inst].pad[0] != 0; }
+
+// Cooperative copy of a POD struct into shared memory.
+template <typename S>
+__device__ __forceinline__ void smem_copy(S* dst, const S* src) {
+  const int* a = reinterpret_cast<const int*>(src);
+  int* b = reinterpret_cast<int*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(S) / sizeof(int)); i += blockDim.x) b[i] = a[i];
+}
+
+#define FM_BATCH_HEAD()                                          \
+  const int k_ = find_item(items, nitems, blockIdx.x);           \
+  const int inst = items[k_].inst;                               \
+  const int lb = blockIdx.x - items[k_].blk0;                    \
+  (void)lb
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(RB_THREADS) kb_smooth_rb2d(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                             const Phys<T>* P, const Ctl* ctl, int level) {
+  FM_BATCH_HEAD();
+  if (!inst_active(ctl, inst)) return;
+  __shared__ Lvl<T> G;
+  smem_copy(&G, &D[inst].lv[level]);
+  __syncthreads();
+  const int ntx = items[k_].aux;
+  rb2d_tile<T, KIND>(G, P[inst], lb % ntx, lb / ntx);
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(TPB) kb_resid(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                const Phys<T>* P, const Ctl* ctl, int level) {
+  FM_BATCH_HEAD();
+  if (!inst_active(ctl, inst)) return;
+  __shared__ Lvl<T> L;
+  smem_copy(&L, &D[inst].lv[level]);
+  __syncthreads();
+  const int idx = lb * TPB + threadIdx.x;
+  if (idx < L.g.N) resid_point<T, KIND, 2>(L, P[inst], idx);
+}
+
+template <typename T, int NU>
+__global__ void __launch_bounds__(TPB) kb_restrict(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                   const Ctl* ctl, int level) {
+  FM_BATCH_HEAD();
+  if (!inst_active(ctl, inst)) return;
+  __shared__ Lvl<T> F, Cc;
+  smem_copy(&F, &D[inst].lv[level]);
+  smem_copy(&Cc, &D[inst].lv[level + 1]);
+  __syncthreads();
+  const int idx = lb * TPB + threadIdx.x;
+  if (idx < Cc.g.N) restrict_point<T, NU, 2>(F, Cc, idx);
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(TPB) kb_coarse_rhs(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                     const Phys<T>* P, const Ctl* ctl, int level) {
+  FM_BATCH_HEAD();
+  if (!inst_active(ctl, inst)) return;
+  __shared__ Lvl<T> L;
+  smem_copy(&L, &D[inst].lv[level]);
+  __syncthreads();
+  const int idx = lb * TPB + threadIdx.x;
+  if (idx < L.g.N) coarse_rhs_point<T, KIND, 2>(L, P[inst], idx);
+}
+
+template <typename T, int NU>
+__global__ void __launch_bounds__(TPB) kb_prolong(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                  const Ctl* ctl, int level) {
+  FM_BATCH_HEAD();
+  if (!inst_active(ctl, inst)) return;
+  __shared__ Lvl<T> F, Cc;
+  smem_copy(&F, &D[inst].lv[level]);
+  smem_copy(&Cc, &D[inst].lv[level + 1]);
+  __syncthreads();
+  const int idx = lb * TPB + threadIdx.x;
+  if (idx < F.g.N) prolong_point<T, NU, 2>(F, Cc, idx);
+}
+
+// one block per instance
+template <typename T, int KIND>
+__global__ void __launch_bounds__(SMALL_TPB) kb_small(const InstDev<T>* D, const Phys<T>* P, const Ctl* ctl,
+                                                      int nu1, int nu2, int ncoarse) {
+  const int inst = blockIdx.x;
+  if (!inst_active(ctl, inst)) return;
+  vcycle_small_smem_body<T, KIND, 2>(D[inst].S, D[inst].M, P[inst], nu1, nu2, ncoarse);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) kb_inject(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                 const Ctl* ctl, int coefficients, int check_active) {
+  FM_BATCH_HEAD();
+  if (check_active && !inst_active(ctl, inst)) return;
+  const InjAll<T>& A = coefficients ? D[inst].inj_cf : D[inst].inj_rk;
+  inject_all_point<T>(A, lb * TPB + threadIdx.x);
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(TPB) kb_prepare(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                  const Phys<double>* P64) {
+  FM_BATCH_HEAD();
+  prepare_point<KIND, 2>(D[inst].F, D[inst].g0, D[inst].h0, P64[inst], lb * TPB + threadIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) kb_prepare_mu(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                     const Phys<double>* P64) {
+  FM_BATCH_HEAD();
+  prepare_mu_point<2>(D[inst].F, D[inst].g0, D[inst].h0, P64[inst], lb * TPB + threadIdx.x);
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(TPB) kb_resid64(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                  const Phys<double>* P64, const Ctl* ctl, int check_active) {
+  FM_BATCH_HEAD();
+  if (check_active && !inst_active(ctl, inst)) return;
+  const InstDev<T>& I = D[inst];
+  resid64_body<KIND, 2, T>(I.F, I.O, I.g0, I.h0, P64[inst], I.partials, lb, I.nblk64);
+}
+
+// one block per instance: norm, cycles, status, active flag
+template <typename T, int NQ>
+__global__ void kb_norm(const InstDev<T>* D, Ctl* ctl, double tol, int max_cycles, int in_body) {
+  const int inst = blockIdx.x;
+  if (in_body && !inst_active(ctl, inst)) return;
+  const InstDev<T>& I = D[inst];
+  const double w = I.h0 * I.h0;
+  const bool cont = norm_ctl_body<NQ>(I.partials, I.nblk64, w, &ctl[inst], tol, max_cycles, in_body);
+  if (threadIdx.x == 0) ctl[inst].pad[0] = cont ? 1 : 0;
+}
+
+__global__ void kb_condition(const Ctl* ctl, int count, cudaGraphConditionalHandle handle) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x)
+    if (ctl[i].pad[0]) atomicOr(&any, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
+}
+
+template <typename T, int NU>
+__global__ void __launch_bounds__(TPB) kb_update64(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                   const Ctl* ctl, double delta) {
+  FM_BATCH_HEAD();
+  if (!inst_active(ctl, inst)) return;
+  const InstDev<T>& I = D[inst];
+  update64_point<NU, T>(I.F, I.O, I.g0.N, delta, lb * TPB + threadIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) kb_closure(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                  const Phys<double>* P64, const Ctl* ctl) {
+  FM_BATCH_HEAD();
+  if (ctl[inst].status != FM_OK) return;
+  const InstDev<T>& I = D[inst];
+  closure_point<2>(I.F, I.g0, I.h0, P64[inst], I.tmp, lb * TPB + threadIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) kb_commit(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                 const Ctl* ctl) {
+  FM_BATCH_HEAD();
+  if (ctl[inst].status != FM_OK) return;
+  const InstDev<T>& I = D[inst];
+  commit_point<2>(I.rho, I.velw, I.tmp, I.gvel, I.g0.N, lb * TPB + threadIdx.x);
+}
+
+}  // namespace fm
+
+using namespace fm;
+
+struct fm_batch {
+  int count;
+  int kind;
+  fm_params prm;
+  fm_functional fn;
+  fm_state** inst;
+  int maxdepth;              // max over instances of small_from (levels handled level by level)
+  size_t small_smem;         // dynamic shared memory of the small-level kernel
+  // device tables
+  void* dev;                 // one allocation: descriptors, phys, ctl, work items
+  void* D;                   // InstDev<T>[count]
+  void* P;                   // Phys<T>[count]
+  Phys<double>* P64;
+  Ctl* ctl;
+  WorkItem* items;
+  // host staging (pinned)
+  void* hP;
+  Phys<double>* hP64;
+  Ctl* hctl;
+  // work lists
+  std::vector<WorkItem> hitems;
+  WList w_fine, w_resid64, w_inject;
+  WList w_smooth[MAXLEV], w_resid[MAXLEV], w_restrict[MAXLEV], w_crhs[MAXLEV], w_prolong[MAXLEV];
+  // graph
+  cudaStream_t stream;
+  cudaStream_t user_stream;
+  cudaStream_t cap[2];
+  cudaGraph_t graph;
+  cudaGraphExec_t gexec;
+  long long cnt_pre, cnt_body, cnt_post, launches;
+};
+
+namespace fm {
+
+#define FMB_CUDA(call)                         \
+  do {                                         \
+    if ((call) != cudaSuccess) {               \
+      cudaGetLastError();                      \
+      return FM_ECUDA;                         \
+    }                                          \
+  } while (0)
+
+#define FMB_LAUNCHED()                         \
+  do {                                         \
+    ++b->launches;                             \
+    if (cudaPeekAtLastError() != cudaSuccess) { \
+      cudaGetLastError();                      \
+      return FM_ECUDA;                         \
+    }                                          \
+  } while (0)
+
+static WList add_list(fm_batch* b, const std::vector<std::pair<int, int>>& inst_blocks,
+                      const std::vector<int>* aux = nullptr) {
+  WList w;
+  w.off = (int)b->hitems.size();
+  w.n = 0;
+  w.nblocks = 0;
+  for (size_t i = 0; i < inst_blocks.size(); ++i) {
+    if (inst_blocks[i].second <= 0) continue;
+    WorkItem it;
+    it.inst = inst_blocks[i].first;
+    it.blk0 = w.nblocks;
+    it.aux = aux ? (*aux)[i] : 0;
+    it.pad = 0;
+    b->hitems.push_back(it);
+    w.nblocks += inst_blocks[i].second;
+    ++w.n;
+  }
+  return w;
+}
+
+template <typename T, int KIND>
+struct Batch {
+  using LY = Layout<KIND, 2>;
+
+  static void build_desc(fm_batch* b, std::vector<InstDev<T>>& H) {
+    for (int i = 0; i < b->count; ++i) {
+      fm_state* st = b->inst[i];
+      InstDev<T>& I = H[i];
+      memset(&I, 0, sizeof(I));
+      for (int l = 0; l < st->nlev; ++l) I.lv[l] = make_lvl<T>(st, l);
+      I.nlev = st->nlev;
+      I.small_from = st->small_from;
+      // small levels and their shared-memory layout
+      I.S.count = st->nlev - st->small_from;
+      int off = 0;
+      for (int q = 0; q < I.S.count; ++q) {
+        I.S.lv[q] = make_lvl<T>(st, st->small_from + q);
+        const int N = I.S.lv[q].g.N;
+        for (int u = 0; u < LY::NU; ++u) {
+          I.M.off_e[q][u] = off; off += N;
+          I.M.off_f[q][u] = off; off += N;
+          if (q + 1 < I.S.count) { I.M.off_r[q][u] = off; off += N; }
+          if (q > 0) { I.M.off_eh[q][u] = off; off += N; }
+        }
+      }
+      const size_t sm = (size_t)off * sizeof(T);
+      if (sm > b->small_smem) b->small_smem = sm;
+      // injections (all coarse levels at once)
+      for (int which = 0; which < 2; ++which) {
+        InjAll<T>& A = which ? I.inj_cf : I.inj_rk;
+        A.nl = st->nlev;
+        A.g0 = st->lv[0].g;
+        A.off[0] = A.off[1] = 0;
+        for (int l = 1; l < st->nlev; ++l) {
+          A.g[l] = st->lv[l].g;
+          A.off[l + 1] = A.off[l] + st->lv[l].g.N;
+        }
+        int q = 0;
+        if (which) {
+          A.src[q] = (const T*)st->lv[0].cr;
+          for (int l = 1; l < st->nlev; ++l) A.dst[l][q] = (T*)st->lv[l].cr;
+          ++q;
+          for (int d = 0; d < 2; ++d, ++q) {
+            A.src[q] = (const T*)st->lv[0].cv[d];
+            for (int l = 1; l < st->nlev; ++l) A.dst[l][q] = (T*)st->lv[l].cv[d];
+          }
+        } else {
+          A.src[q] = (const T*)st->lv[0].rk;
+          for (int l = 1; l < st->nlev; ++l) A.dst[l][q] = (T*)st->lv[l].rk;
+          ++q;
+          A.src[q] = (const T*)st->lv[0].om[0];
+          for (int l = 1; l < st->nlev; ++l) A.dst[l][q] = (T*)st->lv[l].om[0];
+          ++q;
+        }
+        A.nsrc = q;
+      }
+      I.F = make_fields(st);
+      for (int q = 0; q < MAXU; ++q) {
+        I.O.f0[q] = q < LY::NU ? st->lv[0].f[q] : nullptr;
+        I.O.e0[q] = q < LY::NU ? st->lv[0].e[q] : nullptr;
+        I.O.r64[q] = nullptr;
+      }
+      I.O.cr32 = nullptr;
+      for (int d = 0; d < 3; ++d) I.O.cv32[d] = nullptr;
+      if (b->prm.precision == FM_MIXED) {
+        I.O.cr32 = (float*)st->lv[0].cr;
+        for (int d = 0; d < 2; ++d) I.O.cv32[d] = (float*)st->lv[0].cv[d];
+      }
+      I.velw = Vel3W{{st->vel[0], st->vel[1], nullptr}};
+      I.gvel = Vel3{{st->g[1], st->g[2], nullptr}};
+      I.g0 = st->lv[0].g;
+      I.h0 = st->lv[0].h;
+      I.partials = st->partials;
+      I.tmp = st->tmp;
+      I.rho = st->rho;
+      I.nblk64 = st->nblk;
+    }
+  }
+
+  static void build_lists(fm_batch* b) {
+    std::vector<std::pair<int, int>> v;
+    b->maxdepth = 0;
+    for (int i = 0; i < b->count; ++i)
+      if (b->inst[i]->small_from > b->maxdepth) b->maxdepth = b->inst[i]->small_from;
+    // finest points, float64 residual blocks, coarse injection points
+    v.clear();
+    for (int i = 0; i < b->count; ++i) v.push_back({i, nblocks(b->inst[i]->lv[0].g.N)});
+    b->w_fine = add_list(b, v);
+    v.clear();
+    for (int i = 0; i < b->count; ++i) v.push_back({i, b->inst[i]->nblk});
+    b->w_resid64 = add_list(b, v);
+    v.clear();
+    for (int i = 0; i < b->count; ++i) {
+      long long n = 0;
+      for (int l = 1; l < b->inst[i]->nlev; ++l) n += b->inst[i]->lv[l].g.N;
+      v.push_back({i, nblocks(n)});
+    }
+    b->w_inject = add_list(b, v);
+    for (int l = 0; l < b->maxdepth; ++l) {
+      std::vector<std::pair<int, int>> ts, rs, rr, cr, pr;
+      std::vector<int> aux;
+      for (int i = 0; i < b->count; ++i) {
+        fm_state* st = b->inst[i];
+        if (st->small_from <= l) continue;
+        const Geo g = st->lv[l].g, gc = st->lv[l + 1].g;
+        const int ntx = (g.nx + RB_TX - 1) / RB_TX, nty = (g.ny + RB_TY - 1) / RB_TY;
+        ts.push_back({i, ntx * nty});
+        aux.push_back(ntx);
+        rs.push_back({i, nblocks(g.N)});
+        rr.push_back({i, nblocks(gc.N)});
+        cr.push_back({i, nblocks(gc.N)});
+        pr.push_back({i, nblocks(g.N)});
+      }
+      b->w_smooth[l] = add_list(b, ts, &aux);
+      b->w_resid[l] = add_list(b, rs);
+      b->w_restrict[l] = add_list(b, rr);
+      b->w_crhs[l] = add_list(b, cr);
+      b->w_prolong[l] = add_list(b, pr);
+    }
+  }
+
+  static const WorkItem* it(fm_batch* b, const WList& w) { return b->items + w.off; }
+
+  static int smooth(fm_batch* b, int l, int iters) {
+    const WList& w = b->w_smooth[l];
+    if (w.n == 0) return FM_OK;
+    const size_t smem = (size_t)rb_arrays<KIND>() * RB_SN * sizeof(T);
+    for (int k = 0; k < iters; ++k) {
+      kb_smooth_rb2d<T, KIND><<<w.nblocks, RB_THREADS, smem, b->stream>>>(
+          it(b, w), w.n, (const InstDev<T>*)b->D, (const Phys<T>*)b->P, b->ctl, l);
+      FMB_LAUNCHED();
+    }
+    return FM_OK;
+  }
+
+  static int vcycle(fm_batch* b) {
+    const InstDev<T>* D = (const InstDev<T>*)b->D;
+    const Phys<T>* P = (const Phys<T>*)b->P;
+    cudaStream_t s = b->stream;
+    for (int l = 0; l < b->maxdepth; ++l) {
+      int rc = smooth(b, l, b->prm.nu1);
+      if (rc) return rc;
+      const WList &wr = b->w_resid[l], &wq = b->w_restrict[l], &wc = b->w_crhs[l];
+      if (wr.n == 0) continue;
+      kb_resid<T, KIND><<<wr.nblocks, TPB, 0, s>>>(it(b, wr), wr.n, D, P, b->ctl, l);
+      FMB_LAUNCHED();
+      kb_restrict<T, LY::NU><<<wq.nblocks, TPB, 0, s>>>(it(b, wq), wq.n, D, b->ctl, l);
+      FMB_LAUNCHED();
+      kb_coarse_rhs<T, KIND><<<wc.nblocks, TPB, 0, s>>>(it(b, wc), wc.n, D, P, b->ctl, l + 1);
+      FMB_LAUNCHED();
+    }
+    kb_small<T, KIND><<<b->count, SMALL_TPB, b->small_smem, s>>>(D, P, b->ctl, b->prm.nu1, b->prm.nu2,
+                                                                  b->prm.ncoarse);
+    FMB_LAUNCHED();
+    for (int l = b->maxdepth - 1; l >= 0; --l) {
+      const WList& wp = b->w_prolong[l];
+      if (wp.n == 0) continue;
+      kb_prolong<T, LY::NU><<<wp.nblocks, TPB, 0, s>>>(it(b, wp), wp.n, D, b->ctl, l);
+      FMB_LAUNCHED();
+      int rc = smooth(b, l, b->prm.nu2);
+      if (rc) return rc;
+    }
+    return FM_OK;
+  }
+
+  static int resid_norm(fm_batch* b, int in_body, cudaGraphConditionalHandle hdl) {
+    const InstDev<T>* D = (const InstDev<T>*)b->D;
+    const WList& w = b->w_resid64;
+    kb_resid64<T, KIND><<<w.nblocks, TPB, 0, b->stream>>>(it(b, w), w.n, D, b->P64, b->ctl, in_body);
+    FMB_LAUNCHED();
+    kb_norm<T, LY::NU><<<b->count, TPB, 0, b->stream>>>(D, b->ctl, b->prm.tol, b->prm.max_cycles, in_body);
+    FMB_LAUNCHED();
+    kb_condition<<<1, 256, 0, b->stream>>>(b->ctl, b->count, hdl);
+    FMB_LAUNCHED();
+    return FM_OK;
+  }
+
+  static int pre(fm_batch* b, cudaGraphConditionalHandle hdl) {
+    const InstDev<T>* D = (const InstDev<T>*)b->D;
+    cudaStream_t s = b->stream;
+    if (KIND == KCDFT) {
+      for (int i = 0; i < b->count; ++i) {
+        fm_state* st = b->inst[i];
+        st->stream = s;
+        const long long l0 = st->launches;
+        const int rc = fft_convolve(st, st->rho, st->conv);
+        b->launches += st->launches - l0;
+        st->stream = b->user_stream;
+        if (rc) return rc;
+      }
+    }
+    const WList& w = b->w_fine;
+    kb_prepare<T, KIND><<<w.nblocks, TPB, 0, s>>>(it(b, w), w.n, D, b->P64);
+    FMB_LAUNCHED();
+    if (KIND == KPFC) {
+      kb_prepare_mu<T><<<w.nblocks, TPB, 0, s>>>(it(b, w), w.n, D, b->P64);
+      FMB_LAUNCHED();
+    }
+    const WList& wi = b->w_inject;
+    if (wi.n) {
+      kb_inject<T><<<wi.nblocks, TPB, 0, s>>>(it(b, wi), wi.n, D, b->ctl, 0, 0);
+      FMB_LAUNCHED();
+    }
+    return resid_norm(b, 0, hdl);
+  }
+
+  static int body(fm_batch* b, cudaGraphConditionalHandle hdl) {
+    const InstDev<T>* D = (const InstDev<T>*)b->D;
+    const WList& wi = b->w_inject;
+    if (wi.n) {
+      kb_inject<T><<<wi.nblocks, TPB, 0, b->stream>>>(it(b, wi), wi.n, D, b->ctl, 1, 1);
+      FMB_LAUNCHED();
+    }
+    int rc = vcycle(b);
+    if (rc) return rc;
+    const WList& w = b->w_fine;
+    kb_update64<T, LY::NU><<<w.nblocks, TPB, 0, b->stream>>>(it(b, w), w.n, D, b->ctl, b->prm.delta);
+    FMB_LAUNCHED();
+    return resid_norm(b, 1, hdl);
+  }
+
+  static int post(fm_batch* b) {
+    const InstDev<T>* D = (const InstDev<T>*)b->D;
+    const WList& w = b->w_fine;
+    kb_closure<T><<<w.nblocks, TPB, 0, b->stream>>>(it(b, w), w.n, D, b->P64, b->ctl);
+    FMB_LAUNCHED();
+    kb_commit<T><<<w.nblocks, TPB, 0, b->stream>>>(it(b, w), w.n, D, b->ctl);
+    FMB_LAUNCHED();
+    FMB_CUDA(cudaMemcpyAsync(b->hctl, b->ctl, sizeof(Ctl) * b->count, cudaMemcpyDeviceToHost, b->stream));
+    return FM_OK;
+  }
+
+  static int build_graph(fm_batch* b) {
+    cudaStream_t saved = b->stream;
+    cudaStream_t s0 = b->cap[0], s1 = b->cap[1];
+    b->stream = s0;
+    int rc = FM_OK;
+    cudaGraph_t g = nullptr;
+    const long long l0 = b->launches;
+    do {
+      if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = FM_ECUDA; break; }
+      cudaStreamCaptureStatus cs;
+      cudaGraph_t cg = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      if (cudaStreamGetCaptureInfo(s0, &cs, nullptr, &cg, nullptr, nullptr, nullptr) != cudaSuccess) { rc = FM_ECUDA; break; }
+      cudaGraphConditionalHandle hdl;
+      if (cudaGraphConditionalHandleCreate(&hdl, cg, 0, cudaGraphCondAssignDefault) != cudaSuccess) { rc = FM_ECUDA; break; }
+      rc = pre(b, hdl);
+      if (rc) break;
+      b->cnt_pre = b->launches - l0;
+      if (cudaStreamGetCaptureInfo(s0, &cs, nullptr, &cg, &deps, nullptr, &nd) != cudaSuccess) { rc = FM_ECUDA; break; }
+      cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+      cp.conditional.handle = hdl;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t wnode;
+      if (cudaGraphAddNode(&wnode, cg, deps, nullptr, nd, &cp) != cudaSuccess) { rc = FM_ECUDA; break; }
+      cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+      if (cudaStreamUpdateCaptureDependencies(s0, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess) { rc = FM_ECUDA; break; }
+      b->stream = s1;
+      if (cudaStreamBeginCaptureToGraph(s1, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = FM_ECUDA; break; }
+      const long long l1 = b->launches;
+      rc = body(b, hdl);
+      b->cnt_body = b->launches - l1;
+      cudaGraph_t bo = nullptr;
+      if (cudaStreamEndCapture(s1, &bo) != cudaSuccess && rc == FM_OK) rc = FM_ECUDA;
+      if (rc) break;
+      b->stream = s0;
+      const long long l2 = b->launches;
+      rc = post(b);
+      b->cnt_post = b->launches - l2;
+    } while (0);
+    b->stream = s0;
+    if (cudaStreamEndCapture(s0, &g) != cudaSuccess && rc == FM_OK) rc = FM_ECUDA;
+    b->stream = saved;
+    b->launches = l0;
+    if (rc) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (cudaGraphInstantiate(&b->gexec, g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphDestroy(g);
+      return FM_ECUDA;
+    }
+    b->graph = g;
+    return FM_OK;
+  }
+
+  static int setup(fm_batch* b) {
+    std::vector<InstDev<T>> H(b->count);
+    b->small_smem = 0;
+    build_desc(b, H);
+    build_lists(b);
+    const size_t szD = sizeof(InstDev<T>) * b->count;
+    const size_t szP = sizeof(Phys<T>) * b->count;
+    const size_t szP64 = sizeof(Phys<double>) * b->count;
+    const size_t szC = sizeof(Ctl) * b->count;
+    const size_t szI = sizeof(WorkItem) * (b->hitems.size() + 1);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t total = al(szD) + al(szP) + al(szP64) + al(szC) + al(szI);
+    FMB_CUDA(cudaMalloc(&b->dev, total));
+    char* p = (char*)b->dev;
+    b->D = p; p += al(szD);
+    b->P = p; p += al(szP);
+    b->P64 = (Phys<double>*)p; p += al(szP64);
+    b->ctl = (Ctl*)p; p += al(szC);
+    b->items = (WorkItem*)p;
+    FMB_CUDA(cudaMemcpy(b->D, H.data(), szD, cudaMemcpyHostToDevice));
+    if (!b->hitems.empty())
+      FMB_CUDA(cudaMemcpy(b->items, b->hitems.data(), sizeof(WorkItem) * b->hitems.size(), cudaMemcpyHostToDevice));
+    FMB_CUDA(cudaMemset(b->ctl, 0, szC));
+    FMB_CUDA(cudaMallocHost(&b->hP, szP));
+    FMB_CUDA(cudaMallocHost((void**)&b->hP64, szP64));
+    FMB_CUDA(cudaMallocHost((void**)&b->hctl, szC));
+    if (b->small_smem > (size_t)SMALL_SMEM_MAX) return FM_EINVAL;
+    FMB_CUDA(cudaFuncSetAttribute(kb_small<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SMALL_SMEM_MAX));
+    FMB_CUDA(cudaFuncSetAttribute(kb_smooth_rb2d<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(rb_arrays<KIND>() * RB_SN * sizeof(T))));
+    return FM_OK;
+  }
+
+  static int step(fm_batch* b, const double* dt) {
+    Phys<T>* hp = (Phys<T>*)b->hP;
+    for (int i = 0; i < b->count; ++i) {
+      b->inst[i]->dt = dt[i];
+      hp[i] = make_phys<T>(b->inst[i]);
+      b->hP64[i] = make_phys<double>(b->inst[i]);
+    }
+    FMB_CUDA(cudaMemcpyAsync(b->P, hp, sizeof(Phys<T>) * b->count, cudaMemcpyHostToDevice, b->stream));
+    FMB_CUDA(cudaMemcpyAsync(b->P64, b->hP64, sizeof(Phys<double>) * b->count, cudaMemcpyHostToDevice, b->stream));
+    if (!b->gexec) {
+      const int rc = build_graph(b);
+      if (rc) return rc;
+    }
+    FMB_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+    FMB_CUDA(cudaStreamSynchronize(b->stream));
+    long long maxc = 0;
+    for (int i = 0; i < b->count; ++i)
+      if (b->hctl[i].cycles > maxc) maxc = b->hctl[i].cycles;
+    b->launches += b->cnt_pre + maxc * b->cnt_body + b->cnt_post;
+    return FM_OK;
+  }
+};
+
+template <typename T>
+static int batch_dispatch_setup(fm_batch* b) {
+  return b->kind == FM_PFC ? Batch<T, KPFC>::setup(b) : Batch<T, KCDFT>::setup(b);
+}
+template <typename T>
+static int batch_dispatch_step(fm_batch* b, const double* dt) {
+  return b->kind == FM_PFC ? Batch<T, KPFC>::step(b, dt) : Batch<T, KCDFT>::step(b, dt);
+}
+
+}  // namespace fm
+
+extern "C" {
+
+void fm_destroy_batch(fm_batch* b) {
+  if (!b) return;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (int i = 0; i < 2; ++i)
+    if (b->cap[i]) cudaStreamDestroy(b->cap[i]);
+  if (b->dev) cudaFree(b->dev);
+  if (b->hP) cudaFreeHost(b->hP);
+  if (b->hP64) cudaFreeHost(b->hP64);
+  if (b->hctl) cudaFreeHost(b->hctl);
+  if (b->inst) {
+    for (int i = 0; i < b->count; ++i) fm_destroy(b->inst[i]);
+    delete[] b->inst;
+  }
+  delete b;
+}
+
+int fm_create_batch(int count, const fm_grid* grids, const fm_params* prm, const fm_functional* fn,
+                    fm_batch** out) {
+  if (!out || !grids || !prm || !fn || count < 1 || count > 4096) return FM_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i)
+    if (grids[i].dim != 2) return FM_EINVAL;  // batched ensembles are 2-D
+  fm_batch* b = new (std::nothrow) fm_batch();
+  if (!b) return FM_ENOMEM;
+  b->count = count;
+  b->kind = fn->kind;
+  b->prm = *prm;
+  b->fn = *fn;
+  b->stream = 0;
+  b->inst = new (std::nothrow) fm_state*[count]();
+  if (!b->inst) {
+    delete b;
+    return FM_ENOMEM;
+  }
+  for (int i = 0; i < count; ++i) {
+    const int rc = fm_create(&grids[i], prm, fn, &b->inst[i]);
+    if (rc) {
+      fm_destroy_batch(b);
+      return rc;
+    }
+  }
+  if (cudaStreamCreateWithFlags(&b->cap[0], cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap[1], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    fm_destroy_batch(b);
+    return FM_ECUDA;
+  }
+  const int rc = prm->precision == FM_MIXED ? batch_dispatch_setup<float>(b) : batch_dispatch_setup<double>(b);
+  if (rc) {
+    fm_destroy_batch(b);
+    return rc;
+  }
+  *out = b;
+  return FM_OK;
+}
+
+int fm_batch_set_stream(fm_batch* b, void* stream) {
+  if (!b) return FM_EINVAL;
+  b->stream = (cudaStream_t)stream;
+  b->user_stream = (cudaStream_t)stream;
+  for (int i = 0; i < b->count; ++i) fm_set_stream(b->inst[i], stream);
+  return FM_OK;
+}
+
+fm_state* fm_batch_instance(fm_batch* b, int i) {
+  if (!b || i < 0 || i >= b->count) return nullptr;
+  return b->inst[i];
+}
+
+int fm_step_batch(fm_batch* b, const double* dt, fm_step_info* info) {
+  if (!b || !dt) return FM_EINVAL;
+  for (int i = 0; i < b->count; ++i)
+    if (!(dt[i] > 0.0)) return FM_EINVAL;
+  const int rc = b->prm.precision == FM_MIXED ? batch_dispatch_step<float>(b, dt) : batch_dispatch_step<double>(b, dt);
+  if (rc) return rc;
+  int status = FM_OK;
+  for (int i = 0; i < b->count; ++i) {
+    if (info) {
+      info[i].cycles = b->hctl[i].cycles;
+      info[i].res0 = b->hctl[i].norm0;
+      info[i].res = b->hctl[i].norm;
+    }
+    if (b->hctl[i].status != FM_OK && status == FM_OK) status = b->hctl[i].status;
+  }
+  return status;
+}
+
+long long fm_batch_launches(const fm_batch* b) { return b ? b->launches : -1; }
+
+}  // extern "C"

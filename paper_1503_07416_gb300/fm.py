@@ -82,6 +82,13 @@ _SIGS = {
     "fm_restrict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "fm_prolong_add": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "fm_levels": (C.c_int, [C.c_void_p]),
+    "fm_create_batch": (C.c_int, [C.c_int, C.POINTER(fm_grid), C.POINTER(fm_params), C.POINTER(fm_functional),
+                                  C.POINTER(C.c_void_p)]),
+    "fm_destroy_batch": (None, [C.c_void_p]),
+    "fm_batch_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fm_batch_instance": (C.c_void_p, [C.c_void_p, C.c_int]),
+    "fm_step_batch": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(fm_step_info)]),
+    "fm_batch_launches": (C.c_longlong, [C.c_void_p]),
     "fm_mass_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_double, C.c_void_p,
                                   C.c_void_p]),
     "fm_profile": (C.c_int, [C.c_void_p, C.c_int]),
@@ -233,6 +240,37 @@ def fm_levels(st):
     return lib().fm_levels(st)
 
 
+def fm_create_batch(grids, prm: fm_params, fn: fm_functional):
+    arr = (fm_grid * len(grids))(*grids)
+    h = C.c_void_p()
+    _check(lib().fm_create_batch(len(grids), arr, C.byref(prm), C.byref(fn), C.byref(h)), "fm_create_batch")
+    return h
+
+
+def fm_destroy_batch(b):
+    lib().fm_destroy_batch(b)
+
+
+def fm_batch_set_stream(b, stream_handle: int):
+    _check(lib().fm_batch_set_stream(b, C.c_void_p(stream_handle)), "fm_batch_set_stream")
+
+
+def fm_batch_instance(b, i):
+    return C.c_void_p(lib().fm_batch_instance(b, i))
+
+
+def fm_step_batch(b, dts):
+    n = len(dts)
+    arr = (C.c_double * n)(*dts)
+    info = (fm_step_info * n)()
+    code = lib().fm_step_batch(b, arr, info)
+    return code, list(info)
+
+
+def fm_batch_launches(b):
+    return lib().fm_batch_launches(b)
+
+
 def fm_mass_noalloc(rho, h, out, stream=0):
     """Mass of a float64 CUDA tensor into a 1-element float64 CUDA tensor,
     without any device allocation by the library (see include/fm.h)."""
@@ -252,6 +290,60 @@ def fm_profile_read(st):
     ms, n, tot = C.c_double(), C.c_longlong(), C.c_longlong()
     _check(lib().fm_profile_read(st, C.byref(ms), C.byref(n), C.byref(tot)), "fm_profile_read")
     return ms.value, n.value, tot.value
+
+
+class Batch:
+    """Independent 2-D instances stepped together (owns an fm_batch)."""
+
+    def __init__(self, kind, sizes, h, alpha=0.0, nu=0.0, precision=FM_FP64, stream=None, **params):
+        grids = []
+        for n in sizes:
+            g = fm_grid()
+            g.dim = 2
+            ns = list(n) if hasattr(n, "__len__") else [n, n]
+            g.n[0], g.n[1], g.n[2] = ns[0], ns[1], 1
+            g.h = h
+            grids.append(g)
+        f = fm_functional()
+        f.kind = {"pfc": FM_PFC, "cdft": FM_CDFT}.get(kind, kind)
+        f.alpha = alpha
+        f.nu = nu
+        p = fm_default_params()
+        p.precision = precision
+        for k, v in params.items():
+            setattr(p, k, v)
+        self.shapes = [tuple(reversed(list(n) if hasattr(n, "__len__") else [n, n])) for n in sizes]
+        self.handle = fm_create_batch(grids, p, f)
+        if stream is not None:
+            fm_batch_set_stream(self.handle, stream)
+
+    def instance(self, i):
+        return fm_batch_instance(self.handle, i)
+
+    def set_fields(self, i, rho, vel):
+        fm_set_fields(self.instance(i), rho, vel)
+
+    def get_fields(self, i):
+        rho = np.empty(self.shapes[i])
+        vel = [np.empty(self.shapes[i]) for _ in range(2)]
+        fm_get_fields(self.instance(i), rho, vel)
+        return rho, vel
+
+    def step(self, dts):
+        code, info = fm_step_batch(self.handle, dts)
+        _check(code, "fm_step_batch")
+        return info
+
+    def close(self):
+        if self.handle:
+            fm_destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,116 @@
+"""Batched ensembles (fm_create_batch / fm_step_batch) against the oracle and
+against single-instance steps, with uneven grid sizes and per-instance time
+steps.  Tolerances as in test_gpu_parity (float64 1e-10, mixed 1e-8 relative
+per field against the oracle)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import scheme as S
+from paper_1503_07416_gb300 import fm, inputs
+from tests.helpers import gpu_solver, oracle_setup, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_07416_gb300 import build
+    build.build_library()
+    fm.lib()
+
+
+def _ensemble(kind, sizes, seed):
+    rng = np.random.default_rng(seed)
+    states = []
+    for k, n in enumerate(sizes):
+        shape = tuple(reversed(n)) if isinstance(n, tuple) else (n, n)
+        if kind == "pfc":
+            rho = 0.8 + 0.05 * rng.uniform(-1, 1, shape)
+        else:
+            rho = 0.1 * math.pi * (1 + 0.1 * rng.uniform(0, 1, shape))
+        vel = [0.03 * rng.standard_normal(shape) for _ in range(2)]
+        dt = float(math.exp(rng.uniform(math.log(1e-3), math.log(5e-2))))
+        states.append((rho, vel, dt))
+    return states
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_batch_pfc_uneven_sizes(precision):
+    """Six PFC instances of sizes 16^2 .. 128^2 and a ragged 48x40, each with
+    its own dt, two steps; every instance matches the oracle and the
+    single-instance solver."""
+    sizes = [16, 32, (48, 40), 64, 128, 32]
+    ens = _ensemble("pfc", sizes, 5)
+    h, tol = 0.9, 1e-12
+    prm = dict(kind="pfc", dim=2, h=h, alpha=0.6, tol=tol)
+    b = fm.Batch("pfc", sizes, h, alpha=0.6, precision=precision, tol=tol, w_damp=0.0, max_cycles=80)
+    for i, (rho, vel, dt) in enumerate(ens):
+        b.set_fields(i, rho, vel)
+    bound = 1e-10 if precision == fm.FM_FP64 else 1e-8
+    cur = [(r, v) for r, v, _ in ens]
+    for step in range(2):
+        info = b.step([dt for _, _, dt in ens])
+        for i, (rho, vel, dt) in enumerate(ens):
+            assert info[i].res <= tol
+            rg, vg = b.get_fields(i)
+            P, opts, J = oracle_setup(cur[i][0], dict(prm, dt=dt), w_damp=0.0, tol=tol)
+            ro, vo, _ = S.step(cur[i][0], cur[i][1], P, opts, J=J)
+            errs = [rel(rg, ro)] + [rel(a, c) for a, c in zip(vg, vo)]
+            assert max(errs) <= bound, (i, step, errs)
+            # single-instance path from the same state
+            sol = gpu_solver(cur[i][0], dict(prm, dt=dt), precision=precision, w_damp=0.0, tol=tol)
+            sol.set_fields(cur[i][0], cur[i][1])
+            sinfo = sol.step(dt)
+            rs, vs = sol.get_fields()
+            sol.close()
+            assert sinfo.cycles == info[i].cycles
+            assert rel(rg, rs) <= 1e-12 and all(rel(a, c) <= 1e-12 for a, c in zip(vg, vs))
+            cur[i] = (rg, vg)
+    b.close()
+
+
+def test_batch_cdft():
+    """Three CDFT instances (power-of-two sizes) with their own dt."""
+    sizes = [16, 32, 64]
+    ens = _ensemble("cdft", sizes, 7)
+    tol = 1e-12
+    out = []
+    b = fm.Batch("cdft", sizes, 34.0 / 128, nu=2.362, precision=fm.FM_MIXED, tol=tol, w_damp=0.5,
+                 delta=1e-10, max_cycles=80)
+    for i, (rho, vel, dt) in enumerate(ens):
+        b.set_fields(i, rho, vel)
+    info = b.step([dt for _, _, dt in ens])
+    for i, (rho, vel, dt) in enumerate(ens):
+        prm = dict(kind="cdft", dim=2, h=34.0 / 128, nu=2.362, delta=1e-10, dt=dt)
+        P, opts, J = oracle_setup(rho, prm, w_damp=0.5, tol=tol)
+        ro, vo, _ = S.step(rho, vel, P, opts, J=J)
+        rg, vg = b.get_fields(i)
+        errs = [rel(rg, ro)] + [rel(a, c) for a, c in zip(vg, vo)]
+        assert max(errs) <= 1e-8, (i, errs)
+    b.close()
+
+
+def test_batch_failure_is_isolated():
+    """A NaN in one instance makes that instance report FM_ENAN and keep its
+    state; the others advance normally."""
+    sizes = [32, 32, 64]
+    ens = _ensemble("pfc", sizes, 9)
+    b = fm.Batch("pfc", sizes, 0.9, alpha=0.6, precision=fm.FM_MIXED, tol=1e-10, w_damp=0.0)
+    bad = ens[1][0].copy()
+    bad[3, 4] = math.nan
+    for i, (rho, vel, dt) in enumerate(ens):
+        b.set_fields(i, bad if i == 1 else rho, vel)
+    code, info = fm.fm_step_batch(b.handle, [dt for _, _, dt in ens])
+    assert code == fm.FM_ENAN
+    r1, v1 = b.get_fields(1)
+    assert np.isnan(r1[3, 4]) and np.array_equal(v1[0], ens[1][1][0])
+    for i in (0, 2):
+        assert info[i].res <= 1e-10
+        r, _ = b.get_fields(i)
+        assert not np.array_equal(r, ens[i][0])
+    b.close()
