@@ -185,11 +185,13 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
 
     results = {}
+    tuning = {}
     arms = (("mixed", fm.FM_MIXED), ("fp64", fm.FM_FP64))
     if args.only:
         arms = tuple(a for a in arms if a[0] == args.only)
     for name, prec in arms:
         sol = make_solver(fm, rho.shape, prm, prec, stream)
+        tuning[name] = [fm.fm_tuning(sol.handle, l) for l in range(3)]
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -300,6 +302,8 @@ def run_ours(args):
                 "smoother_gbs": round(words * 8 * N / (f64_avg * 1e-3) / 1e9, 1) if f64_sm_n else None,
             },
             "speedup_mixed_over_fp64": round(f64["total_ms"] / mix["total_ms"], 3),
+            "sweep_variants": {k: [{"level": l, "variant": v[0], "ms": [round(x, 4) for x in v[1]]}
+                                   for l, v in enumerate(vals)] for k, vals in tuning.items()},
         },
         "roofline": {
             "kernel": "k_smooth_rb2d<float,PFC> (finest level, one red-black sweep)",
@@ -325,11 +329,132 @@ def run_ours(args):
         "gpu_launches": mix["launches"],
         "clocks": mix["clocks"],
     }
+    if not args.no_secondary:
+        out["secondary"] = secondary_all(torch, fm, inputs, flush, peak)
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def _timed_steps(torch, step_fn, steps, flush):
+    """CUDA-event time (ms) of each call of step_fn, L2 flushed (untimed)
+    before each."""
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    out = []
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        out.append(step_fn())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], out
+
+
+def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2):
+    """48 independent PFC instances (n from {128..1024}, per-instance dt),
+    mixed precision, stepped together (fm_step_batch)."""
+    ens = inputs.batch48()
+    sizes = [prm["n"] for _, _, prm in ens]
+    p0 = ens[0][2]
+    stream = torch.cuda.current_stream().cuda_stream
+    b = fm.Batch("pfc", sizes, p0["h"], alpha=p0["alpha"], precision=fm.FM_MIXED, tol=p0["tol"],
+                 w_damp=0.0, gamma=p0["gamma"], delta=0.0, stream=stream)
+    for i, (rho, vel, _) in enumerate(ens):
+        b.set_fields(i, rho, vel)
+    dts = [prm["dt"] for _, _, prm in ens]
+    for _ in range(warmup):
+        b.step(dts)
+    for i, (rho, vel, _) in enumerate(ens):
+        b.set_fields(i, rho, vel)
+    torch.cuda.synchronize()
+    l0 = fm.fm_batch_launches(b.handle)
+    times, infos = _timed_steps(torch, lambda: b.step(dts), steps, flush)
+    launches = fm.fm_batch_launches(b.handle) - l0
+    ms_sm, pts = fm.fm_batch_time_smoother(b.handle, 20)
+    tune0 = fm.fm_batch_tuning(b.handle, 0)
+    b.close()
+    cyc = [i.cycles for inf in infos for i in inf]
+    total = sum(times)
+    words = 20
+    gbs = words * 4 * pts / (ms_sm * 1e-3) / 1e9
+    return {
+        "workload": "batch48: 48 PFC instances, n in {128,256,512,1024}, dt log-uniform [1e-3,1e-1], "
+                    "eps=0.4, mixed, V(2,2) to 1e-10",
+        "points": int(sum(n * n for n in sizes)),
+        "instance_steps_per_s": round(len(sizes) * steps / (total / 1e3), 2),
+        "batch_steps_per_s": round(steps / (total / 1e3), 3),
+        "ms_per_batch_step": round(total / steps, 3),
+        "cycles_mean": round(sum(cyc) / len(cyc), 3), "cycles_max": max(cyc),
+        "gpu_launches": launches,
+        "smoother_roofline": {"kernel": "kb_smooth_rb2d<float,PFC> (finest level of all instances)",
+                              "bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                              "frac": round(gbs / peak, 4), "launch_ms": round(ms_sm, 5),
+                              "algorithmic_bytes_per_launch": words * 4 * pts,
+                              "timing": "20 back-to-back launches after a warm-up, CUDA events",
+                              "autotuned_variant": tune0[0],
+                              "variant_ms": [round(x, 4) for x in tune0[1]]},
+    }
+
+
+def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, warmup=2, dim=2):
+    n = list(reversed(rho.shape))
+    stream = torch.cuda.current_stream().cuda_stream
+    sol = fm.Solver(kind, n, prm["h"], dim=dim, alpha=prm.get("alpha", 0.0), nu=prm.get("nu", 0.0),
+                    precision=precision, tol=prm["tol"], w_damp=prm.get("w_damp", 0.0),
+                    delta=prm.get("delta", 0.0), gamma=prm["gamma"], stream=stream)
+    rho_d = torch.from_numpy(rho).cuda()
+    vel_d = [torch.from_numpy(v).cuda() for v in vel]
+    sol.set_fields(rho_d, vel_d)
+    for _ in range(warmup):
+        sol.step(prm["dt"])
+    sol.set_fields(rho_d, vel_d)
+    torch.cuda.synchronize()
+    times, infos = _timed_steps(torch, lambda: sol.step(prm["dt"]), steps, flush)
+    sol.close()
+    total = sum(times)
+    return {"steps_per_s": round(steps / (total / 1e3), 3), "ms_per_step": round(total / steps, 4),
+            "cycles_mean": round(sum(i.cycles for i in infos) / len(infos), 3)}
+
+
+def profile_batch(count):
+    """Small ncu target: the first `count` instances of batch48, one step,
+    then 4 timed finest-level batched sweeps."""
+    import torch
+    from paper_1503_07416_gb300 import build, fm, inputs
+    build.build_library()
+    ens = inputs.batch48()[:count]
+    sizes = [prm["n"] for _, _, prm in ens]
+    p0 = ens[0][2]
+    b = fm.Batch("pfc", sizes, p0["h"], alpha=p0["alpha"], precision=fm.FM_MIXED, tol=p0["tol"], w_damp=0.0,
+                 stream=torch.cuda.current_stream().cuda_stream)
+    for i, (rho, vel, _) in enumerate(ens):
+        b.set_fields(i, rho, vel)
+    b.step([prm["dt"] for _, _, prm in ens])
+    ms, pts = fm.fm_batch_time_smoother(b.handle, 4)
+    torch.cuda.synchronize()
+    b.close()
+    print(json.dumps({"profile_batch": count, "points": pts, "ms_per_launch": ms,
+                      "gbs": 80 * pts / (ms * 1e-3) / 1e9}))
+
+
+def secondary_all(torch, fm, inputs, flush, peak):
+    out = {"batch48": secondary_batch48(torch, fm, inputs, flush, peak)}
+    rho, vel, prm = inputs.cdft256()
+    out["cdft256"] = {
+        "workload": "cdft256: 2-D CDFT 256x256, h=17/128, nu=2.362, s=0.02, w_damp 0.5, delta 1e-10",
+        "mixed": secondary_single(torch, fm, flush, "cdft", rho, vel, prm, fm.FM_MIXED, 20),
+        "fp64": secondary_single(torch, fm, flush, "cdft", rho, vel, prm, fm.FM_FP64, 10),
+    }
+    rho, vel, prm = inputs.pfc3d128()
+    out["pfc3d128"] = {
+        "workload": "pfc3d128: 3-D PFC 128^3, eps=0.4, s=0.02, one nucleus, V(2,2) to 1e-10",
+        "mixed": secondary_single(torch, fm, flush, "pfc", rho, vel, prm, fm.FM_MIXED, 5, dim=3),
+        "fp64": secondary_single(torch, fm, flush, "pfc", rho, vel, prm, fm.FM_FP64, 2, warmup=1, dim=3),
+    }
+    return out
 
 
 def oracle_steps(nsteps, budget_s):
@@ -388,10 +513,16 @@ def main():
     ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
                     help="time one arm only and print a short diagnostic line (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="profiling target: first K batch48 instances, timed batched sweeps only")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the batched, CDFT and 3-D workloads measured beside the headline")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile_batch:
+        profile_batch(args.profile_batch)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -212,7 +212,26 @@ int fm_step_batch(fm_batch* b, const double* dt, fm_step_info* info);
 /* Kernels launched by the batch since creation. */
 long long fm_batch_launches(const fm_batch* b);
 
+/* Autotuner choice of the fused-sweep variant for multigrid level `level` of
+ * the batch (same encoding and timings as fm_tuning). */
+int fm_batch_tuning(const fm_batch* b, int level, int* variant, float* ms_per_variant);
+
+/* Measurement (no counterpart in the paper): mean duration (ms, CUDA events)
+ * of one launch of the finest-level fused red-black sweep over all instances,
+ * timed over `iters` back-to-back launches after one warm-up launch, and the
+ * number of finest-level points one launch sweeps.  Overwrites only solver
+ * scratch (the corrections), which the next fm_step_batch resets. */
+int fm_batch_time_smoother(fm_batch* b, int iters, double* ms_per_launch, long long* points);
+
 /* ---- Measurement (no counterpart in the paper). ---- */
+
+/* Variant of the 2-D fused red-black sweep the autotuner chose for `level`
+ * at fm_create (bit 2: 64x8 tiles instead of 32x16; bit 1: right-hand side
+ * staged in shared memory; bit 0: persistent double-buffered blocks), and its
+ * timings of all 8 variants in ms per sweep (ms_per_variant may be null; 0 for
+ * levels that were not tuned).  Setting the environment variable
+ * FM_RB_VARIANT=v before fm_create fixes the variant (no timing). */
+int fm_tuning(const fm_state* st, int level, int* variant, float* ms_per_variant);
 
 /* Enable (1) or disable (0) CUDA-event timing of every finest-level smoother
  * launch issued by fm_step, and reset the accumulated totals. */

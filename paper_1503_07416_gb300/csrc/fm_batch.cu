@@ -82,16 +82,63 @@ __device__ __forceinline__ void smem_copy(S* dst, const S* src) {
   const int lb = blockIdx.x - items[k_].blk0;                    \
   (void)lb
 
-template <typename T, int KIND>
+// Fused sweep over the tiles of level `level` of all instances (the work list
+// maps a tile to its instance; tiles of converged instances are skipped).
+// PIPE: persistent blocks over tiles t = blockIdx.x, blockIdx.x + gridDim.x,
+// ..., two shared-memory buffers, the next tile's copies in flight while the
+// current one is computed; otherwise one tile per block.
+template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
 __global__ void __launch_bounds__(RB_THREADS) kb_smooth_rb2d(const WorkItem* items, int nitems, const InstDev<T>* D,
-                                                             const Phys<T>* P, const Ctl* ctl, int level) {
-  FM_BATCH_HEAD();
-  if (!inst_active(ctl, inst)) return;
-  __shared__ Lvl<T> G;
-  smem_copy(&G, &D[inst].lv[level]);
-  __syncthreads();
-  const int ntx = items[k_].aux;
-  rb2d_tile<T, KIND>(G, P[inst], lb % ntx, lb / ntx);
+                                                             const Phys<T>* P, const Ctl* ctl, int level,
+                                                             int ntiles) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* buf0 = reinterpret_cast<T*>(smraw);
+  constexpr int BUFSTRIDE = rb_arrays<KIND, SF>() * RBGeom<TX, TY>::SN;
+  __shared__ Lvl<T> Gs[2];
+  __shared__ int s_inst[2], s_x0[2], s_y0[2];
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  auto fetch = [&](int tt, int slot) {
+    if (threadIdx.x == 0) {
+      const int k = find_item(items, nitems, tt);
+      const int inst = items[k].inst;
+      const int lb = tt - items[k].blk0;
+      const int ntx = items[k].aux;
+      s_inst[slot] = inst_active(ctl, inst) ? inst : -1;
+      s_x0[slot] = (lb % ntx) * TX;
+      s_y0[slot] = (lb / ntx) * TY;
+    }
+    __syncthreads();
+    if (s_inst[slot] >= 0) {
+      smem_copy(&Gs[slot], &D[s_inst[slot]].lv[level]);
+      __syncthreads();
+      rb2d_issue<T, KIND, TX, TY, SF>(Gs[slot], buf0 + slot * BUFSTRIDE, s_x0[slot], s_y0[slot]);
+    }
+    cp_async_commit();
+  };
+  if constexpr (!PIPE) {
+    fetch(t, 0);
+    cp_async_wait_all();
+    __syncthreads();
+    if (s_inst[0] >= 0) rb2d_compute<T, KIND, TX, TY, SF>(Gs[0], P[s_inst[0]], buf0, s_x0[0], s_y0[0]);
+  } else {
+    fetch(t, 0);
+    for (int k = 0;; ++k) {
+      const int tn = t + gridDim.x;
+      const bool next = tn < ntiles;
+      if (next) fetch(tn, (k + 1) & 1);
+      else cp_async_commit();
+      cp_async_wait_one();
+      __syncthreads();
+      const int slot = k & 1;
+      if (s_inst[slot] >= 0)
+        rb2d_compute<T, KIND, TX, TY, SF>(Gs[slot], P[s_inst[slot]], buf0 + slot * BUFSTRIDE, s_x0[slot],
+                                          s_y0[slot]);
+      __syncthreads();
+      if (!next) break;
+      t = tn;
+    }
+  }
 }
 
 template <typename T, int KIND>
@@ -196,6 +243,11 @@ __global__ void kb_norm(const InstDev<T>* D, Ctl* ctl, double tol, int max_cycle
   if (threadIdx.x == 0) ctl[inst].pad[0] = cont ? 1 : 0;
 }
 
+__global__ void kb_set_active(Ctl* ctl, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) ctl[i].pad[0] = 1;
+}
+
 __global__ void kb_condition(const Ctl* ctl, int count, cudaGraphConditionalHandle handle) {
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
@@ -259,7 +311,10 @@ struct fm_batch {
   // work lists
   std::vector<WorkItem> hitems;
   WList w_fine, w_resid64, w_inject;
-  WList w_smooth[MAXLEV], w_resid[MAXLEV], w_restrict[MAXLEV], w_crhs[MAXLEV], w_prolong[MAXLEV];
+  WList w_smooth[2][MAXLEV];  // per tile shape (32x16, 64x8)
+  WList w_resid[MAXLEV], w_restrict[MAXLEV], w_crhs[MAXLEV], w_prolong[MAXLEV];
+  int rbv[MAXLEV];           // chosen fused-sweep variant per level
+  float rbt[MAXLEV][8];      // autotuner timings (ms per launch)
   // graph
   cudaStream_t stream;
   cudaStream_t user_stream;
@@ -407,21 +462,24 @@ struct Batch {
     }
     b->w_inject = add_list(b, v);
     for (int l = 0; l < b->maxdepth; ++l) {
-      std::vector<std::pair<int, int>> ts, rs, rr, cr, pr;
-      std::vector<int> aux;
+      std::vector<std::pair<int, int>> ts[2], rs, rr, cr, pr;
+      std::vector<int> aux[2];
       for (int i = 0; i < b->count; ++i) {
         fm_state* st = b->inst[i];
         if (st->small_from <= l) continue;
         const Geo g = st->lv[l].g, gc = st->lv[l + 1].g;
-        const int ntx = (g.nx + RB_TX - 1) / RB_TX, nty = (g.ny + RB_TY - 1) / RB_TY;
-        ts.push_back({i, ntx * nty});
-        aux.push_back(ntx);
+        for (int sh = 0; sh < 2; ++sh) {
+          const int TX = sh ? 64 : 32, TY = sh ? 8 : 16;
+          const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
+          ts[sh].push_back({i, ntx * nty});
+          aux[sh].push_back(ntx);
+        }
         rs.push_back({i, nblocks(g.N)});
         rr.push_back({i, nblocks(gc.N)});
         cr.push_back({i, nblocks(gc.N)});
         pr.push_back({i, nblocks(g.N)});
       }
-      b->w_smooth[l] = add_list(b, ts, &aux);
+      for (int sh = 0; sh < 2; ++sh) b->w_smooth[sh][l] = add_list(b, ts[sh], &aux[sh]);
       b->w_resid[l] = add_list(b, rs);
       b->w_restrict[l] = add_list(b, rr);
       b->w_crhs[l] = add_list(b, cr);
@@ -431,16 +489,89 @@ struct Batch {
 
   static const WorkItem* it(fm_batch* b, const WList& w) { return b->items + w.off; }
 
+  template <int TX, int TY, bool SF, bool PIPE>
+  static int launch_v(fm_batch* b, int l) {
+    constexpr size_t smem = rb_smem_bytes<T, KIND, TX, TY, SF, PIPE>();
+    static int per_sm = 0;
+    if (!per_sm) {
+      FMB_CUDA(cudaFuncSetAttribute(kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FMB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>,
+                                                             RB_THREADS, smem));
+      if (per_sm < 1) per_sm = 1;
+    }
+    const WList& w = b->w_smooth[TX == 64 ? 1 : 0][l];
+    int grid = w.nblocks;
+    if (PIPE && grid > per_sm * b->inst[0]->sms) grid = per_sm * b->inst[0]->sms;
+    kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE><<<grid, RB_THREADS, smem, b->stream>>>(
+        it(b, w), w.n, (const InstDev<T>*)b->D, (const Phys<T>*)b->P, b->ctl, l, w.nblocks);
+    FMB_LAUNCHED();
+    return FM_OK;
+  }
+
+  static int launch_variant(fm_batch* b, int v, int l) {
+    switch (v) {
+      case 0: return launch_v<32, 16, false, false>(b, l);
+      case 1: return launch_v<32, 16, false, true>(b, l);
+      case 2: return launch_v<32, 16, true, false>(b, l);
+      case 3: return launch_v<32, 16, true, true>(b, l);
+      case 4: return launch_v<64, 8, false, false>(b, l);
+      case 5: return launch_v<64, 8, false, true>(b, l);
+      case 6: return launch_v<64, 8, true, false>(b, l);
+      default: return launch_v<64, 8, true, true>(b, l);
+    }
+  }
+
   static int smooth(fm_batch* b, int l, int iters) {
-    const WList& w = b->w_smooth[l];
-    if (w.n == 0) return FM_OK;
-    const size_t smem = (size_t)rb_arrays<KIND>() * RB_SN * sizeof(T);
+    if (b->w_smooth[0][l].n == 0) return FM_OK;
     for (int k = 0; k < iters; ++k) {
-      kb_smooth_rb2d<T, KIND><<<w.nblocks, RB_THREADS, smem, b->stream>>>(
-          it(b, w), w.n, (const InstDev<T>*)b->D, (const Phys<T>*)b->P, b->ctl, l);
-      FMB_LAUNCHED();
+      const int rc = launch_variant(b, b->rbv[l], l);
+      if (rc) return rc;
     }
     return FM_OK;
+  }
+
+  // Per level, time every variant of the fused sweep over all instances
+  // (one warm-up and three timed launches, CUDA events) and keep the fastest.
+  static int autotune(fm_batch* b) {
+    for (int l = 0; l < MAXLEV; ++l) b->rbv[l] = 0;
+    const char* fixed = getenv("FM_RB_VARIANT");
+    if (fixed && fixed[0]) {
+      const int v = atoi(fixed);
+      for (int l = 0; l < MAXLEV; ++l) b->rbv[l] = (v >= 0 && v < RB_NVAR) ? v : 0;
+      return FM_OK;
+    }
+    kb_set_active<<<(b->count + 255) / 256, 256, 0, b->stream>>>(b->ctl, b->count);
+    FMB_LAUNCHED();
+    cudaEvent_t e0, e1;
+    FMB_CUDA(cudaEventCreate(&e0));
+    FMB_CUDA(cudaEventCreate(&e1));
+    int rc = FM_OK;
+    for (int l = 0; l < b->maxdepth && rc == FM_OK; ++l) {
+      float best = 1e30f;
+      for (int v = 0; v < RB_NVAR && rc == FM_OK; ++v) {
+        rc = launch_variant(b, v, l);
+        if (rc) break;
+        if (cudaEventRecord(e0, b->stream) != cudaSuccess) { rc = FM_ECUDA; break; }
+        for (int k = 0; k < 3 && rc == FM_OK; ++k) rc = launch_variant(b, v, l);
+        if (rc) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          rc = FM_ECUDA;
+          break;
+        }
+        b->rbt[l][v] = ms / 3.f;
+        if (ms < best) {
+          best = ms;
+          b->rbv[l] = v;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    return rc;
   }
 
   static int vcycle(fm_batch* b) {
@@ -628,9 +759,31 @@ struct Batch {
     if (b->small_smem > (size_t)SMALL_SMEM_MAX) return FM_EINVAL;
     FMB_CUDA(cudaFuncSetAttribute(kb_small<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)SMALL_SMEM_MAX));
-    FMB_CUDA(cudaFuncSetAttribute(kb_smooth_rb2d<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(rb_arrays<KIND>() * RB_SN * sizeof(T))));
+    return autotune(b);
     return FM_OK;
+  }
+
+  // Time `iters` finest-level fused sweeps over all instances (CUDA events on
+  // the batch stream); the corrections they write are scratch that the next
+  // step resets.
+  static int time_smoother(fm_batch* b, int iters, double* ms) {
+    kb_set_active<<<(b->count + 255) / 256, 256, 0, b->stream>>>(b->ctl, b->count);
+    FMB_LAUNCHED();
+    cudaEvent_t e0, e1;
+    FMB_CUDA(cudaEventCreate(&e0));
+    FMB_CUDA(cudaEventCreate(&e1));
+    int rc = smooth(b, 0, 1);  // warm-up
+    if (rc == FM_OK && cudaEventRecord(e0, b->stream) != cudaSuccess) rc = FM_ECUDA;
+    if (rc == FM_OK) rc = smooth(b, 0, iters);
+    if (rc == FM_OK && cudaEventRecord(e1, b->stream) != cudaSuccess) rc = FM_ECUDA;
+    if (rc == FM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = FM_ECUDA;
+    float t = 0.f;
+    if (rc == FM_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = FM_ECUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    *ms = (double)t / iters;
+    return rc;
   }
 
   static int step(fm_batch* b, const double* dt) {
@@ -758,5 +911,27 @@ int fm_step_batch(fm_batch* b, const double* dt, fm_step_info* info) {
 }
 
 long long fm_batch_launches(const fm_batch* b) { return b ? b->launches : -1; }
+
+int fm_batch_tuning(const fm_batch* b, int level, int* variant, float* ms_per_variant) {
+  if (!b || level < 0 || level >= MAXLEV) return FM_EINVAL;
+  if (variant) *variant = b->rbv[level];
+  if (ms_per_variant)
+    for (int v = 0; v < RB_NVAR; ++v) ms_per_variant[v] = b->rbt[level][v];
+  return FM_OK;
+}
+
+int fm_batch_time_smoother(fm_batch* b, int iters, double* ms_per_launch, long long* points) {
+  if (!b || iters < 1 || !ms_per_launch) return FM_EINVAL;
+  if (b->maxdepth < 1) return FM_EINVAL;  // no instance has a multi-kernel finest level
+  long long np = 0;
+  for (int i = 0; i < b->count; ++i)
+    if (b->inst[i]->small_from > 0) np += b->inst[i]->lv[0].g.N;
+  if (points) *points = np;
+  if (b->prm.precision == FM_MIXED)
+    return b->kind == FM_PFC ? Batch<float, KPFC>::time_smoother(b, iters, ms_per_launch)
+                             : Batch<float, KCDFT>::time_smoother(b, iters, ms_per_launch);
+  return b->kind == FM_PFC ? Batch<double, KPFC>::time_smoother(b, iters, ms_per_launch)
+                           : Batch<double, KCDFT>::time_smoother(b, iters, ms_per_launch);
+}
 
 }  // extern "C"

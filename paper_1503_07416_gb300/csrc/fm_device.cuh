@@ -19,8 +19,11 @@ static inline int nblocks(long long work) { return (int)((work + TPB - 1) / TPB)
 // --------------------------------------------------------------------------
 // Smoother point update (correction form)
 // --------------------------------------------------------------------------
+// Point-block update of one point; the right-hand side f and omega^k are
+// read through (Fr, Om) at index fc, everything else through L at n.
 template <typename T, int KIND, int DIM>
-__device__ __forceinline__ void smooth_point(const Lvl<T>& L, const Phys<T>& P, const Nb& n) {
+__device__ __forceinline__ void smooth_point_ex(const Lvl<T>& L, const Phys<T>& P, const Nb& n,
+                                                T* const* Fr, const T* const* Om, int fc) {
   using LY = Layout<KIND, DIM>;
   T* const* E = L.e;
   const T ih = T(1) / L.h;
@@ -37,7 +40,7 @@ __device__ __forceinline__ void smooth_point(const Lvl<T>& L, const Phys<T>& P, 
 #pragma unroll
   for (int d = 0; d < DIM; ++d)
     div += L.rk[n.p[d]] * E[1 + d][n.p[d]] - L.rk[n.m[d]] * E[1 + d][n.m[d]];
-  T er = L.f[0][c] - P.s * T(0.25) * ih * div;
+  T er = Fr[0][fc] - P.s * T(0.25) * ih * div;
   {
     const T x = crc + er;
     if (x <= T(0)) er = sqrt_t(x * x + P.delta * P.delta) - crc;  // Sec. 6 projection
@@ -47,10 +50,10 @@ __device__ __forceinline__ void smooth_point(const Lvl<T>& L, const Phys<T>& P, 
 
   if constexpr (KIND == KPFC) {
     // kappa = f5 + Lap_h e_rho with the new centre value
-    const T ek = L.f[LY::IKA][c] + (nbsum<T, DIM>(E[0], n) - T(2 * DIM) * er) * ih2;
+    const T ek = Fr[LY::IKA][fc] + (nbsum<T, DIM>(E[0], n) - T(2 * DIM) * er) * ih2;
     // mu = f4 + [(p+e)^3 - p^3]/3 + alpha e + Lap_h e_kappa (exact: the block is triangular)
     const T psi = crc - T(1.5);
-    const T em = L.f[LY::IMU][c] + er * (psi * psi + psi * er + er * er / T(3)) + P.alpha * er
+    const T em = Fr[LY::IMU][fc] + er * (psi * psi + psi * er + er * er / T(3)) + P.alpha * er
                + (nbsum<T, DIM>(E[LY::IKA], n) - T(2 * DIM) * ek) * ih2;
     eg[LY::IKA] = ek;
     eg[LY::IMU] = em;
@@ -62,20 +65,20 @@ __device__ __forceinline__ void smooth_point(const Lvl<T>& L, const Phys<T>& P, 
   for (int a = 0; a < DIM; ++a) {
     const T dq = qcorr<T, DIM>(E, L.cv, n.p[a]) - qcorr<T, DIM>(E, L.cv, n.m[a]);
     const T dm = mcorr<T, KIND, DIM>(E, L.cr, n.p[a], P.ce) - mcorr<T, KIND, DIM>(E, L.cr, n.m[a], P.ce);
-    rhs[a] = L.f[1 + a][c] - P.s * rkc * ih * (T(0.25) * dq + T(0.5) * dm)
+    rhs[a] = Fr[1 + a][fc] - P.s * rkc * ih * (T(0.25) * dq + T(0.5) * dm)
            + T(0.5) * P.s * P.gamma * ih2 * nbsum<T, DIM>(E[1 + a], n);
   }
   const T A = rkc + P.s * P.gamma * T(DIM) * ih2;
   const T bs = T(0.5) * P.sigma * P.s * rkc;
   if constexpr (DIM == 2) {
-    const T b = bs * L.om[0][c];
+    const T b = bs * Om[0][fc];
     const T inv = T(1) / (A * A + b * b);
     eg[1] = (A * rhs[0] + b * rhs[1]) * inv;
     eg[2] = (A * rhs[1] - b * rhs[0]) * inv;
   } else {
     T b[3], bx[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) b[d] = bs * L.om[d][c];
+    for (int d = 0; d < 3; ++d) b[d] = bs * Om[d][fc];
     cross<T, 3>(b, rhs, bx);
     const T bdy = b[0] * rhs[0] + b[1] * rhs[1] + b[2] * rhs[2];
     const T inv = T(1) / (A * (A * A + b[0] * b[0] + b[1] * b[1] + b[2] * b[2]));
@@ -86,6 +89,11 @@ __device__ __forceinline__ void smooth_point(const Lvl<T>& L, const Phys<T>& P, 
   const T w = P.w;
 #pragma unroll
   for (int q = 0; q < LY::NU; ++q) E[q][c] = (T(1) - w) * eg[q] + w * eo[q];
+}
+
+template <typename T, int KIND, int DIM>
+__device__ __forceinline__ void smooth_point(const Lvl<T>& L, const Phys<T>& P, const Nb& n) {
+  smooth_point_ex<T, KIND, DIM>(L, P, n, L.f, L.om, n.c);
 }
 
 // --------------------------------------------------------------------------
@@ -223,104 +231,219 @@ __global__ void __launch_bounds__(TPB) k_prolong(Lvl<T> F, Lvl<T> C) {
   if (idx < F.g.N) prolong_point<T, NU, DIM>(F, C, idx);
 }
 
-// Fused red-black sweep of a 2-D level: one thread block per RB_TX x RB_TY
-// tile.  The tile and a halo of two points of every array the point update
-// reads are staged in shared memory; red points are updated on the tile and
-// its first halo ring (their black neighbours are all staged), then black
-// points on the tile, and the tile's corrections are written back.  Red
-// values on the ring are recomputed identically by the neighbouring tiles, so
-// the result equals a red launch followed by a black launch.
-constexpr int RB_TX = 32, RB_TY = 16, RB_H = 2;
-constexpr int RB_SW = RB_TX + 2 * RB_H;
-constexpr int RB_SN = RB_SW * (RB_TY + 2 * RB_H);
+// Fused red-black sweep of a 2-D level in TX x TY tiles.  The tile and a
+// halo of two points of every array the point update reads are staged in
+// shared memory; red points are updated on the tile and its first halo ring
+// (their black neighbours are all staged), then black points on the tile, and
+// the tile's corrections are written back.  Red values on the ring are
+// recomputed identically by the neighbouring tiles, so a sweep equals a red
+// launch followed by a black launch.  Blocks are persistent: each walks a
+// strided sequence of tiles with two shared-memory buffers, copying the next
+// tile in with cp.async (global -> shared, no register staging) while it
+// computes the current one.
+constexpr int RB_H = 2;
 constexpr int RB_THREADS = 256;
 
-template <int KIND>
-constexpr int rb_arrays() {
-  return 2 * Layout<KIND, 2>::NU + 5;  // e, f, rk, om, cr, cv0, cv1
+// Shared-memory tile: rows of SW = TX + 2*XO values (the tile starts at
+// column XO = 4 so that every row begins on a 16-byte boundary in global and
+// shared memory), TY + 2*RB_H rows.
+constexpr int RB_XO = 4;
+
+template <int TX, int TY>
+struct RBGeom {
+  static constexpr int SW = TX + 2 * RB_XO;
+  static constexpr int SN = SW * (TY + 2 * RB_H);
+};
+
+// Arrays staged per tile: e (NU), rk, cr, cv0, cv1, and with SF also f (NU)
+// and omega (otherwise f and omega are read from global memory).
+template <int KIND, bool SF>
+__host__ __device__ constexpr int rb_arrays() {
+  return Layout<KIND, 2>::NU + 4 + (SF ? Layout<KIND, 2>::NU + 1 : 0);
+}
+
+template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
+__host__ __device__ constexpr size_t rb_smem_bytes() {
+  return (PIPE ? 2 : 1) * (size_t)rb_arrays<KIND, SF>() * RBGeom<TX, TY>::SN * sizeof(T);
 }
 
 __device__ __forceinline__ int wrapi(int x, int n) {
-  x %= n;
-  return x < 0 ? x + n : x;
+  if (x < 0) x += n;
+  else if (x >= n) x -= n;
+  if ((unsigned)x >= (unsigned)n) {
+    x %= n;
+    if (x < 0) x += n;
+  }
+  return x;
 }
 
-template <typename T, int KIND>
-__device__ __forceinline__ void rb2d_tile(const Lvl<T>& G, const Phys<T>& P, int bx, int by) {
-  using LY = Layout<KIND, 2>;
-  constexpr int NU = LY::NU;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_16(T* smem, const T* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Start the copies of tile (x0, y0) of level G into buf: 16-byte chunks when
+// the row length is a multiple of the chunk (chunks then never straddle the
+// periodic wrap), single elements otherwise.
+template <typename T, int KIND, int TX, int TY, bool SF>
+__device__ __forceinline__ void rb2d_issue(const Lvl<T>& G, T* buf, int x0, int y0) {
+  using Gm = RBGeom<TX, TY>;
+  constexpr int NU = Layout<KIND, 2>::NU;
+  constexpr int NA = rb_arrays<KIND, SF>();
+  constexpr int V = 16 / sizeof(T);
   const int nx = G.g.nx, ny = G.g.ny;
-  const int x0 = bx * RB_TX, y0 = by * RB_TY;
-  for (int t = threadIdx.x; t < RB_SN; t += blockDim.x) {
-    const int ly = t / RB_SW, lx = t - ly * RB_SW;
-    const int gidx = wrapi(y0 + ly - RB_H, ny) * nx + wrapi(x0 + lx - RB_H, nx);
+  const T* src[NA];
 #pragma unroll
-    for (int q = 0; q < NU; ++q) {
-      sm[q * RB_SN + t] = G.e[q][gidx];
-      sm[(NU + q) * RB_SN + t] = G.f[q][gidx];
-    }
-    sm[(2 * NU) * RB_SN + t] = G.rk[gidx];
-    sm[(2 * NU + 1) * RB_SN + t] = G.om[0][gidx];
-    sm[(2 * NU + 2) * RB_SN + t] = G.cr[gidx];
-    sm[(2 * NU + 3) * RB_SN + t] = G.cv[0][gidx];
-    sm[(2 * NU + 4) * RB_SN + t] = G.cv[1][gidx];
+  for (int q = 0; q < NU; ++q) src[q] = G.e[q];
+  src[NU + 0] = G.rk;
+  src[NU + 1] = G.cr;
+  src[NU + 2] = G.cv[0];
+  src[NU + 3] = G.cv[1];
+  if constexpr (SF) {
+#pragma unroll
+    for (int q = 0; q < NU; ++q) src[NU + 4 + q] = G.f[q];
+    src[2 * NU + 4] = G.om[0];
   }
+  if (nx % V == 0) {
+    constexpr int CPR = Gm::SW / V;  // chunks per row
+    constexpr int NCH = CPR * (TY + 2 * RB_H);
+    for (int t = threadIdx.x; t < NCH; t += blockDim.x) {
+      const int ly = t / CPR, c = t - ly * CPR;
+      const int gidx = wrapi(y0 + ly - RB_H, ny) * nx + wrapi(x0 - RB_XO + c * V, nx);
+      const int sidx = ly * Gm::SW + c * V;
+#pragma unroll
+      for (int a = 0; a < NA; ++a) cp_async_16(buf + a * Gm::SN + sidx, src[a] + gidx);
+    }
+  } else {
+    for (int t = threadIdx.x; t < Gm::SN; t += blockDim.x) {
+      const int ly = t / Gm::SW, lx = t - ly * Gm::SW;
+      const int gidx = wrapi(y0 + ly - RB_H, ny) * nx + wrapi(x0 + lx - RB_XO, nx);
+#pragma unroll
+      for (int a = 0; a < NA; ++a) cp_async_elem(buf + a * Gm::SN + t, src[a] + gidx);
+    }
+  }
+}
+
+// Red pass on tile + ring 1, black pass on the tile, write-back of the tile.
+template <typename T, int KIND, int TX, int TY, bool SF>
+__device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, T* buf, int x0, int y0) {
+  using Gm = RBGeom<TX, TY>;
+  constexpr int NU = Layout<KIND, 2>::NU;
+  constexpr int SN = Gm::SN, SW = Gm::SW;
   Lvl<T> L;
   L.g = G.g;
   L.h = G.h;
+  T* Fs[MAXU];
+  const T* Os[3];
 #pragma unroll
   for (int q = 0; q < MAXU; ++q) {
-    L.e[q] = q < NU ? sm + q * RB_SN : nullptr;
-    L.f[q] = q < NU ? sm + (NU + q) * RB_SN : nullptr;
-    L.r[q] = L.eh[q] = nullptr;
+    L.e[q] = q < NU ? buf + q * SN : nullptr;
+    L.f[q] = L.r[q] = L.eh[q] = nullptr;
+    Fs[q] = q < NU ? buf + (NU + 4 + q) * SN : nullptr;
   }
-  L.rk = sm + (2 * NU) * RB_SN;
-  L.om[0] = sm + (2 * NU + 1) * RB_SN;
-  L.om[1] = L.om[2] = nullptr;
-  L.cr = sm + (2 * NU + 2) * RB_SN;
-  L.cv[0] = sm + (2 * NU + 3) * RB_SN;
-  L.cv[1] = sm + (2 * NU + 4) * RB_SN;
+  L.rk = buf + (NU + 0) * SN;
+  L.cr = buf + (NU + 1) * SN;
+  L.cv[0] = buf + (NU + 2) * SN;
+  L.cv[1] = buf + (NU + 3) * SN;
   L.cv[2] = nullptr;
-  __syncthreads();
+  L.om[0] = L.om[1] = L.om[2] = nullptr;
+  Os[0] = buf + (2 * NU + 4) * SN;
+  Os[1] = Os[2] = nullptr;
+  const int nx = G.g.nx, ny = G.g.ny;
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
     const int color = pass;              // red (i + j even) first, then black
     const int ring = pass == 0 ? 1 : 0;  // red also on the first halo ring
-    const int w = RB_TX + 2 * ring;      // even
+    const int w = TX + 2 * ring;         // even
     const int hw = w >> 1;
-    const int npts = hw * (RB_TY + 2 * ring);
+    const int npts = hw * (TY + 2 * ring);
     for (int t = threadIdx.x; t < npts; t += blockDim.x) {
       const int ry = t / hw;
       const int gy = y0 - ring + ry;
       const int rx = 2 * (t - ry * hw) + ((color + x0 + ring + gy) & 1);
-      const int lx = RB_H - ring + rx, ly = RB_H - ring + ry;
+      const int lx = RB_XO - ring + rx, ly = RB_H - ring + ry;
       Nb n;
-      n.c = ly * RB_SW + lx;
+      n.c = ly * SW + lx;
       n.m[0] = n.c - 1;
       n.p[0] = n.c + 1;
-      n.m[1] = n.c - RB_SW;
-      n.p[1] = n.c + RB_SW;
+      n.m[1] = n.c - SW;
+      n.p[1] = n.c + SW;
       n.m[2] = n.p[2] = n.c;
-      smooth_point<T, KIND, 2>(L, P, n);
+      if constexpr (SF) {
+        smooth_point_ex<T, KIND, 2>(L, P, n, Fs, Os, n.c);
+      } else {
+        const int gidx = wrapi(gy, ny) * nx + wrapi(x0 - ring + rx, nx);
+        smooth_point_ex<T, KIND, 2>(L, P, n, G.f, G.om, gidx);
+      }
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < RB_TX * RB_TY; t += blockDim.x) {
-    const int ty = t / RB_TX, tx = t - ty * RB_TX;
+  for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
+    const int ty = t / TX, tx = t - ty * TX;
     const int gx = x0 + tx, gy = y0 + ty;
     if (gx < nx && gy < ny) {
-      const int sidx = (ty + RB_H) * RB_SW + tx + RB_H;
+      const int sidx = (ty + RB_H) * SW + tx + RB_XO;
 #pragma unroll
       for (int q = 0; q < NU; ++q) G.e[q][gy * nx + gx] = L.e[q][sidx];
     }
   }
 }
 
-template <typename T, int KIND>
-__global__ void __launch_bounds__(RB_THREADS) k_smooth_rb2d(Lvl<T> G, Phys<T> P) {
-  rb2d_tile<T, KIND>(G, P, blockIdx.x, blockIdx.y);
+// Single level.  PIPE: persistent blocks over tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ..., the next tile's copies in flight while the
+// current one is computed; otherwise one tile per block.
+template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
+__global__ void __launch_bounds__(RB_THREADS) k_smooth_rb2d(Lvl<T> G, Phys<T> P, int ntx, int ntiles) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* buf0 = reinterpret_cast<T*>(smraw);
+  constexpr int BUFSTRIDE = rb_arrays<KIND, SF>() * RBGeom<TX, TY>::SN;
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  if constexpr (!PIPE) {
+    rb2d_issue<T, KIND, TX, TY, SF>(G, buf0, (t % ntx) * TX, (t / ntx) * TY);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    rb2d_compute<T, KIND, TX, TY, SF>(G, P, buf0, (t % ntx) * TX, (t / ntx) * TY);
+  } else {
+    rb2d_issue<T, KIND, TX, TY, SF>(G, buf0, (t % ntx) * TX, (t / ntx) * TY);
+    cp_async_commit();
+    for (int k = 0;; ++k) {
+      const int tn = t + gridDim.x;
+      const bool next = tn < ntiles;
+      if (next) rb2d_issue<T, KIND, TX, TY, SF>(G, buf0 + ((k + 1) & 1) * BUFSTRIDE, (tn % ntx) * TX, (tn / ntx) * TY);
+      cp_async_commit();
+      cp_async_wait_one();
+      __syncthreads();
+      rb2d_compute<T, KIND, TX, TY, SF>(G, P, buf0 + (k & 1) * BUFSTRIDE, (t % ntx) * TX, (t / ntx) * TY);
+      __syncthreads();
+      if (!next) break;
+      t = tn;
+    }
+  }
+}
+
+// Variants of the 2-D fused sweep (tile shape, staging of f/omega,
+// pipelining), chosen per level by the autotuner.
+struct RBVariant {
+  int tx, ty;
+  bool sf, pipe;
+};
+constexpr int RB_NVAR = 8;
+__host__ __device__ constexpr RBVariant rb_variant(int v) {
+  return RBVariant{(v & 4) ? 64 : 32, (v & 4) ? 8 : 16, (v & 2) != 0, (v & 1) != 0};
 }
 
 // The whole V-cycle of the small levels (each at most SMALL_N points) in one

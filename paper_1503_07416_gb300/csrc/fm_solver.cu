@@ -105,6 +105,43 @@ __global__ void k_prolong_one(const double* coarse, double* fine, Geo F, Geo C, 
     }                                                   \
   } while (0)
 
+// Launch variant (TX, TY, SF, PIPE) of the 2-D fused sweep on level L.
+template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
+static int launch_rb_v(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s) {
+  constexpr size_t smem = rb_smem_bytes<T, KIND, TX, TY, SF, PIPE>();
+  static int per_sm = 0;
+  if (!per_sm) {
+    if (cudaFuncSetAttribute(k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>, RB_THREADS,
+                                                      smem) != cudaSuccess) {
+      cudaGetLastError();
+      return FM_ECUDA;
+    }
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int ntx = (L.g.nx + TX - 1) / TX;
+  const int ntiles = ntx * ((L.g.ny + TY - 1) / TY);
+  int grid = ntiles;
+  if (PIPE && grid > per_sm * st->sms) grid = per_sm * st->sms;
+  k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE><<<grid, RB_THREADS, smem, s>>>(L, P, ntx, ntiles);
+  return FM_OK;
+}
+
+template <typename T, int KIND>
+static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s) {
+  switch (v) {
+    case 0: return launch_rb_v<T, KIND, 32, 16, false, false>(st, L, P, s);
+    case 1: return launch_rb_v<T, KIND, 32, 16, false, true>(st, L, P, s);
+    case 2: return launch_rb_v<T, KIND, 32, 16, true, false>(st, L, P, s);
+    case 3: return launch_rb_v<T, KIND, 32, 16, true, true>(st, L, P, s);
+    case 4: return launch_rb_v<T, KIND, 64, 8, false, false>(st, L, P, s);
+    case 5: return launch_rb_v<T, KIND, 64, 8, false, true>(st, L, P, s);
+    case 6: return launch_rb_v<T, KIND, 64, 8, true, false>(st, L, P, s);
+    default: return launch_rb_v<T, KIND, 64, 8, true, true>(st, L, P, s);
+  }
+}
+
 // Sum the durations of the recorded (start, end) event pairs; call only after
 // the stream has been synchronised.
 static int harvest_profile(fm_state* st) {
@@ -166,6 +203,55 @@ struct Solver {
     k_inject_all<T><<<nblocks(A.off[st->nlev]), TPB, 0, st->stream>>>(A);
     FM_LAUNCHED();
     return FM_OK;
+  }
+
+  // Choose, per multi-kernel level, the fastest variant of the fused 2-D
+  // sweep: each variant is timed with CUDA events (one warm-up and three timed
+  // launches) on the level itself.  The sweeps only touch solver scratch.
+  static int autotune(fm_state* st) {
+    if constexpr (DIM != 2) {
+      return FM_OK;
+    } else {
+      const char* fixed = getenv("FM_RB_VARIANT");
+      for (int l = 0; l < MAXLEV; ++l) st->rbv[l] = 0;
+      if (fixed && fixed[0]) {
+        const int v = atoi(fixed);
+        for (int l = 0; l < MAXLEV; ++l) st->rbv[l] = (v >= 0 && v < RB_NVAR) ? v : 0;
+        return FM_OK;
+      }
+      if (!st->fused_rb) return FM_OK;
+      Phys<T> P = make_phys<T>(st);
+      cudaEvent_t e0, e1;
+      FM_CUDA(cudaEventCreate(&e0));
+      FM_CUDA(cudaEventCreate(&e1));
+      int rc = FM_OK;
+      for (int l = 0; l < st->small_from && rc == FM_OK; ++l) {
+        Lvl<T> L = make_lvl<T>(st, l);
+        float best = 1e30f;
+        for (int v = 0; v < RB_NVAR && rc == FM_OK; ++v) {
+          rc = launch_rb<T, KIND>(st, v, L, P, st->stream);
+          if (rc) break;
+          if (cudaEventRecord(e0, st->stream) != cudaSuccess) { rc = FM_ECUDA; break; }
+          for (int k = 0; k < 3 && rc == FM_OK; ++k) rc = launch_rb<T, KIND>(st, v, L, P, st->stream);
+          if (rc) break;
+          if (cudaEventRecord(e1, st->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = FM_ECUDA;
+            break;
+          }
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = FM_ECUDA; break; }
+          st->rbt[l][v] = ms / 3.f;
+          if (ms < best) {
+            best = ms;
+            st->rbv[l] = v;
+          }
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      cudaGetLastError();
+      return rc;
+    }
   }
 
   static int enqueue_prepare(fm_state* st) {
@@ -254,24 +340,18 @@ struct Solver {
     const int half = L.g.N / 2;
     const bool prof = st->prof && !st->capturing && l == 0;
     const bool fused = DIM == 2 && st->fused_rb;
-    const size_t smem = (size_t)rb_arrays<KIND>() * RB_SN * sizeof(T);
-    if (fused) {
-      static bool attr = false;
-      if (!attr) {
-        FM_CUDA(cudaFuncSetAttribute(k_smooth_rb2d<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-        attr = true;
-      }
-    }
-    const dim3 tiles((L.g.nx + RB_TX - 1) / RB_TX, (L.g.ny + RB_TY - 1) / RB_TY);
     for (int it = 0; it < iters; ++it) {
       const int nlaunch = fused ? 1 : 2;
       for (int color = 0; color < nlaunch; ++color) {
         if (prof && st->npev + 2 <= MAXEV) FM_CUDA(cudaEventRecord(st->pev[st->npev], s));
-        if (fused)
-          k_smooth_rb2d<T, KIND><<<tiles, RB_THREADS, smem, s>>>(L, P);
-        else
+        if (fused) {
+          if constexpr (DIM == 2) {
+            const int rc = launch_rb<T, KIND>(st, st->rbv[l], L, P, s);
+            if (rc) return rc;
+          }
+        } else {
           k_smooth<T, KIND, DIM><<<nblocks(half), TPB, 0, s>>>(L, P, color);
+        }
         FM_LAUNCHED();
         if (prof && st->npev + 2 <= MAXEV) {
           FM_CUDA(cudaEventRecord(st->pev[st->npev + 1], s));
@@ -497,6 +577,13 @@ static int dispatch_step(fm_state* st, fm_step_info* info) {
 }
 
 template <typename T>
+static int dispatch_autotune(fm_state* st) {
+  if (st->kind == FM_PFC)
+    return st->dim == 2 ? Solver<T, KPFC, 2>::autotune(st) : Solver<T, KPFC, 3>::autotune(st);
+  return st->dim == 2 ? Solver<T, KCDFT, 2>::autotune(st) : Solver<T, KCDFT, 3>::autotune(st);
+}
+
+template <typename T>
 static int dispatch_prepare(fm_state* st) {
   if (st->kind == FM_PFC)
     return st->dim == 2 ? Solver<T, KPFC, 2>::prepare(st) : Solver<T, KPFC, 3>::prepare(st);
@@ -692,6 +779,7 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
     delete st;
     return FM_ECUDA;
   }
+  st->sms = sms;
   const int need = (int)((st->lv[0].g.N + TPB - 1) / TPB);
   st->nblk = need < 4 * sms ? need : 4 * sms;
   const size_t bytes = carve(st, nullptr);
@@ -729,6 +817,13 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
       return rc;
     }
   }
+  {
+    const int rc = prm->precision == FM_MIXED ? dispatch_autotune<float>(st) : dispatch_autotune<double>(st);
+    if (rc) {
+      fm_destroy(st);
+      return rc;
+    }
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     fm_destroy(st);
@@ -760,6 +855,14 @@ int fm_set_stream(fm_state* st, void* stream) {
 }
 
 int fm_levels(const fm_state* st) { return st ? st->nlev : FM_EINVAL; }
+
+int fm_tuning(const fm_state* st, int level, int* variant, float* ms_per_variant) {
+  if (!st || level < 0 || level >= st->nlev) return FM_EINVAL;
+  if (variant) *variant = st->rbv[level];
+  if (ms_per_variant)
+    for (int v = 0; v < RB_NVAR; ++v) ms_per_variant[v] = st->rbt[level][v];
+  return FM_OK;
+}
 
 int fm_profile(fm_state* st, int enable) {
   if (!st) return FM_EINVAL;

@@ -50,6 +50,7 @@ struct fm_state {
   double* r64[fm::MAXU];          // float64 residual scratch (row-level entry points)
   double* partials;               // per-block partial sums (deterministic reductions)
   int nblk;                       // blocks of the reduction kernels
+  int sms;                        // multiprocessors of the device
   double* dscal;                  // device scalars
   double* hscal;                  // pinned host mirror of dscal
   double ce;                      // (J_e * 1) (CDFT)
@@ -61,6 +62,8 @@ struct fm_state {
   bool capturing;
   bool use_graph;                 // run fm_step as one CUDA graph launch
   bool fused_rb;                  // 2-D: one tiled launch per red-black sweep
+  int rbv[fm::MAXLEV];            // chosen variant of the fused sweep per level
+  float rbt[fm::MAXLEV][8];       // autotuner timings (ms per launch)
   int small_from;                 // first level handled by the single-block V-cycle
   void* ctl;                      // device control block of the step
   cudaGraph_t graph;

@@ -89,9 +89,12 @@ _SIGS = {
     "fm_batch_instance": (C.c_void_p, [C.c_void_p, C.c_int]),
     "fm_step_batch": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(fm_step_info)]),
     "fm_batch_launches": (C.c_longlong, [C.c_void_p]),
+    "fm_batch_tuning": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "fm_batch_time_smoother": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "fm_mass_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_double, C.c_void_p,
                                   C.c_void_p]),
     "fm_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "fm_tuning": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "fm_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                   C.POINTER(C.c_longlong)]),
 }
@@ -271,6 +274,20 @@ def fm_batch_launches(b):
     return lib().fm_batch_launches(b)
 
 
+def fm_batch_tuning(b, level):
+    v = C.c_int()
+    ms = (C.c_float * 8)()
+    _check(lib().fm_batch_tuning(b, level, C.byref(v), ms), "fm_batch_tuning")
+    return v.value, list(ms)
+
+
+def fm_batch_time_smoother(b, iters):
+    """(ms per launch, finest points per launch)."""
+    ms, pts = C.c_double(), C.c_longlong()
+    _check(lib().fm_batch_time_smoother(b, iters, C.byref(ms), C.byref(pts)), "fm_batch_time_smoother")
+    return ms.value, pts.value
+
+
 def fm_mass_noalloc(rho, h, out, stream=0):
     """Mass of a float64 CUDA tensor into a 1-element float64 CUDA tensor,
     without any device allocation by the library (see include/fm.h)."""
@@ -279,6 +296,14 @@ def fm_mass_noalloc(rho, h, out, stream=0):
     code = lib().fm_mass_noalloc(C.c_void_p(rho.data_ptr()), len(dims), n, C.c_double(h),
                                  C.c_void_p(out.data_ptr()), C.c_void_p(stream))
     _check(code, "fm_mass_noalloc")
+
+
+def fm_tuning(st, level):
+    """(chosen variant, [ms of the 8 variants]) of the fused sweep at `level`."""
+    v = C.c_int()
+    ms = (C.c_float * 8)()
+    _check(lib().fm_tuning(st, level, C.byref(v), ms), "fm_tuning")
+    return v.value, list(ms)
 
 
 def fm_profile(st, enable):
