@@ -106,6 +106,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def profiled_traffic(key, variant):
+    """DRAM bytes per launch from the committed ncu summary of this kernel, or
+    None when the variant timed here is not the profiled one."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            ent = json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+    if not ent or ent.get("variant") != variant:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -265,13 +278,7 @@ def run_ours(args):
     bytes_launch = words * 4 * N
     avg_ms = sm_ms / max(1, sm_n)
     achieved = bytes_launch / (avg_ms * 1e-3) / 1e9 if sm_n else None
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "smoother_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get("mixed_pfc512_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = profiled_traffic("k_smooth_rb2d_pfc512_level0", tuning["mixed"][0][0])
     f64_sm_ms, f64_sm_n = f64["prof"]
     f64_avg = f64_sm_ms / max(1, f64_sm_n)
     out = {
@@ -394,6 +401,7 @@ def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2):
                               "frac": round(gbs / peak, 4), "launch_ms": round(ms_sm, 5),
                               "algorithmic_bytes_per_launch": words * 4 * pts,
                               "timing": "20 back-to-back launches after a warm-up, CUDA events",
+                              "traffic": profiled_traffic("kb_smooth_rb2d_batch48", tune0[0]),
                               "autotuned_variant": tune0[0],
                               "variant_ms": [round(x, 4) for x in tune0[1]]},
     }
