@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "implicit steps/s at 512^2 (FP32-smoothed FAS, float64 residual 1e-10)"
 UNIT = "steps/s"
-WORKLOAD = "pfc512: 2-D PFC 512x512, eps=0.4, s=0.02, 4 nuclei, V(2,2) to 1e-10"
+WORKLOAD = "pfc512: 2-D PFC 512x512, eps=0.4, s=0.02, 4 nuclei, undamped, V(2,2) to 1e-10"
 
 
 def dist_env():
@@ -411,7 +411,7 @@ def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, wa
     n = list(reversed(rho.shape))
     stream = torch.cuda.current_stream().cuda_stream
     sol = fm.Solver(kind, n, prm["h"], dim=dim, alpha=prm.get("alpha", 0.0), nu=prm.get("nu", 0.0),
-                    precision=precision, tol=prm["tol"], w_damp=prm.get("w_damp", 0.0),
+                    precision=precision, tol=prm["tol"], w_damp=0.0,
                     delta=prm.get("delta", 0.0), gamma=prm["gamma"], stream=stream)
     rho_d = torch.from_numpy(rho).cuda()
     vel_d = [torch.from_numpy(v).cuda() for v in vel]
@@ -452,13 +452,13 @@ def secondary_all(torch, fm, inputs, flush, peak):
     out = {"batch48": secondary_batch48(torch, fm, inputs, flush, peak)}
     rho, vel, prm = inputs.cdft256()
     out["cdft256"] = {
-        "workload": "cdft256: 2-D CDFT 256x256, h=17/128, nu=2.362, s=0.02, w_damp 0.5, delta 1e-10",
+        "workload": "cdft256: 2-D CDFT 256x256, h=17/128, nu=2.362, s=0.02, delta 1e-10, undamped, V(2,2) to 1e-10",
         "mixed": secondary_single(torch, fm, flush, "cdft", rho, vel, prm, fm.FM_MIXED, 20),
         "fp64": secondary_single(torch, fm, flush, "cdft", rho, vel, prm, fm.FM_FP64, 10),
     }
     rho, vel, prm = inputs.pfc3d128()
     out["pfc3d128"] = {
-        "workload": "pfc3d128: 3-D PFC 128^3, eps=0.4, s=0.02, one nucleus, V(2,2) to 1e-10",
+        "workload": "pfc3d128: 3-D PFC 128^3, eps=0.4, s=0.02, one nucleus, undamped, V(2,2) to 1e-10",
         "mixed": secondary_single(torch, fm, flush, "pfc", rho, vel, prm, fm.FM_MIXED, 5, dim=3),
         "fp64": secondary_single(torch, fm, flush, "pfc", rho, vel, prm, fm.FM_FP64, 2, warmup=1, dim=3),
     }

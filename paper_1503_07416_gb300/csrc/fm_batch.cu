@@ -153,9 +153,9 @@ __global__ void __launch_bounds__(TPB) kb_resid(const WorkItem* items, int nitem
   if (idx < L.g.N) resid_point<T, KIND, 2>(L, P[inst], idx);
 }
 
-template <typename T, int NU>
-__global__ void __launch_bounds__(TPB) kb_restrict(const WorkItem* items, int nitems, const InstDev<T>* D,
-                                                   const Ctl* ctl, int level) {
+template <typename T, int KIND>
+__global__ void __launch_bounds__(TPB) kb_restrict_rhs(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                       const Phys<T>* P, const Ctl* ctl, int level) {
   FM_BATCH_HEAD();
   if (!inst_active(ctl, inst)) return;
   __shared__ Lvl<T> F, Cc;
@@ -163,19 +163,7 @@ __global__ void __launch_bounds__(TPB) kb_restrict(const WorkItem* items, int ni
   smem_copy(&Cc, &D[inst].lv[level + 1]);
   __syncthreads();
   const int idx = lb * TPB + threadIdx.x;
-  if (idx < Cc.g.N) restrict_point<T, NU, 2>(F, Cc, idx);
-}
-
-template <typename T, int KIND>
-__global__ void __launch_bounds__(TPB) kb_coarse_rhs(const WorkItem* items, int nitems, const InstDev<T>* D,
-                                                     const Phys<T>* P, const Ctl* ctl, int level) {
-  FM_BATCH_HEAD();
-  if (!inst_active(ctl, inst)) return;
-  __shared__ Lvl<T> L;
-  smem_copy(&L, &D[inst].lv[level]);
-  __syncthreads();
-  const int idx = lb * TPB + threadIdx.x;
-  if (idx < L.g.N) coarse_rhs_point<T, KIND, 2>(L, P[inst], idx);
+  if (idx < Cc.g.N) restrict_rhs_point<T, KIND, 2>(F, Cc, P[inst], idx);
 }
 
 template <typename T, int NU>
@@ -229,7 +217,7 @@ __global__ void __launch_bounds__(TPB) kb_resid64(const WorkItem* items, int nit
   FM_BATCH_HEAD();
   if (check_active && !inst_active(ctl, inst)) return;
   const InstDev<T>& I = D[inst];
-  resid64_body<KIND, 2, T>(I.F, I.O, I.g0, I.h0, P64[inst], I.partials, lb, I.nblk64);
+  resid64_tile_body<KIND, T>(I.F, I.O, I.g0, I.h0, P64[inst], I.partials, lb, I.nblk64);
 }
 
 // one block per instance: norm, cycles, status, active flag
@@ -377,19 +365,9 @@ struct Batch {
       I.small_from = st->small_from;
       // small levels and their shared-memory layout
       I.S.count = st->nlev - st->small_from;
-      int off = 0;
-      for (int q = 0; q < I.S.count; ++q) {
-        I.S.lv[q] = make_lvl<T>(st, st->small_from + q);
-        const int N = I.S.lv[q].g.N;
-        for (int u = 0; u < LY::NU; ++u) {
-          I.M.off_e[q][u] = off; off += N;
-          I.M.off_f[q][u] = off; off += N;
-          if (q + 1 < I.S.count) { I.M.off_r[q][u] = off; off += N; }
-          if (q > 0) { I.M.off_eh[q][u] = off; off += N; }
-        }
-      }
-      const size_t sm = (size_t)off * sizeof(T);
-      if (sm > b->small_smem) b->small_smem = sm;
+      for (int q = 0; q < I.S.count; ++q) I.S.lv[q] = make_lvl<T>(st, st->small_from + q);
+      const size_t smb = small_layout<T, KIND, 2>(I.S, I.M, SMALL_SMEM_MAX);
+      if (smb > b->small_smem) b->small_smem = smb;
       // injections (all coarse levels at once)
       for (int which = 0; which < 2; ++which) {
         InjAll<T>& A = which ? I.inj_cf : I.inj_rk;
@@ -581,13 +559,11 @@ struct Batch {
     for (int l = 0; l < b->maxdepth; ++l) {
       int rc = smooth(b, l, b->prm.nu1);
       if (rc) return rc;
-      const WList &wr = b->w_resid[l], &wq = b->w_restrict[l], &wc = b->w_crhs[l];
+      const WList &wr = b->w_resid[l], &wq = b->w_restrict[l];
       if (wr.n == 0) continue;
       kb_resid<T, KIND><<<wr.nblocks, TPB, 0, s>>>(it(b, wr), wr.n, D, P, b->ctl, l);
       FMB_LAUNCHED();
-      kb_restrict<T, LY::NU><<<wq.nblocks, TPB, 0, s>>>(it(b, wq), wq.n, D, b->ctl, l);
-      FMB_LAUNCHED();
-      kb_coarse_rhs<T, KIND><<<wc.nblocks, TPB, 0, s>>>(it(b, wc), wc.n, D, P, b->ctl, l + 1);
+      kb_restrict_rhs<T, KIND><<<wq.nblocks, TPB, 0, s>>>(it(b, wq), wq.n, D, P, b->ctl, l);
       FMB_LAUNCHED();
     }
     kb_small<T, KIND><<<b->count, SMALL_TPB, b->small_smem, s>>>(D, P, b->ctl, b->prm.nu1, b->prm.nu2,

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 #include <cmath>
+#include <cstring>
 
 #include "fm_state.h"
 
@@ -196,6 +197,46 @@ __device__ __forceinline__ void prolong_point(const Lvl<T>& F, const Lvl<T>& C, 
         }
     F.e[q][idx] += w * acc;
   }
+}
+
+// Coarse point idx: f_C = FW(r_F) + M_C(eh_C), e_C = eh_C = inject(e_F), in
+// one pass.  Every coarse coefficient is the injection of the fine one, so
+// M_C(eh) at the coarse point is evaluated on the fine arrays at the fine
+// indices 2I and 2I +- 2 with the coarse spacing.
+template <typename T, int KIND, int DIM>
+__device__ __forceinline__ void restrict_rhs_point(const Lvl<T>& F, const Lvl<T>& C, const Phys<T>& P, int idx) {
+  using LY = Layout<KIND, DIM>;
+  restrict_point<T, LY::NU, DIM>(F, C, idx);
+  int I, J, K;
+  coords(idx, C.g, I, J, K);
+  const int fnx = F.g.nx, fny = F.g.ny, fnz = F.g.nz;
+  const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
+  Nb n;
+  const int row = (fk * fny + fj) * fnx;
+  n.c = row + fi;
+  n.m[0] = row + (fi == 0 ? fnx - 2 : fi - 2);
+  n.p[0] = row + (fi + 2 >= fnx ? fi + 2 - fnx : fi + 2);
+  n.m[1] = n.c + (fj == 0 ? (fny - 2) * fnx : -2 * fnx);
+  n.p[1] = n.c + (fj + 2 >= fny ? (2 - fny) * fnx : 2 * fnx);
+  if constexpr (DIM == 3) {
+    const int pl = fnx * fny;
+    n.m[2] = n.c + (fk == 0 ? (fnz - 2) * pl : -2 * pl);
+    n.p[2] = n.c + (fk + 2 >= fnz ? (2 - fnz) * pl : 2 * pl);
+  } else {
+    n.m[2] = n.p[2] = n.c;
+  }
+  Lvl<T> V = F;
+  V.h = C.h;
+  T M[LY::NU];
+  applyM<T, KIND, DIM>(V, P, n, F.e, M);
+#pragma unroll
+  for (int q = 0; q < LY::NU; ++q) C.f[q][idx] += M[q];
+}
+
+template <typename T, int KIND, int DIM>
+__global__ void __launch_bounds__(TPB) k_restrict_rhs(Lvl<T> F, Lvl<T> C, Phys<T> P) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < C.g.N) restrict_rhs_point<T, KIND, DIM>(F, C, P, idx);
 }
 
 template <typename T, int KIND, int DIM>
@@ -517,7 +558,66 @@ struct SmallSmem {
   int off_f[MAXSMALL][MAXU];
   int off_r[MAXSMALL][MAXU];
   int off_eh[MAXSMALL][MAXU];
+  int off_rk[MAXSMALL];
+  int off_cr[MAXSMALL];
+  int off_om[MAXSMALL][3];
+  int off_cv[MAXSMALL][3];
+  int stage_coef;  // coefficients also in shared memory
 };
+
+// Levels of at most SMALL_WARP_N points are processed by warp 0 alone
+// (phases separated by __syncwarp instead of __syncthreads).
+constexpr int SMALL_WARP_N = 64;
+
+// One smoothing iteration set of level L by a group of threads: the whole
+// block (WARP = false) or warp 0 (WARP = true).
+template <typename T, int KIND, int DIM, bool WARP>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (WARP) __syncwarp();
+  else __syncthreads();
+}
+
+template <typename T, int KIND, int DIM, bool WARP>
+__device__ __forceinline__ void group_smooth(const Lvl<T>& L, const Phys<T>& P, int iters) {
+  const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
+  const int nth = WARP ? 32 : blockDim.x;
+  const int half = L.g.N / 2;
+  for (int it = 0; it < iters; ++it)
+    for (int color = 0; color < 2; ++color) {
+      for (int t = tid; t < half; t += nth) {
+        int i, j, k;
+        colour_point(t, color, L.g, i, j, k);
+        const Nb n = neighbours(i, j, k, L.g);
+        smooth_point<T, KIND, DIM>(L, P, n);
+      }
+      group_sync<T, KIND, DIM, WARP>();
+    }
+}
+
+// Down sweep of level l (smooth, residual, restriction, coarse right-hand side).
+template <typename T, int KIND, int DIM, bool WARP>
+__device__ __forceinline__ void group_down(const Lvl<T>& F, const Lvl<T>& C, const Phys<T>& P, int nu1) {
+  using LY = Layout<KIND, DIM>;
+  const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
+  const int nth = WARP ? 32 : blockDim.x;
+  group_smooth<T, KIND, DIM, WARP>(F, P, nu1);
+  for (int idx = tid; idx < F.g.N; idx += nth) resid_point<T, KIND, DIM>(F, P, idx);
+  group_sync<T, KIND, DIM, WARP>();
+  for (int idx = tid; idx < C.g.N; idx += nth) restrict_point<T, LY::NU, DIM>(F, C, idx);
+  group_sync<T, KIND, DIM, WARP>();
+  for (int idx = tid; idx < C.g.N; idx += nth) coarse_rhs_point<T, KIND, DIM>(C, P, idx);
+  group_sync<T, KIND, DIM, WARP>();
+}
+
+template <typename T, int KIND, int DIM, bool WARP>
+__device__ __forceinline__ void group_up(const Lvl<T>& F, const Lvl<T>& C, const Phys<T>& P, int nu2) {
+  using LY = Layout<KIND, DIM>;
+  const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
+  const int nth = WARP ? 32 : blockDim.x;
+  for (int idx = tid; idx < F.g.N; idx += nth) prolong_point<T, LY::NU, DIM>(F, C, idx);
+  group_sync<T, KIND, DIM, WARP>();
+  group_smooth<T, KIND, DIM, WARP>(F, P, nu2);
+}
 
 template <typename T, int KIND, int DIM>
 __device__ __forceinline__ void vcycle_small_smem_body(const SmallLv<T>& S, const SmallSmem<T>& M,
@@ -536,6 +636,14 @@ __device__ __forceinline__ void vcycle_small_smem_body(const SmallLv<T>& S, cons
         SL[l].r[q] = (q < LY::NU && l + 1 < nl) ? sm + M.off_r[l][q] : nullptr;
         SL[l].eh[q] = (q < LY::NU && l > 0) ? sm + M.off_eh[l][q] : nullptr;
       }
+      if (M.stage_coef) {
+        SL[l].rk = sm + M.off_rk[l];
+        SL[l].cr = sm + M.off_cr[l];
+        for (int d = 0; d < 3; ++d) {
+          SL[l].om[d] = d < LY::NOM ? sm + M.off_om[l][d] : nullptr;
+          SL[l].cv[d] = d < DIM ? sm + M.off_cv[l][d] : nullptr;
+        }
+      }
     }
   }
   __syncthreads();
@@ -547,27 +655,41 @@ __device__ __forceinline__ void vcycle_small_smem_body(const SmallLv<T>& S, cons
         SL[0].e[q][idx] = G.e[q][idx];
         SL[0].f[q][idx] = G.f[q][idx];
       }
+    if (M.stage_coef)
+      for (int l = 0; l < nl; ++l) {
+        const Lvl<T>& H = S.lv[l];
+        for (int idx = threadIdx.x; idx < H.g.N; idx += blockDim.x) {
+          sm[M.off_rk[l] + idx] = H.rk[idx];
+          sm[M.off_cr[l] + idx] = H.cr[idx];
+#pragma unroll
+          for (int d = 0; d < LY::NOM; ++d) sm[M.off_om[l][d] + idx] = H.om[d][idx];
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) sm[M.off_cv[l][d] + idx] = H.cv[d][idx];
+        }
+      }
   }
   __syncthreads();
-  for (int l = 0; l + 1 < nl; ++l) {
-    const Lvl<T>& F = SL[l];
-    const Lvl<T>& C = SL[l + 1];
-    block_smooth<T, KIND, DIM>(F, P, nu1);
-    for (int idx = threadIdx.x; idx < F.g.N; idx += blockDim.x) resid_point<T, KIND, DIM>(F, P, idx);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < C.g.N; idx += blockDim.x) restrict_point<T, LY::NU, DIM>(F, C, idx);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < C.g.N; idx += blockDim.x) coarse_rhs_point<T, KIND, DIM>(C, P, idx);
+  // first level handled by warp 0 alone
+  int lw = nl;
+  for (int l = 0; l < nl; ++l)
+    if (SL[l].g.N <= SMALL_WARP_N) {
+      lw = l;
+      break;
+    }
+  if (lw == 0) lw = 1;  // the entry level is always block-wide
+  const int nb = lw < nl - 1 ? lw : nl - 1;  // levels 0..nb-1 go down block-wide
+  for (int l = 0; l < nb; ++l) group_down<T, KIND, DIM, false>(SL[l], SL[l + 1], P, nu1);
+  if (lw >= nl) {
+    group_smooth<T, KIND, DIM, false>(SL[nl - 1], P, ncoarse);
+  } else {
+    if ((threadIdx.x >> 5) == 0) {
+      for (int l = lw; l + 1 < nl; ++l) group_down<T, KIND, DIM, true>(SL[l], SL[l + 1], P, nu1);
+      group_smooth<T, KIND, DIM, true>(SL[nl - 1], P, ncoarse);
+      for (int l = nl - 2; l >= lw; --l) group_up<T, KIND, DIM, true>(SL[l], SL[l + 1], P, nu2);
+    }
     __syncthreads();
   }
-  block_smooth<T, KIND, DIM>(SL[nl - 1], P, ncoarse);
-  for (int l = nl - 2; l >= 0; --l) {
-    const Lvl<T>& F = SL[l];
-    const Lvl<T>& C = SL[l + 1];
-    for (int idx = threadIdx.x; idx < F.g.N; idx += blockDim.x) prolong_point<T, LY::NU, DIM>(F, C, idx);
-    __syncthreads();
-    block_smooth<T, KIND, DIM>(F, P, nu2);
-  }
+  for (int l = nb - 1; l >= 0; --l) group_up<T, KIND, DIM, false>(SL[l], SL[l + 1], P, nu2);
   {
     const Lvl<T>& G = S.lv[0];
     for (int idx = threadIdx.x; idx < G.g.N; idx += blockDim.x)
@@ -887,6 +1009,105 @@ __device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out
   block_partials<LY::NU>(acc, partials, lb);
 }
 
+// 2-D float64 residual in 32 x 8 tiles: the quantities every point shares
+// with its neighbours -- |u|^2, rho^k u, rho^k v and the implicit chemical
+// potential (mu, or ln rho + 2 c_e rho) -- are computed once per point of the
+// tile and its one-point halo in shared memory, then N is evaluated on the
+// tile.  Block lb of nb walks tiles lb, lb + nb, ...; partial sums of r^2 as
+// in resid64_body (same per-block accumulation order on every run).
+constexpr int R64_TX = 32, R64_TY = 8;
+constexpr int R64_SW = R64_TX + 2, R64_SN = R64_SW * (R64_TY + 2);
+
+template <int KIND, typename T>
+__device__ __forceinline__ void resid64_tile_body(const Fields64& F, const Resid64Out& O, const Geo& G, double h,
+                                                  const Phys<double>& P, double* partials, int lb, int nb) {
+  using LY = Layout<KIND, 2>;
+  __shared__ double sQ[R64_SN], sM[R64_SN], sRU[R64_SN], sRV[R64_SN];
+  double acc[LY::NU];
+#pragma unroll
+  for (int q = 0; q < LY::NU; ++q) acc[q] = 0.0;
+  const double ih = 1.0 / h, ih2 = ih * ih;
+  const int nx = G.nx, ny = G.ny;
+  const int ntx = (nx + R64_TX - 1) / R64_TX;
+  const int ntiles = ntx * ((ny + R64_TY - 1) / R64_TY);
+  const double* const* g = F.g;
+  for (int tile = lb; tile < ntiles; tile += nb) {
+    const int x0 = (tile % ntx) * R64_TX, y0 = (tile / ntx) * R64_TY;
+    for (int t = threadIdx.x; t < R64_SN; t += blockDim.x) {
+      const int ly = t / R64_SW, lx = t - ly * R64_SW;
+      int gx = x0 + lx - 1, gy = y0 + ly - 1;
+      gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+      gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+      gx = gx >= nx ? gx % nx : gx;
+      gy = gy >= ny ? gy % ny : gy;
+      const int gi = gy * nx + gx;
+      const double u = g[1][gi], v = g[2][gi], rk = F.rho[gi];
+      sQ[t] = u * u + v * v;
+      sRU[t] = rk * u;
+      sRV[t] = rk * v;
+      if constexpr (KIND == KPFC) {
+        sM[t] = g[LY::IMU][gi];
+      } else {
+        const double r = g[0][gi];
+        sM[t] = log(r) + 2.0 * P.ce * r;
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < R64_TX * R64_TY; t += blockDim.x) {
+      const int ty = t / R64_TX, tx = t - ty * R64_TX;
+      const int i = x0 + tx, j = y0 + ty;
+      if (i < nx && j < ny) {
+        const int idx = j * nx + i;
+        const Nb n = neighbours(i, j, 0, G);
+        const int c = (ty + 1) * R64_SW + tx + 1;
+        const int xm = c - 1, xp = c + 1, ym = c - R64_SW, yp = c + R64_SW;
+        const double rkc = F.rho[idx];
+        double N[LY::NU];
+        N[0] = g[0][idx] + P.s * 0.25 * ih * ((sRU[xp] - sRU[xm]) + (sRV[yp] - sRV[ym]));
+        const double uc = g[1][idx], vc = g[2][idx];
+        const double w = F.om[0][idx];
+        const double wx0 = -w * vc, wx1 = w * uc;
+        const double lapu = (nbsum<double, 2>(g[1], n) - 4.0 * uc) * ih2;
+        const double lapv = (nbsum<double, 2>(g[2], n) - 4.0 * vc) * ih2;
+        N[1] = rkc * uc + 0.5 * P.sigma * P.s * rkc * wx0
+             + P.s * rkc * ih * (0.25 * (sQ[xp] - sQ[xm]) + 0.5 * (sM[xp] - sM[xm])) - 0.5 * P.s * P.gamma * lapu;
+        N[2] = rkc * vc + 0.5 * P.sigma * P.s * rkc * wx1
+             + P.s * rkc * ih * (0.25 * (sQ[yp] - sQ[ym]) + 0.5 * (sM[yp] - sM[ym])) - 0.5 * P.s * P.gamma * lapv;
+        if constexpr (KIND == KPFC) {
+          const double rc = g[0][idx];
+          const double psi = rc - 1.5;
+          const double kc = g[LY::IKA][idx];
+          const double lapk = (nbsum<double, 2>(g[LY::IKA], n) - 4.0 * kc) * ih2;
+          const double lapr = (nbsum<double, 2>(g[0], n) - 4.0 * rc) * ih2;
+          N[LY::IMU] = g[LY::IMU][idx] - psi * psi * psi / 3.0 - P.alpha * psi - lapk;
+          N[LY::IKA] = kc - lapr;
+        }
+#pragma unroll
+        for (int q = 0; q < LY::NU; ++q) {
+          const double r = F.S[q][idx] - N[q];
+          acc[q] += r * r;
+          if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = (T)r;
+          if (O.e0[q]) static_cast<T*>(O.e0[q])[idx] = T(0);
+          if (O.r64[q]) O.r64[q][idx] = r;
+        }
+        if (O.cr32) {
+          O.cr32[idx] = (float)g[0][idx];
+          O.cv32[0][idx] = (float)uc;
+          O.cv32[1][idx] = (float)vc;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  block_partials<LY::NU>(acc, partials, lb);
+}
+
+template <int KIND, typename T>
+__global__ void __launch_bounds__(TPB) k_resid64_tile(Fields64 F, Resid64Out O, Geo G, double h,
+                                                      Phys<double> P, double* partials) {
+  resid64_tile_body<KIND, T>(F, O, G, h, P, partials, blockIdx.x, gridDim.x);
+}
+
 template <int KIND, int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_resid64(Fields64 F, Resid64Out O, Geo G, double h,
                                                  Phys<double> P, double* partials) {
@@ -1045,6 +1266,33 @@ __global__ void __launch_bounds__(TPB) k_energy(const double* rho, Vel3 vel3,
     }
   }
   block_partials<NQ>(acc, partials, blockIdx.x);
+}
+
+// Shared-memory layout of the small-level V-cycle; returns the bytes needed.
+template <typename T, int KIND, int DIM>
+static size_t small_layout(const SmallLv<T>& S, SmallSmem<T>& M, size_t limit) {
+  using LY = Layout<KIND, DIM>;
+  memset(&M, 0, sizeof(M));
+  int off = 0;
+  for (int q = 0; q < S.count; ++q) {
+    const int N = S.lv[q].g.N;
+    for (int u = 0; u < LY::NU; ++u) {
+      M.off_e[q][u] = off; off += N;
+      M.off_f[q][u] = off; off += N;
+      if (q + 1 < S.count) { M.off_r[q][u] = off; off += N; }
+      if (q > 0) { M.off_eh[q][u] = off; off += N; }
+    }
+  }
+  const int base = off;
+  for (int q = 0; q < S.count; ++q) {
+    const int N = S.lv[q].g.N;
+    M.off_rk[q] = off; off += N;
+    M.off_cr[q] = off; off += N;
+    for (int d = 0; d < LY::NOM; ++d) { M.off_om[q][d] = off; off += N; }
+    for (int d = 0; d < DIM; ++d) { M.off_cv[q][d] = off; off += N; }
+  }
+  M.stage_coef = (size_t)off * sizeof(T) <= limit ? 1 : 0;
+  return (size_t)(M.stage_coef ? off : base) * sizeof(T);
 }
 
 // --------------------------------------------------------------------------

@@ -306,7 +306,10 @@ struct Solver {
     cudaStream_t s = st->stream;
     Fields64 F = make_fields(st);
     Resid64Out O = resid_out(st, true, nullptr);
-    k_resid64<KIND, DIM, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
+    if constexpr (DIM == 2)
+      k_resid64_tile<KIND, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
+    else
+      k_resid64<KIND, DIM, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
     FM_LAUNCHED();
     const double w = (DIM == 3) ? h * h * h : h * h;
     k_norm_ctl<LY::NU><<<1, TPB, 0, s>>>(st->partials, st->nblk, w, (Ctl*)st->ctl, st->prm.tol,
@@ -323,7 +326,10 @@ struct Solver {
     cudaStream_t s = st->stream;
     Fields64 F = make_fields(st);
     Resid64Out O = resid_out(st, false, r64);
-    k_resid64<KIND, DIM, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
+    if constexpr (DIM == 2)
+      k_resid64_tile<KIND, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
+    else
+      k_resid64<KIND, DIM, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
     FM_LAUNCHED();
     const double w = (DIM == 3) ? h * h * h : h * h;
     k_norm_final<LY::NU><<<1, TPB, 0, s>>>(st->partials, st->nblk, w, st->dscal);
@@ -368,20 +374,8 @@ struct Solver {
       SmallLv<T> S;
       S.count = st->nlev - l;
       for (int q = 0; q < S.count; ++q) S.lv[q] = make_lvl<T>(st, l + q);
-      // shared-memory layout of the small levels' e, f, r, eh
       SmallSmem<T> M;
-      memset(&M, 0, sizeof(M));
-      int off = 0;
-      for (int q = 0; q < S.count; ++q) {
-        const int N = S.lv[q].g.N;
-        for (int u = 0; u < LY::NU; ++u) {
-          M.off_e[q][u] = off; off += N;
-          M.off_f[q][u] = off; off += N;
-          if (q + 1 < S.count) { M.off_r[q][u] = off; off += N; }
-          if (q > 0) { M.off_eh[q][u] = off; off += N; }
-        }
-      }
-      const size_t smem = (size_t)off * sizeof(T);
+      const size_t smem = small_layout<T, KIND, DIM>(S, M, SMALL_SMEM_MAX);
       if (smem <= SMALL_SMEM_MAX && S.lv[0].g.N <= SMALL_SMEM_N) {
         static bool attr = false;
         if (!attr) {
@@ -403,9 +397,7 @@ struct Solver {
     Lvl<T> C = make_lvl<T>(st, l + 1);
     k_resid<T, KIND, DIM><<<nblocks(F.g.N), TPB, 0, s>>>(F, P);
     FM_LAUNCHED();
-    k_restrict<T, LY::NU, DIM><<<nblocks(C.g.N), TPB, 0, s>>>(F, C);
-    FM_LAUNCHED();
-    k_coarse_rhs<T, KIND, DIM><<<nblocks(C.g.N), TPB, 0, s>>>(C, P);
+    k_restrict_rhs<T, KIND, DIM><<<nblocks(C.g.N), TPB, 0, s>>>(F, C, P);
     FM_LAUNCHED();
     rc = vcycle(st, l + 1, P);
     if (rc) return rc;
@@ -684,7 +676,7 @@ void fm_default_params(fm_params* p) {
   p->nu2 = 2;
   p->max_cycles = 50;
   p->coarsest = 4;
-  p->ncoarse = 16;
+  p->ncoarse = 4;
   p->precision = FM_FP64;
 }
 

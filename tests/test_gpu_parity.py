@@ -329,3 +329,19 @@ def test_fused_tile_smoother_matches_two_colour_launches(kind, precision, monkey
     (rb, vb), cb = res[1]
     assert ca == cb
     assert rel(ra, rb) <= 1e-12 and all(rel(a, b) <= 1e-12 for a, b in zip(va, vb))
+
+
+@pytest.mark.parametrize("kind,n", [("pfc", 32), ("pfc", 16), ("cdft", 32)])
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_whole_cycle_in_one_block(kind, n, precision):
+    """Grids of at most 1024 points run the whole V-cycle (32^2 -> 4^2) in the
+    single-block kernel, its 8^2 and 4^2 levels in one warp."""
+    rng = np.random.default_rng(n)
+    if kind == "pfc":
+        rho = 0.8 + 0.05 * rng.uniform(-1, 1, (n, n))
+        prm = dict(kind="pfc", dim=2, h=0.9, dt=0.05, alpha=0.6, tol=1e-12)
+    else:
+        rho = 0.3 + 0.05 * rng.uniform(0, 1, (n, n))
+        prm = dict(kind="cdft", dim=2, h=17.0 / 32, dt=0.02, nu=2.362, delta=1e-10, tol=1e-12)
+    vel = [0.05 * rng.standard_normal((n, n)) for _ in range(2)]
+    _compare_step(rho, vel, prm, precision, w_damp=0.0, steps=2)
