@@ -407,7 +407,7 @@ def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2):
     }
 
 
-def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, warmup=2, dim=2):
+def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, warmup=2, dim=2, smoother=False):
     n = list(reversed(rho.shape))
     stream = torch.cuda.current_stream().cuda_stream
     sol = fm.Solver(kind, n, prm["h"], dim=dim, alpha=prm.get("alpha", 0.0), nu=prm.get("nu", 0.0),
@@ -421,10 +421,25 @@ def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, wa
     sol.set_fields(rho_d, vel_d)
     torch.cuda.synchronize()
     times, infos = _timed_steps(torch, lambda: sol.step(prm["dt"]), steps, flush)
+    out = {"steps_per_s": round(steps / (total_ms(times) / 1e3), 3), "ms_per_step": round(total_ms(times) / steps, 4),
+           "cycles_mean": round(sum(i.cycles for i in infos) / len(infos), 3)}
+    if smoother:
+        ms, n = time_smoother(torch, fm, sol, rho_d, vel_d, prm["dt"], 2, flush)
+        per = ms / max(1, n)
+        # finest level, one launch: one colour of the 3-D sweep (half the points)
+        # or one full fused 2-D sweep
+        pts = rho.size // 2 if dim == 3 else rho.size
+        words = 26 if dim == 3 else 20  # 3-D PFC: e 6, f 6, rho^k, omega 3, rho, u 3 read; e 6 written
+        wb = 4 if precision == fm.FM_MIXED else 8
+        out["smoother"] = {"launch_ms": round(per, 5), "points_per_launch": pts,
+                           "achieved_gbs": round(words * wb * pts / (per * 1e-3) / 1e9, 1),
+                           "algorithmic_bytes_per_launch": words * wb * pts}
     sol.close()
-    total = sum(times)
-    return {"steps_per_s": round(steps / (total / 1e3), 3), "ms_per_step": round(total / steps, 4),
-            "cycles_mean": round(sum(i.cycles for i in infos) / len(infos), 3)}
+    return out
+
+
+def total_ms(times):
+    return sum(times)
 
 
 def profile_batch(count):
@@ -459,7 +474,7 @@ def secondary_all(torch, fm, inputs, flush, peak):
     rho, vel, prm = inputs.pfc3d128()
     out["pfc3d128"] = {
         "workload": "pfc3d128: 3-D PFC 128^3, eps=0.4, s=0.02, one nucleus, undamped, V(2,2) to 1e-10",
-        "mixed": secondary_single(torch, fm, flush, "pfc", rho, vel, prm, fm.FM_MIXED, 5, dim=3),
+        "mixed": secondary_single(torch, fm, flush, "pfc", rho, vel, prm, fm.FM_MIXED, 5, dim=3, smoother=True),
         "fp64": secondary_single(torch, fm, flush, "pfc", rho, vel, prm, fm.FM_FP64, 2, warmup=1, dim=3),
     }
     return out

@@ -87,7 +87,7 @@ typedef struct {
                        (discrete_b)]; -1 reproduces the App. G printing */
     int nu1, nu2;   /* pre- and post-smoothing iterations [2, 2] */
     int max_cycles; /* [50] */
-    int coarsest;   /* coarsen while every n[d]/2 >= coarsest and is even [4] */
+    int coarsest;   /* coarsen while every n[d]/2 >= coarsest and is even [16] */
     int ncoarse;    /* smoothing iterations on the coarsest grid [4] */
     int precision;  /* FM_FP64 or FM_MIXED [FM_FP64] */
 } fm_params;

@@ -675,7 +675,7 @@ void fm_default_params(fm_params* p) {
   p->nu1 = 2;
   p->nu2 = 2;
   p->max_cycles = 50;
-  p->coarsest = 4;
+  p->coarsest = 16;
   p->ncoarse = 4;
   p->precision = FM_FP64;
 }

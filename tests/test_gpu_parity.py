@@ -199,7 +199,7 @@ def test_transfer_rows():
     for shape in [(16, 24), (8, 8, 8)]:
         dim = len(shape)
         prm = dict(kind="pfc", dim=dim, h=0.5, dt=0.01, alpha=0.6)
-        sol = gpu_solver(np.zeros(shape), prm)
+        sol = gpu_solver(np.zeros(shape), prm, coarsest=2)
         fine = rng.standard_normal(shape)
         coarse = np.empty(tuple(x // 2 for x in shape))
         fm.fm_restrict(sol.handle, fine, coarse)
