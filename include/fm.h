@@ -226,10 +226,10 @@ int fm_batch_time_smoother(fm_batch* b, int iters, double* ms_per_launch, long l
 /* ---- Measurement (no counterpart in the paper). ---- */
 
 /* Variant of the 2-D fused red-black sweep the autotuner chose for `level`
- * at fm_create (bit 2: 64x8 tiles instead of 32x16; bit 1: right-hand side
+ * at fm_create (v >> 2: tile 32x16, 64x8 or 32x32; bit 1: right-hand side
  * staged in shared memory; bit 0: persistent double-buffered blocks), and its
- * timings of all 8 variants in ms per sweep (ms_per_variant may be null; 0 for
- * levels that were not tuned).  Setting the environment variable
+ * timings of all 12 variants in ms per sweep (ms_per_variant may be null; 0
+ * for levels that were not tuned).  Setting the environment variable
  * FM_RB_VARIANT=v before fm_create fixes the variant (no timing). */
 int fm_tuning(const fm_state* st, int level, int* variant, float* ms_per_variant);
 

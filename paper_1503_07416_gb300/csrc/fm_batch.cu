@@ -88,7 +88,7 @@ __device__ __forceinline__ void smem_copy(S* dst, const S* src) {
 // ..., two shared-memory buffers, the next tile's copies in flight while the
 // current one is computed; otherwise one tile per block.
 template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
-__global__ void __launch_bounds__(RB_THREADS) kb_smooth_rb2d(const WorkItem* items, int nitems, const InstDev<T>* D,
+__global__ void __launch_bounds__(rb_threads(TX, TY)) kb_smooth_rb2d(const WorkItem* items, int nitems, const InstDev<T>* D,
                                                              const Phys<T>* P, const Ctl* ctl, int level,
                                                              int ntiles) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(RB_THREADS) kb_smooth_rb2d(const WorkItem* ite
     fetch(t, 0);
     cp_async_wait_all();
     __syncthreads();
-    if (s_inst[0] >= 0) rb2d_compute<T, KIND, TX, TY, SF>(Gs[0], P[s_inst[0]], buf0, s_x0[0], s_y0[0]);
+    if (s_inst[0] >= 0) rb2d_compute<T, KIND, TX, TY, SF>(Gs[0], P[s_inst[0]], 0, s_x0[0], s_y0[0]);
   } else {
     fetch(t, 0);
     for (int k = 0;; ++k) {
@@ -132,8 +132,7 @@ __global__ void __launch_bounds__(RB_THREADS) kb_smooth_rb2d(const WorkItem* ite
       __syncthreads();
       const int slot = k & 1;
       if (s_inst[slot] >= 0)
-        rb2d_compute<T, KIND, TX, TY, SF>(Gs[slot], P[s_inst[slot]], buf0 + slot * BUFSTRIDE, s_x0[slot],
-                                          s_y0[slot]);
+        rb2d_compute<T, KIND, TX, TY, SF>(Gs[slot], P[s_inst[slot]], slot * BUFSTRIDE, s_x0[slot], s_y0[slot]);
       __syncthreads();
       if (!next) break;
       t = tn;
@@ -299,10 +298,10 @@ struct fm_batch {
   // work lists
   std::vector<WorkItem> hitems;
   WList w_fine, w_resid64, w_inject;
-  WList w_smooth[2][MAXLEV];  // per tile shape (32x16, 64x8)
+  WList w_smooth[3][MAXLEV];  // per tile shape (32x16, 64x8, 32x32)
   WList w_resid[MAXLEV], w_restrict[MAXLEV], w_crhs[MAXLEV], w_prolong[MAXLEV];
   int rbv[MAXLEV];           // chosen fused-sweep variant per level
-  float rbt[MAXLEV][8];      // autotuner timings (ms per launch)
+  float rbt[MAXLEV][12];     // autotuner timings (ms per launch)
   // graph
   cudaStream_t stream;
   cudaStream_t user_stream;
@@ -440,14 +439,14 @@ struct Batch {
     }
     b->w_inject = add_list(b, v);
     for (int l = 0; l < b->maxdepth; ++l) {
-      std::vector<std::pair<int, int>> ts[2], rs, rr, cr, pr;
-      std::vector<int> aux[2];
+      std::vector<std::pair<int, int>> ts[3], rs, rr, cr, pr;
+      std::vector<int> aux[3];
       for (int i = 0; i < b->count; ++i) {
         fm_state* st = b->inst[i];
         if (st->small_from <= l) continue;
         const Geo g = st->lv[l].g, gc = st->lv[l + 1].g;
-        for (int sh = 0; sh < 2; ++sh) {
-          const int TX = sh ? 64 : 32, TY = sh ? 8 : 16;
+        for (int sh = 0; sh < 3; ++sh) {
+          const int TX = sh == 1 ? 64 : 32, TY = sh == 0 ? 16 : (sh == 1 ? 8 : 32);
           const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
           ts[sh].push_back({i, ntx * nty});
           aux[sh].push_back(ntx);
@@ -457,7 +456,7 @@ struct Batch {
         cr.push_back({i, nblocks(gc.N)});
         pr.push_back({i, nblocks(g.N)});
       }
-      for (int sh = 0; sh < 2; ++sh) b->w_smooth[sh][l] = add_list(b, ts[sh], &aux[sh]);
+      for (int sh = 0; sh < 3; ++sh) b->w_smooth[sh][l] = add_list(b, ts[sh], &aux[sh]);
       b->w_resid[l] = add_list(b, rs);
       b->w_restrict[l] = add_list(b, rr);
       b->w_crhs[l] = add_list(b, cr);
@@ -470,18 +469,19 @@ struct Batch {
   template <int TX, int TY, bool SF, bool PIPE>
   static int launch_v(fm_batch* b, int l) {
     constexpr size_t smem = rb_smem_bytes<T, KIND, TX, TY, SF, PIPE>();
+    if (smem + 4096 > (size_t)b->inst[0]->smem_optin) return FM_EINVAL;  // does not fit: skip
     static int per_sm = 0;
     if (!per_sm) {
       FMB_CUDA(cudaFuncSetAttribute(kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       FMB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>,
-                                                             RB_THREADS, smem));
+                                                             rb_threads(TX, TY), smem));
       if (per_sm < 1) per_sm = 1;
     }
-    const WList& w = b->w_smooth[TX == 64 ? 1 : 0][l];
+    const WList& w = b->w_smooth[TX == 64 ? 1 : (TY == 32 ? 2 : 0)][l];
     int grid = w.nblocks;
     if (PIPE && grid > per_sm * b->inst[0]->sms) grid = per_sm * b->inst[0]->sms;
-    kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE><<<grid, RB_THREADS, smem, b->stream>>>(
+    kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE><<<grid, rb_threads(TX, TY), smem, b->stream>>>(
         it(b, w), w.n, (const InstDev<T>*)b->D, (const Phys<T>*)b->P, b->ctl, l, w.nblocks);
     FMB_LAUNCHED();
     return FM_OK;
@@ -496,7 +496,11 @@ struct Batch {
       case 4: return launch_v<64, 8, false, false>(b, l);
       case 5: return launch_v<64, 8, false, true>(b, l);
       case 6: return launch_v<64, 8, true, false>(b, l);
-      default: return launch_v<64, 8, true, true>(b, l);
+      case 7: return launch_v<64, 8, true, true>(b, l);
+      case 8: return launch_v<32, 32, false, false>(b, l);
+      case 9: return launch_v<32, 32, false, true>(b, l);
+      case 10: return launch_v<32, 32, true, false>(b, l);
+      default: return launch_v<32, 32, true, true>(b, l);
     }
   }
 
@@ -529,6 +533,10 @@ struct Batch {
       float best = 1e30f;
       for (int v = 0; v < RB_NVAR && rc == FM_OK; ++v) {
         rc = launch_variant(b, v, l);
+        if (rc == FM_EINVAL) {  // does not fit in shared memory: skip
+          rc = FM_OK;
+          continue;
+        }
         if (rc) break;
         if (cudaEventRecord(e0, b->stream) != cudaSuccess) { rc = FM_ECUDA; break; }
         for (int k = 0; k < 3 && rc == FM_OK; ++k) rc = launch_variant(b, v, l);

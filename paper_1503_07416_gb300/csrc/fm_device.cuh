@@ -20,28 +20,29 @@ static inline int nblocks(long long work) { return (int)((work + TPB - 1) / TPB)
 // --------------------------------------------------------------------------
 // Smoother point update (correction form)
 // --------------------------------------------------------------------------
-// Point-block update of one point; the right-hand side f and omega^k are
-// read through (Fr, Om) at index fc, everything else through L at n.
-template <typename T, int KIND, int DIM>
-__device__ __forceinline__ void smooth_point_ex(const Lvl<T>& L, const Phys<T>& P, const Nb& n,
-                                                T* const* Fr, const T* const* Om, int fc) {
+// Point-block update of one point, written against an accessor A that
+// provides e(q, i) / set_e(q, i, v), rk(i), cr(i), cv(d, i), f(q, fc),
+// om(d, fc) and h (A is a level descriptor in any memory, or a shared-memory
+// tile with compile-time strides).  Neighbours are at n.m / n.p; the
+// right-hand side and omega^k are read at index fc.
+template <typename T, int KIND, int DIM, class A>
+__device__ __forceinline__ void smooth_point_a(const A& a, const Phys<T>& P, const Nb& n, int fc) {
   using LY = Layout<KIND, DIM>;
-  T* const* E = L.e;
-  const T ih = T(1) / L.h;
+  const T ih = T(1) / a.h();
   const T ih2 = ih * ih;
   const int c = n.c;
-  const T rkc = L.rk[c];
-  const T crc = L.cr[c];
+  const T rkc = a.rk(c);
+  const T crc = a.cr(c);
   T eo[LY::NU];
 #pragma unroll
-  for (int q = 0; q < LY::NU; ++q) eo[q] = E[q][c];
+  for (int q = 0; q < LY::NU; ++q) eo[q] = a.e(q, c);
 
   // rho from the continuity row (neighbour velocities only)
   T div = 0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d)
-    div += L.rk[n.p[d]] * E[1 + d][n.p[d]] - L.rk[n.m[d]] * E[1 + d][n.m[d]];
-  T er = Fr[0][fc] - P.s * T(0.25) * ih * div;
+    div += a.rk(n.p[d]) * a.e(1 + d, n.p[d]) - a.rk(n.m[d]) * a.e(1 + d, n.m[d]);
+  T er = a.f(0, fc) - P.s * T(0.25) * ih * div;
   {
     const T x = crc + er;
     if (x <= T(0)) er = sqrt_t(x * x + P.delta * P.delta) - crc;  // Sec. 6 projection
@@ -49,13 +50,36 @@ __device__ __forceinline__ void smooth_point_ex(const Lvl<T>& L, const Phys<T>& 
   T eg[LY::NU];
   eg[0] = er;
 
+  auto nbs = [&](int q) {
+    T s = a.e(q, n.m[0]) + a.e(q, n.p[0]) + a.e(q, n.m[1]) + a.e(q, n.p[1]);
+    if constexpr (DIM == 3) s += a.e(q, n.m[2]) + a.e(q, n.p[2]);
+    return s;
+  };
+  auto qc = [&](int idx) {
+    T q = 0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const T e = a.e(1 + d, idx);
+      q += e * (T(2) * a.cv(d, idx) + e);
+    }
+    return q;
+  };
+  auto mc = [&](int idx) {
+    if constexpr (KIND == KPFC) {
+      return a.e(LY::IMU, idx);
+    } else {
+      const T e = a.e(0, idx);
+      return log1p_t(e / a.cr(idx)) + T(2) * P.ce * e;
+    }
+  };
+
   if constexpr (KIND == KPFC) {
     // kappa = f5 + Lap_h e_rho with the new centre value
-    const T ek = Fr[LY::IKA][fc] + (nbsum<T, DIM>(E[0], n) - T(2 * DIM) * er) * ih2;
+    const T ek = a.f(LY::IKA, fc) + (nbs(0) - T(2 * DIM) * er) * ih2;
     // mu = f4 + [(p+e)^3 - p^3]/3 + alpha e + Lap_h e_kappa (exact: the block is triangular)
     const T psi = crc - T(1.5);
-    const T em = Fr[LY::IMU][fc] + er * (psi * psi + psi * er + er * er / T(3)) + P.alpha * er
-               + (nbsum<T, DIM>(E[LY::IKA], n) - T(2 * DIM) * ek) * ih2;
+    const T em = a.f(LY::IMU, fc) + er * (psi * psi + psi * er + er * er / T(3)) + P.alpha * er
+               + (nbs(LY::IKA) - T(2 * DIM) * ek) * ih2;
     eg[LY::IKA] = ek;
     eg[LY::IMU] = em;
   }
@@ -63,33 +87,56 @@ __device__ __forceinline__ void smooth_point_ex(const Lvl<T>& L, const Phys<T>& 
   // velocity block: (a I + [b]_x) e_u = rhs
   T rhs[3];
 #pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    const T dq = qcorr<T, DIM>(E, L.cv, n.p[a]) - qcorr<T, DIM>(E, L.cv, n.m[a]);
-    const T dm = mcorr<T, KIND, DIM>(E, L.cr, n.p[a], P.ce) - mcorr<T, KIND, DIM>(E, L.cr, n.m[a], P.ce);
-    rhs[a] = Fr[1 + a][fc] - P.s * rkc * ih * (T(0.25) * dq + T(0.5) * dm)
-           + T(0.5) * P.s * P.gamma * ih2 * nbsum<T, DIM>(E[1 + a], n);
+  for (int d = 0; d < DIM; ++d) {
+    const T dq = qc(n.p[d]) - qc(n.m[d]);
+    const T dm = mc(n.p[d]) - mc(n.m[d]);
+    rhs[d] = a.f(1 + d, fc) - P.s * rkc * ih * (T(0.25) * dq + T(0.5) * dm)
+           + T(0.5) * P.s * P.gamma * ih2 * nbs(1 + d);
   }
-  const T A = rkc + P.s * P.gamma * T(DIM) * ih2;
+  const T Ad = rkc + P.s * P.gamma * T(DIM) * ih2;
   const T bs = T(0.5) * P.sigma * P.s * rkc;
   if constexpr (DIM == 2) {
-    const T b = bs * Om[0][fc];
-    const T inv = T(1) / (A * A + b * b);
-    eg[1] = (A * rhs[0] + b * rhs[1]) * inv;
-    eg[2] = (A * rhs[1] - b * rhs[0]) * inv;
+    const T b = bs * a.om(0, fc);
+    const T inv = T(1) / (Ad * Ad + b * b);
+    eg[1] = (Ad * rhs[0] + b * rhs[1]) * inv;
+    eg[2] = (Ad * rhs[1] - b * rhs[0]) * inv;
   } else {
     T b[3], bx[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) b[d] = bs * Om[d][fc];
+    for (int d = 0; d < 3; ++d) b[d] = bs * a.om(d, fc);
     cross<T, 3>(b, rhs, bx);
     const T bdy = b[0] * rhs[0] + b[1] * rhs[1] + b[2] * rhs[2];
-    const T inv = T(1) / (A * (A * A + b[0] * b[0] + b[1] * b[1] + b[2] * b[2]));
+    const T inv = T(1) / (Ad * (Ad * Ad + b[0] * b[0] + b[1] * b[1] + b[2] * b[2]));
 #pragma unroll
-    for (int d = 0; d < 3; ++d) eg[1 + d] = (A * A * rhs[d] - A * bx[d] + bdy * b[d]) * inv;
+    for (int d = 0; d < 3; ++d) eg[1 + d] = (Ad * Ad * rhs[d] - Ad * bx[d] + bdy * b[d]) * inv;
   }
   // damping of the whole point block (App. G.3)
   const T w = P.w;
 #pragma unroll
-  for (int q = 0; q < LY::NU; ++q) E[q][c] = (T(1) - w) * eg[q] + w * eo[q];
+  for (int q = 0; q < LY::NU; ++q) a.set_e(q, c, (T(1) - w) * eg[q] + w * eo[q]);
+}
+
+// Accessor through a level descriptor; f and omega through (Fr, Om).
+template <typename T>
+struct LvlAcc {
+  const Lvl<T>& L;
+  T* const* Fr;
+  const T* const* Om;
+  __device__ __forceinline__ T h() const { return L.h; }
+  __device__ __forceinline__ T e(int q, int i) const { return L.e[q][i]; }
+  __device__ __forceinline__ void set_e(int q, int i, T v) const { L.e[q][i] = v; }
+  __device__ __forceinline__ T rk(int i) const { return L.rk[i]; }
+  __device__ __forceinline__ T cr(int i) const { return L.cr[i]; }
+  __device__ __forceinline__ T cv(int d, int i) const { return L.cv[d][i]; }
+  __device__ __forceinline__ T f(int q, int i) const { return Fr[q][i]; }
+  __device__ __forceinline__ T om(int d, int i) const { return Om[d][i]; }
+};
+
+template <typename T, int KIND, int DIM>
+__device__ __forceinline__ void smooth_point_ex(const Lvl<T>& L, const Phys<T>& P, const Nb& n,
+                                                T* const* Fr, const T* const* Om, int fc) {
+  LvlAcc<T> a{L, Fr, Om};
+  smooth_point_a<T, KIND, DIM>(a, P, n, fc);
 }
 
 template <typename T, int KIND, int DIM>
@@ -283,7 +330,40 @@ __global__ void __launch_bounds__(TPB) k_prolong(Lvl<T> F, Lvl<T> C) {
 // tile in with cp.async (global -> shared, no register staging) while it
 // computes the current one.
 constexpr int RB_H = 2;
-constexpr int RB_THREADS = 256;
+// Threads of a tile block (measured: 256 beats sizing the block to the red
+// pass, which leaves fewer blocks per SM).
+__host__ __device__ constexpr int rb_threads(int tx, int ty) { return tx * ty >= 1024 ? 512 : 256; }
+
+// The dynamic shared memory of the tile kernels (every extern __shared__
+// array of a kernel starts at the same address).
+extern __shared__ __align__(16) unsigned char fm_dyn_smem[];
+
+// Accessor of a staged tile: arrays e[NU], rk, cr, cv0, cv1 and (SF) f[NU],
+// omega at compile-time strides SN from element `base` of the dynamic shared
+// memory, so every access is a shared-memory load; without SF the right-hand
+// side and omega are read from the level in global memory.
+template <typename T, int KIND, int SN, bool SF>
+struct TileAcc {
+  static constexpr int NU = Layout<KIND, 2>::NU;
+  int base;
+  T hh;
+  const Lvl<T>* G;
+  __device__ __forceinline__ T* sm() const { return reinterpret_cast<T*>(fm_dyn_smem) + base; }
+  __device__ __forceinline__ T h() const { return hh; }
+  __device__ __forceinline__ T e(int q, int i) const { return sm()[q * SN + i]; }
+  __device__ __forceinline__ void set_e(int q, int i, T v) const { sm()[q * SN + i] = v; }
+  __device__ __forceinline__ T rk(int i) const { return sm()[NU * SN + i]; }
+  __device__ __forceinline__ T cr(int i) const { return sm()[(NU + 1) * SN + i]; }
+  __device__ __forceinline__ T cv(int d, int i) const { return sm()[(NU + 2 + d) * SN + i]; }
+  __device__ __forceinline__ T f(int q, int i) const {
+    if constexpr (SF) return sm()[(NU + 4 + q) * SN + i];
+    else return G->f[q][i];
+  }
+  __device__ __forceinline__ T om(int d, int i) const {
+    if constexpr (SF) return sm()[(2 * NU + 4) * SN + i];
+    else return G->om[d][i];
+  }
+};
 
 // Shared-memory tile: rows of SW = TX + 2*XO values (the tile starts at
 // column XO = 4 so that every row begins on a 16-byte boundary in global and
@@ -377,31 +457,14 @@ __device__ __forceinline__ void rb2d_issue(const Lvl<T>& G, T* buf, int x0, int 
   }
 }
 
-// Red pass on tile + ring 1, black pass on the tile, write-back of the tile.
+// Red pass on tile + ring 1, black pass on the tile, write-back of the tile;
+// the staged tile starts at element `base` of the dynamic shared memory.
 template <typename T, int KIND, int TX, int TY, bool SF>
-__device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, T* buf, int x0, int y0) {
+__device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, int base, int x0, int y0) {
   using Gm = RBGeom<TX, TY>;
   constexpr int NU = Layout<KIND, 2>::NU;
   constexpr int SN = Gm::SN, SW = Gm::SW;
-  Lvl<T> L;
-  L.g = G.g;
-  L.h = G.h;
-  T* Fs[MAXU];
-  const T* Os[3];
-#pragma unroll
-  for (int q = 0; q < MAXU; ++q) {
-    L.e[q] = q < NU ? buf + q * SN : nullptr;
-    L.f[q] = L.r[q] = L.eh[q] = nullptr;
-    Fs[q] = q < NU ? buf + (NU + 4 + q) * SN : nullptr;
-  }
-  L.rk = buf + (NU + 0) * SN;
-  L.cr = buf + (NU + 1) * SN;
-  L.cv[0] = buf + (NU + 2) * SN;
-  L.cv[1] = buf + (NU + 3) * SN;
-  L.cv[2] = nullptr;
-  L.om[0] = L.om[1] = L.om[2] = nullptr;
-  Os[0] = buf + (2 * NU + 4) * SN;
-  Os[1] = Os[2] = nullptr;
+  const TileAcc<T, KIND, SN, SF> acc{base, G.h, &G};
   const int nx = G.g.nx, ny = G.g.ny;
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
@@ -422,12 +485,8 @@ __device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, 
       n.m[1] = n.c - SW;
       n.p[1] = n.c + SW;
       n.m[2] = n.p[2] = n.c;
-      if constexpr (SF) {
-        smooth_point_ex<T, KIND, 2>(L, P, n, Fs, Os, n.c);
-      } else {
-        const int gidx = wrapi(gy, ny) * nx + wrapi(x0 - ring + rx, nx);
-        smooth_point_ex<T, KIND, 2>(L, P, n, G.f, G.om, gidx);
-      }
+      const int fc = SF ? n.c : wrapi(gy, ny) * nx + wrapi(x0 - ring + rx, nx);
+      smooth_point_a<T, KIND, 2>(acc, P, n, fc);
     }
     __syncthreads();
   }
@@ -437,7 +496,7 @@ __device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, 
     if (gx < nx && gy < ny) {
       const int sidx = (ty + RB_H) * SW + tx + RB_XO;
 #pragma unroll
-      for (int q = 0; q < NU; ++q) G.e[q][gy * nx + gx] = L.e[q][sidx];
+      for (int q = 0; q < NU; ++q) G.e[q][gy * nx + gx] = acc.e(q, sidx);
     }
   }
 }
@@ -446,7 +505,7 @@ __device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, 
 // blockIdx.x + gridDim.x, ..., the next tile's copies in flight while the
 // current one is computed; otherwise one tile per block.
 template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
-__global__ void __launch_bounds__(RB_THREADS) k_smooth_rb2d(Lvl<T> G, Phys<T> P, int ntx, int ntiles) {
+__global__ void __launch_bounds__(rb_threads(TX, TY)) k_smooth_rb2d(Lvl<T> G, Phys<T> P, int ntx, int ntiles) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* buf0 = reinterpret_cast<T*>(smraw);
   constexpr int BUFSTRIDE = rb_arrays<KIND, SF>() * RBGeom<TX, TY>::SN;
@@ -457,7 +516,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_smooth_rb2d(Lvl<T> G, Phys<T> P,
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    rb2d_compute<T, KIND, TX, TY, SF>(G, P, buf0, (t % ntx) * TX, (t / ntx) * TY);
+    rb2d_compute<T, KIND, TX, TY, SF>(G, P, 0, (t % ntx) * TX, (t / ntx) * TY);
   } else {
     rb2d_issue<T, KIND, TX, TY, SF>(G, buf0, (t % ntx) * TX, (t / ntx) * TY);
     cp_async_commit();
@@ -468,7 +527,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_smooth_rb2d(Lvl<T> G, Phys<T> P,
       cp_async_commit();
       cp_async_wait_one();
       __syncthreads();
-      rb2d_compute<T, KIND, TX, TY, SF>(G, P, buf0 + (k & 1) * BUFSTRIDE, (t % ntx) * TX, (t / ntx) * TY);
+      rb2d_compute<T, KIND, TX, TY, SF>(G, P, (k & 1) * BUFSTRIDE, (t % ntx) * TX, (t / ntx) * TY);
       __syncthreads();
       if (!next) break;
       t = tn;
@@ -482,10 +541,7 @@ struct RBVariant {
   int tx, ty;
   bool sf, pipe;
 };
-constexpr int RB_NVAR = 8;
-__host__ __device__ constexpr RBVariant rb_variant(int v) {
-  return RBVariant{(v & 4) ? 64 : 32, (v & 4) ? 8 : 16, (v & 2) != 0, (v & 1) != 0};
-}
+constexpr int RB_NVAR = 12;   // bits 0-1: PIPE, SF; v >> 2: tile 32x16, 64x8, 32x32
 
 // The whole V-cycle of the small levels (each at most SMALL_N points) in one
 // thread block: phases separated by __syncthreads, data in L1/L2.

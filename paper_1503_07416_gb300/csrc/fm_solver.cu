@@ -109,11 +109,12 @@ __global__ void k_prolong_one(const double* coarse, double* fine, Geo F, Geo C, 
 template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
 static int launch_rb_v(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s) {
   constexpr size_t smem = rb_smem_bytes<T, KIND, TX, TY, SF, PIPE>();
+  if (smem + 4096 > (size_t)st->smem_optin) return FM_EINVAL;  // variant does not fit on this device
   static int per_sm = 0;
   if (!per_sm) {
     if (cudaFuncSetAttribute(k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>, RB_THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>, rb_threads(TX, TY),
                                                       smem) != cudaSuccess) {
       cudaGetLastError();
       return FM_ECUDA;
@@ -124,7 +125,7 @@ static int launch_rb_v(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStre
   const int ntiles = ntx * ((L.g.ny + TY - 1) / TY);
   int grid = ntiles;
   if (PIPE && grid > per_sm * st->sms) grid = per_sm * st->sms;
-  k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE><<<grid, RB_THREADS, smem, s>>>(L, P, ntx, ntiles);
+  k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE><<<grid, rb_threads(TX, TY), smem, s>>>(L, P, ntx, ntiles);
   return FM_OK;
 }
 
@@ -138,7 +139,11 @@ static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cud
     case 4: return launch_rb_v<T, KIND, 64, 8, false, false>(st, L, P, s);
     case 5: return launch_rb_v<T, KIND, 64, 8, false, true>(st, L, P, s);
     case 6: return launch_rb_v<T, KIND, 64, 8, true, false>(st, L, P, s);
-    default: return launch_rb_v<T, KIND, 64, 8, true, true>(st, L, P, s);
+    case 7: return launch_rb_v<T, KIND, 64, 8, true, true>(st, L, P, s);
+    case 8: return launch_rb_v<T, KIND, 32, 32, false, false>(st, L, P, s);
+    case 9: return launch_rb_v<T, KIND, 32, 32, false, true>(st, L, P, s);
+    case 10: return launch_rb_v<T, KIND, 32, 32, true, false>(st, L, P, s);
+    default: return launch_rb_v<T, KIND, 32, 32, true, true>(st, L, P, s);
   }
 }
 
@@ -230,6 +235,10 @@ struct Solver {
         float best = 1e30f;
         for (int v = 0; v < RB_NVAR && rc == FM_OK; ++v) {
           rc = launch_rb<T, KIND>(st, v, L, P, st->stream);
+          if (rc == FM_EINVAL) {  // does not fit in shared memory: skip
+            rc = FM_OK;
+            continue;
+          }
           if (rc) break;
           if (cudaEventRecord(e0, st->stream) != cudaSuccess) { rc = FM_ECUDA; break; }
           for (int k = 0; k < 3 && rc == FM_OK; ++k) rc = launch_rb<T, KIND>(st, v, L, P, st->stream);
@@ -772,6 +781,11 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
     return FM_ECUDA;
   }
   st->sms = sms;
+  if (cudaDeviceGetAttribute(&st->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    delete st;
+    return FM_ECUDA;
+  }
   const int need = (int)((st->lv[0].g.N + TPB - 1) / TPB);
   st->nblk = need < 4 * sms ? need : 4 * sms;
   const size_t bytes = carve(st, nullptr);

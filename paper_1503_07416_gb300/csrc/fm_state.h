@@ -51,6 +51,7 @@ struct fm_state {
   double* partials;               // per-block partial sums (deterministic reductions)
   int nblk;                       // blocks of the reduction kernels
   int sms;                        // multiprocessors of the device
+  int smem_optin;                 // shared memory per block (opt-in maximum)
   double* dscal;                  // device scalars
   double* hscal;                  // pinned host mirror of dscal
   double ce;                      // (J_e * 1) (CDFT)
@@ -63,7 +64,7 @@ struct fm_state {
   bool use_graph;                 // run fm_step as one CUDA graph launch
   bool fused_rb;                  // 2-D: one tiled launch per red-black sweep
   int rbv[fm::MAXLEV];            // chosen variant of the fused sweep per level
-  float rbt[fm::MAXLEV][8];       // autotuner timings (ms per launch)
+  float rbt[fm::MAXLEV][12];      // autotuner timings (ms per launch)
   int small_from;                 // first level handled by the single-block V-cycle
   void* ctl;                      // device control block of the step
   cudaGraph_t graph;

@@ -276,7 +276,7 @@ def fm_batch_launches(b):
 
 def fm_batch_tuning(b, level):
     v = C.c_int()
-    ms = (C.c_float * 8)()
+    ms = (C.c_float * 12)()
     _check(lib().fm_batch_tuning(b, level, C.byref(v), ms), "fm_batch_tuning")
     return v.value, list(ms)
 
@@ -299,9 +299,9 @@ def fm_mass_noalloc(rho, h, out, stream=0):
 
 
 def fm_tuning(st, level):
-    """(chosen variant, [ms of the 8 variants]) of the fused sweep at `level`."""
+    """(chosen variant, [ms of the 12 variants]) of the fused sweep at `level`."""
     v = C.c_int()
-    ms = (C.c_float * 8)()
+    ms = (C.c_float * 12)()
     _check(lib().fm_tuning(st, level, C.byref(v), ms), "fm_tuning")
     return v.value, list(ms)
 
