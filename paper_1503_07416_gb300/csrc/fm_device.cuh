@@ -78,7 +78,7 @@ __device__ __forceinline__ void smooth_point_a(const A& a, const Phys<T>& P, con
     const T ek = a.f(LY::IKA, fc) + (nbs(0) - T(2 * DIM) * er) * ih2;
     // mu = f4 + [(p+e)^3 - p^3]/3 + alpha e + Lap_h e_kappa (exact: the block is triangular)
     const T psi = crc - T(1.5);
-    const T em = a.f(LY::IMU, fc) + er * (psi * psi + psi * er + er * er / T(3)) + P.alpha * er
+    const T em = a.f(LY::IMU, fc) + er * (psi * psi + psi * er + er * er * T(1.0 / 3.0)) + P.alpha * er
                + (nbs(LY::IKA) - T(2 * DIM) * ek) * ih2;
     eg[LY::IKA] = ek;
     eg[LY::IMU] = em;
@@ -889,7 +889,7 @@ __device__ __forceinline__ void prepare_mu_point(const Fields64& F, const Geo& G
   const double psi = F.rho[idx] - 1.5;
   const double* ka = F.g[LY::IKA];
   const double lapk = (nbsum<double, DIM>(ka, n) - 2.0 * DIM * ka[idx]) / (h * h);
-  F.g[LY::IMU][idx] = psi * psi * psi / 3.0 + P.alpha * psi + lapk + F.S[LY::IMU][idx];
+  F.g[LY::IMU][idx] = psi * psi * psi * (1.0 / 3.0) + P.alpha * psi + lapk + F.S[LY::IMU][idx];
 }
 
 template <int DIM>
@@ -1045,7 +1045,7 @@ __device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out
       const double kc = g[LY::IKA][n.c];
       const double lapk = (nbsum<double, DIM>(g[LY::IKA], n) - 2.0 * DIM * kc) * ih2;
       const double lapr = (nbsum<double, DIM>(g[0], n) - 2.0 * DIM * rc) * ih2;
-      N[LY::IMU] = g[LY::IMU][n.c] - psi * psi * psi / 3.0 - P.alpha * psi - lapk;
+      N[LY::IMU] = g[LY::IMU][n.c] - psi * psi * psi * (1.0 / 3.0) - P.alpha * psi - lapk;
       N[LY::IKA] = kc - lapr;
     }
 #pragma unroll
@@ -1083,6 +1083,13 @@ __device__ __forceinline__ void resid64_tile_body(const Fields64& F, const Resid
 #pragma unroll
   for (int q = 0; q < LY::NU; ++q) acc[q] = 0.0;
   const double ih = 1.0 / h, ih2 = ih * ih;
+  // step constants, formed once per thread
+  const double c_div = P.s * 0.25 * ih;          // continuity flux difference
+  const double c_w = 0.5 * P.sigma * P.s;        // vorticity term
+  const double c_q = 0.25 * P.s * ih;            // kinetic-energy gradient
+  const double c_m = 0.5 * P.s * ih;             // chemical-potential gradient
+  const double c_v = 0.5 * P.s * P.gamma * ih2;  // viscous Laplacian
+  const double third = 1.0 / 3.0;
   const int nx = G.nx, ny = G.ny;
   const int ntx = (nx + R64_TX - 1) / R64_TX;
   const int ntiles = ntx * ((ny + R64_TY - 1) / R64_TY);
@@ -1119,23 +1126,20 @@ __device__ __forceinline__ void resid64_tile_body(const Fields64& F, const Resid
         const int xm = c - 1, xp = c + 1, ym = c - R64_SW, yp = c + R64_SW;
         const double rkc = F.rho[idx];
         double N[LY::NU];
-        N[0] = g[0][idx] + P.s * 0.25 * ih * ((sRU[xp] - sRU[xm]) + (sRV[yp] - sRV[ym]));
+        N[0] = g[0][idx] + c_div * ((sRU[xp] - sRU[xm]) + (sRV[yp] - sRV[ym]));
         const double uc = g[1][idx], vc = g[2][idx];
         const double w = F.om[0][idx];
-        const double wx0 = -w * vc, wx1 = w * uc;
-        const double lapu = (nbsum<double, 2>(g[1], n) - 4.0 * uc) * ih2;
-        const double lapv = (nbsum<double, 2>(g[2], n) - 4.0 * vc) * ih2;
-        N[1] = rkc * uc + 0.5 * P.sigma * P.s * rkc * wx0
-             + P.s * rkc * ih * (0.25 * (sQ[xp] - sQ[xm]) + 0.5 * (sM[xp] - sM[xm])) - 0.5 * P.s * P.gamma * lapu;
-        N[2] = rkc * vc + 0.5 * P.sigma * P.s * rkc * wx1
-             + P.s * rkc * ih * (0.25 * (sQ[yp] - sQ[ym]) + 0.5 * (sM[yp] - sM[ym])) - 0.5 * P.s * P.gamma * lapv;
+        N[1] = rkc * (uc - c_w * w * vc + c_q * (sQ[xp] - sQ[xm]) + c_m * (sM[xp] - sM[xm]))
+             - c_v * (nbsum<double, 2>(g[1], n) - 4.0 * uc);
+        N[2] = rkc * (vc + c_w * w * uc + c_q * (sQ[yp] - sQ[ym]) + c_m * (sM[yp] - sM[ym]))
+             - c_v * (nbsum<double, 2>(g[2], n) - 4.0 * vc);
         if constexpr (KIND == KPFC) {
           const double rc = g[0][idx];
           const double psi = rc - 1.5;
           const double kc = g[LY::IKA][idx];
           const double lapk = (nbsum<double, 2>(g[LY::IKA], n) - 4.0 * kc) * ih2;
           const double lapr = (nbsum<double, 2>(g[0], n) - 4.0 * rc) * ih2;
-          N[LY::IMU] = g[LY::IMU][idx] - psi * psi * psi / 3.0 - P.alpha * psi - lapk;
+          N[LY::IMU] = g[LY::IMU][idx] - psi * psi * psi * third - P.alpha * psi - lapk;
           N[LY::IKA] = kc - lapr;
         }
 #pragma unroll

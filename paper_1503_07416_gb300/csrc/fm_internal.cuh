@@ -173,7 +173,7 @@ __device__ __forceinline__ void applyM(const Lvl<T>& L, const Phys<T>& P, const 
     const T ek = E[LY::IKA][n.c];
     const T lapk = (nbsum<T, DIM>(E[LY::IKA], n) - T(2 * DIM) * ek) * ih2;
     const T lapr = (nbsum<T, DIM>(E[0], n) - T(2 * DIM) * er) * ih2;
-    M[LY::IMU] = E[LY::IMU][n.c] - er * (psi * psi + psi * er + er * er / T(3)) - P.alpha * er - lapk;
+    M[LY::IMU] = E[LY::IMU][n.c] - er * (psi * psi + psi * er + er * er * T(1.0 / 3.0)) - P.alpha * er - lapk;
     M[LY::IKA] = ek - lapr;
   }
 }
