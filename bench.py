@@ -42,6 +42,29 @@ UNIT = "steps/s"
 WORKLOAD = "pfc512: 2-D PFC 512x512, eps=0.4, s=0.02, 4 nuclei, undamped, V(2,2) to 1e-10"
 
 
+def rank_seed(rank):
+    """Seed of the independent instance a rank advances."""
+    return 2 + 1000 * rank
+
+
+def shard(n, rank, world):
+    """Instances of an ensemble of n that rank `rank` of `world` owns."""
+    return list(range(rank, n, world))
+
+
+def max_over_ranks(dist, value, device):
+    """Largest value over all ranks (the job time is the slowest rank's)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, max_ms):
+    """Whole-job units per second: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -190,7 +213,7 @@ def run_ours(args):
         dist.barrier()
     fm.lib()
 
-    rho, vel, prm = inputs.pfc512(seed=2 + 1000 * rank)
+    rho, vel, prm = inputs.pfc512(seed=rank_seed(rank))
     N = rho.size
     stream = torch.cuda.current_stream().cuda_stream
     rho_d = torch.from_numpy(rho).cuda()
@@ -214,9 +237,7 @@ def run_ours(args):
         prof = time_smoother(torch, fm, sol, rho_d, vel_d, prm["dt"], min(args.steps, 20), flush)
         total_ms = sum(times)
         if world > 1:
-            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+            total_ms = max_over_ranks(dist, total_ms, "cuda")
         results[name] = dict(total_ms=total_ms, cycles=cycles, launches=launches, prof=prof,
                              clocks=clk.summary(), sol=sol, prec=prec)
 
@@ -254,9 +275,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = e_start.elapsed_time(e_end)
     if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(dist, e2e_ms, "cuda")
 
     for r in results.values():
         r["sol"].close()
@@ -267,7 +286,7 @@ def run_ours(args):
 
     mix, f64 = results["mixed"], results["fp64"]
     steps = args.steps
-    value = world * steps / (mix["total_ms"] / 1e3)
+    value = job_throughput(world, steps, mix["total_ms"])
     ms_per_step = mix["total_ms"] / steps
     peak, peak_kind = load_peaks()
     # smoother roofline: one launch of the fused 2-D kernel is one red-black
@@ -328,7 +347,7 @@ def run_ours(args):
                              "the same steps run launch by launch (the timed steps run as graphs)",
         },
         "e2e": {
-            "value": round(world * steps / (e2e_ms / 1e3), 3),
+            "value": round(job_throughput(world, steps, e2e_ms), 3),
             "unit": UNIT,
             "h2d_bytes_per_step": 3 * N * 8,
             "d2h_bytes_per_step": 3 * N * 8,
