@@ -482,6 +482,24 @@ def profile_batch(count):
                       "gbs": 80 * pts / (ms * 1e-3) / 1e9}))
 
 
+def profile_single(name):
+    """Small ncu target: one solver of a named workload (mixed), 1 warm-up and
+    2 steps."""
+    import torch
+    from paper_1503_07416_gb300 import build, fm, inputs
+    build.build_library()
+    rho, vel, prm = getattr(inputs, name)()
+    n = list(reversed(rho.shape))
+    sol = fm.Solver(prm["kind"], n, prm["h"], dim=prm["dim"], alpha=prm.get("alpha", 0.0), nu=prm.get("nu", 0.0),
+                    precision=fm.FM_MIXED, tol=prm["tol"], w_damp=0.0, delta=prm.get("delta", 0.0),
+                    stream=torch.cuda.current_stream().cuda_stream)
+    sol.set_fields(rho, vel)
+    cyc = [sol.step(prm["dt"]).cycles for _ in range(3)]
+    torch.cuda.synchronize()
+    sol.close()
+    print(json.dumps({"profile_single": name, "cycles": cyc}))
+
+
 def secondary_all(torch, fm, inputs, flush, peak):
     out = {"batch48": secondary_batch48(torch, fm, inputs, flush, peak)}
     rho, vel, prm = inputs.cdft256()
@@ -555,6 +573,8 @@ def main():
     ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
                     help="time one arm only and print a short diagnostic line (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-single", choices=["pfc512", "cdft256", "pfc3d128", "pfc64"], default=None,
+                    help="profiling target: one solver of the named workload, 3 steps")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="profiling target: first K batch48 instances, timed batched sweeps only")
     ap.add_argument("--no-secondary", action="store_true",
@@ -564,6 +584,8 @@ def main():
         args.warmup = 3
     if args.profile_batch:
         profile_batch(args.profile_batch)
+    elif args.profile_single:
+        profile_single(args.profile_single)
     elif args.impl == "reference":
         run_reference(args)
     else:

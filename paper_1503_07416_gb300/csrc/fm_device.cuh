@@ -998,6 +998,8 @@ __device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out
 #pragma unroll
   for (int q = 0; q < LY::NU; ++q) acc[q] = 0.0;
   const double ih = 1.0 / h, ih2 = ih * ih;
+  const double c_div = P.s * 0.25 * ih, c_w = 0.5 * P.sigma * P.s, c_q = 0.25 * P.s * ih;
+  const double c_m = 0.5 * P.s * ih, c_v = 0.5 * P.s * P.gamma * ih2, third = 1.0 / 3.0;
   for (int idx = lb * blockDim.x + threadIdx.x; idx < G.N; idx += nb * blockDim.x) {
     int i, j, k;
     coords(idx, G, i, j, k);
@@ -1009,7 +1011,7 @@ __device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
       div += F.rho[n.p[d]] * g[1 + d][n.p[d]] - F.rho[n.m[d]] * g[1 + d][n.m[d]];
-    N[0] = g[0][n.c] + P.s * 0.25 * ih * div;
+    N[0] = g[0][n.c] + c_div * div;
     double uc[3], w[3], wx[3];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) uc[d] = g[1 + d][n.c];
@@ -1034,10 +1036,8 @@ __device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out
         mp = log(rp) + 2.0 * P.ce * rp;
         mm = log(rm) + 2.0 * P.ce * rm;
       }
-      const double lapa = (nbsum<double, DIM>(g[1 + a], n) - 2.0 * DIM * uc[a]) * ih2;
-      N[1 + a] = rkc * uc[a] + 0.5 * P.sigma * P.s * rkc * wx[a]
-               + P.s * rkc * ih * (0.25 * (qp - qm) + 0.5 * (mp - mm))
-               - 0.5 * P.s * P.gamma * lapa;
+      N[1 + a] = rkc * (uc[a] + c_w * wx[a] + c_q * (qp - qm) + c_m * (mp - mm))
+               - c_v * (nbsum<double, DIM>(g[1 + a], n) - 2.0 * DIM * uc[a]);
     }
     if constexpr (KIND == KPFC) {
       const double rc = g[0][n.c];
@@ -1045,7 +1045,7 @@ __device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out
       const double kc = g[LY::IKA][n.c];
       const double lapk = (nbsum<double, DIM>(g[LY::IKA], n) - 2.0 * DIM * kc) * ih2;
       const double lapr = (nbsum<double, DIM>(g[0], n) - 2.0 * DIM * rc) * ih2;
-      N[LY::IMU] = g[LY::IMU][n.c] - psi * psi * psi * (1.0 / 3.0) - P.alpha * psi - lapk;
+      N[LY::IMU] = g[LY::IMU][n.c] - psi * psi * psi * third - P.alpha * psi - lapk;
       N[LY::IKA] = kc - lapr;
     }
 #pragma unroll
@@ -1166,6 +1166,92 @@ template <int KIND, typename T>
 __global__ void __launch_bounds__(TPB) k_resid64_tile(Fields64 F, Resid64Out O, Geo G, double h,
                                                       Phys<double> P, double* partials) {
   resid64_tile_body<KIND, T>(F, O, G, h, P, partials, blockIdx.x, gridDim.x);
+}
+
+// Per-point quantities every point shares with its neighbours in the
+// float64 residual (used in 3-D): X[0] = |u|^2, X[1 + d] = rho^k u_d, and for
+// CDFT X[4] = ln rho + 2 c_e rho.
+struct Shared64 {
+  double* x[5];
+};
+
+template <int KIND, int DIM>
+__global__ void __launch_bounds__(TPB) k_shared64(Fields64 F, Shared64 X, int N, double ce) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N) return;
+  const double rk = F.rho[idx];
+  double q = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const double u = F.g[1 + d][idx];
+    q += u * u;
+    X.x[1 + d][idx] = rk * u;
+  }
+  X.x[0][idx] = q;
+  if constexpr (KIND == KCDFT) {
+    const double r = F.g[0][idx];
+    X.x[4][idx] = log(r) + 2.0 * ce * r;
+  }
+}
+
+// Float64 residual reading the shared quantities of k_shared64.
+template <int KIND, int DIM, typename T>
+__global__ void __launch_bounds__(TPB) k_resid64_x(Fields64 F, Shared64 X, Resid64Out O, Geo G, double h,
+                                                   Phys<double> P, double* partials) {
+  using LY = Layout<KIND, DIM>;
+  double acc[LY::NU];
+#pragma unroll
+  for (int q = 0; q < LY::NU; ++q) acc[q] = 0.0;
+  const double ih = 1.0 / h, ih2 = ih * ih;
+  const double c_div = P.s * 0.25 * ih, c_w = 0.5 * P.sigma * P.s, c_q = 0.25 * P.s * ih;
+  const double c_m = 0.5 * P.s * ih, c_v = 0.5 * P.s * P.gamma * ih2, third = 1.0 / 3.0;
+  const double* const* g = F.g;
+  const double* M = (KIND == KPFC) ? g[LY::IMU] : X.x[4];
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < G.N; idx += gridDim.x * blockDim.x) {
+    int i, j, k;
+    coords(idx, G, i, j, k);
+    const Nb n = neighbours(i, j, k, G);
+    const double rkc = F.rho[n.c];
+    double N[LY::NU];
+    double div = 0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) div += X.x[1 + d][n.p[d]] - X.x[1 + d][n.m[d]];
+    N[0] = g[0][n.c] + c_div * div;
+    double uc[3], w[3], wx[3];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) uc[d] = g[1 + d][n.c];
+#pragma unroll
+    for (int d = 0; d < LY::NOM; ++d) w[d] = F.om[d][n.c];
+    cross<double, DIM>(w, uc, wx);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      N[1 + a] = rkc * (uc[a] + c_w * wx[a] + c_q * (X.x[0][n.p[a]] - X.x[0][n.m[a]]) + c_m * (M[n.p[a]] - M[n.m[a]]))
+               - c_v * (nbsum<double, DIM>(g[1 + a], n) - 2.0 * DIM * uc[a]);
+    }
+    if constexpr (KIND == KPFC) {
+      const double rc = g[0][n.c];
+      const double psi = rc - 1.5;
+      const double kc = g[LY::IKA][n.c];
+      const double lapk = (nbsum<double, DIM>(g[LY::IKA], n) - 2.0 * DIM * kc) * ih2;
+      const double lapr = (nbsum<double, DIM>(g[0], n) - 2.0 * DIM * rc) * ih2;
+      N[LY::IMU] = g[LY::IMU][n.c] - psi * psi * psi * third - P.alpha * psi - lapk;
+      N[LY::IKA] = kc - lapr;
+    }
+#pragma unroll
+    for (int q = 0; q < LY::NU; ++q) {
+      const double r = F.S[q][idx] - N[q];
+      acc[q] += r * r;
+      if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = (T)r;
+      if (O.e0[q]) static_cast<T*>(O.e0[q])[idx] = T(0);
+      if (O.r64[q]) O.r64[q][idx] = r;
+    }
+    if (O.cr32) {
+      O.cr32[idx] = (float)g[0][idx];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) O.cv32[d][idx] = (float)uc[d];
+    }
+  }
+  block_partials<LY::NU>(acc, partials, blockIdx.x);
 }
 
 template <int KIND, int DIM, typename T>

@@ -306,6 +306,24 @@ struct Solver {
     return O;
   }
 
+  // Float64 residual: 2-D tiled kernel; 3-D shared quantities then residual.
+  static int launch_resid64(fm_state* st, const Fields64& F, const Resid64Out& O, const Geo& G, double h,
+                            const Phys<double>& P) {
+    cudaStream_t s = st->stream;
+    if constexpr (DIM == 2) {
+      k_resid64_tile<KIND, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
+      FM_LAUNCHED();
+    } else {
+      Shared64 X;
+      for (int q = 0; q < 5; ++q) X.x[q] = st->x64[q];
+      k_shared64<KIND, DIM><<<nblocks(G.N), TPB, 0, s>>>(F, X, G.N, P.ce);
+      FM_LAUNCHED();
+      k_resid64_x<KIND, DIM, T><<<st->nblk, TPB, 0, s>>>(F, X, O, G, h, P, st->partials);
+      FM_LAUNCHED();
+    }
+    return FM_OK;
+  }
+
   // float64 residual of the current iterate, the level-0 set-up of a cycle
   // and the control-block update (in_body: this follows a cycle).
   static int enqueue_resid_norm(fm_state* st, int in_body, cudaGraphConditionalHandle hdl, int use_handle) {
@@ -315,11 +333,8 @@ struct Solver {
     cudaStream_t s = st->stream;
     Fields64 F = make_fields(st);
     Resid64Out O = resid_out(st, true, nullptr);
-    if constexpr (DIM == 2)
-      k_resid64_tile<KIND, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
-    else
-      k_resid64<KIND, DIM, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
-    FM_LAUNCHED();
+    int rc = launch_resid64(st, F, O, G, h, P);
+    if (rc) return rc;
     const double w = (DIM == 3) ? h * h * h : h * h;
     k_norm_ctl<LY::NU><<<1, TPB, 0, s>>>(st->partials, st->nblk, w, (Ctl*)st->ctl, st->prm.tol,
                                          st->prm.max_cycles, in_body, hdl, use_handle);
@@ -335,11 +350,8 @@ struct Solver {
     cudaStream_t s = st->stream;
     Fields64 F = make_fields(st);
     Resid64Out O = resid_out(st, false, r64);
-    if constexpr (DIM == 2)
-      k_resid64_tile<KIND, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
-    else
-      k_resid64<KIND, DIM, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
-    FM_LAUNCHED();
+    int rc = launch_resid64(st, F, O, G, h, P);
+    if (rc) return rc;
     const double w = (DIM == 3) ? h * h * h : h * h;
     k_norm_final<LY::NU><<<1, TPB, 0, s>>>(st->partials, st->nblk, w, st->dscal);
     FM_LAUNCHED();
@@ -629,6 +641,8 @@ static size_t carve(fm_state* st, char* base) {
   st->conv = st->kind == FM_CDFT ? (double*)C.take(N0 * d8) : nullptr;
   st->tmp = (double*)C.take(N0 * d8);
   for (int q = 0; q < MAXU; ++q) st->r64[q] = q < st->nu ? (double*)C.take(N0 * d8) : nullptr;
+  for (int q = 0; q < 5; ++q)
+    st->x64[q] = (st->dim == 3 && (q < 4 || st->kind == FM_CDFT)) ? (double*)C.take(N0 * d8) : nullptr;
   st->partials = (double*)C.take((size_t)st->nblk * 8 * d8);
   st->dscal = (double*)C.take(64 * d8);
   st->ctl = C.take(64);

@@ -48,6 +48,7 @@ struct fm_state {
   double* conv;                   // J * rho^k (CDFT)
   double* tmp;                    // float64 scratch of N values
   double* r64[fm::MAXU];          // float64 residual scratch (row-level entry points)
+  double* x64[5];                 // 3-D: per-point quantities shared by the residual
   double* partials;               // per-block partial sums (deterministic reductions)
   int nblk;                       // blocks of the reduction kernels
   int sms;                        // multiprocessors of the device
