@@ -47,6 +47,7 @@ struct InstDev {
   Vel3 gvel;
   Geo g0;
   double h0;
+  double ih0;
   double* partials;
   double* tmp;
   double* rho;
@@ -200,14 +201,14 @@ template <typename T, int KIND>
 __global__ void __launch_bounds__(TPB) kb_prepare(const WorkItem* items, int nitems, const InstDev<T>* D,
                                                   const Phys<double>* P64) {
   FM_BATCH_HEAD();
-  prepare_point<KIND, 2>(D[inst].F, D[inst].g0, D[inst].h0, P64[inst], lb * TPB + threadIdx.x);
+  prepare_point<KIND, 2>(D[inst].F, D[inst].g0, D[inst].ih0, P64[inst], lb * TPB + threadIdx.x);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(TPB) kb_prepare_mu(const WorkItem* items, int nitems, const InstDev<T>* D,
                                                      const Phys<double>* P64) {
   FM_BATCH_HEAD();
-  prepare_mu_point<2>(D[inst].F, D[inst].g0, D[inst].h0, P64[inst], lb * TPB + threadIdx.x);
+  prepare_mu_point<2>(D[inst].F, D[inst].g0, D[inst].ih0, P64[inst], lb * TPB + threadIdx.x);
 }
 
 template <typename T, int KIND>
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(TPB) kb_closure(const WorkItem* items, int nit
   FM_BATCH_HEAD();
   if (ctl[inst].status != FM_OK) return;
   const InstDev<T>& I = D[inst];
-  closure_point<2>(I.F, I.g0, I.h0, P64[inst], I.tmp, lb * TPB + threadIdx.x);
+  closure_point<2>(I.F, I.g0, I.ih0, P64[inst], I.tmp, lb * TPB + threadIdx.x);
 }
 
 template <typename T>
@@ -412,6 +413,7 @@ struct Batch {
       I.gvel = Vel3{{st->g[1], st->g[2], nullptr}};
       I.g0 = st->lv[0].g;
       I.h0 = st->lv[0].h;
+      I.ih0 = 1.0 / st->lv[0].h;
       I.partials = st->partials;
       I.tmp = st->tmp;
       I.rho = st->rho;

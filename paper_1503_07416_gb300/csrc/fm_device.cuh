@@ -815,14 +815,14 @@ struct Fields64 {
 
 // omega^k, S and the initial iterate g^0 (kappa^0 = Lap_h rho^k for PFC).
 template <int KIND, int DIM>
-__device__ __forceinline__ void prepare_point(const Fields64& F, const Geo& G, double h, const Phys<double>& P,
+__device__ __forceinline__ void prepare_point(const Fields64& F, const Geo& G, double ih, const Phys<double>& P,
                                               int idx) {
   using LY = Layout<KIND, DIM>;
   if (idx >= G.N) return;
   int i, j, k;
   coords(idx, G, i, j, k);
   const Nb n = neighbours(i, j, k, G);
-  const double ih = 1.0 / h, ih2 = ih * ih;
+  const double ih2 = ih * ih;
   const double* u = F.vel[0];
   const double* v = F.vel[1];
   double w[3];
@@ -839,19 +839,19 @@ __device__ __forceinline__ void prepare_point(const Fields64& F, const Geo& G, d
 #pragma unroll
   for (int d = 0; d < DIM; ++d)
     div += F.rho[n.p[d]] * F.vel[d][n.p[d]] - F.rho[n.m[d]] * F.vel[d][n.m[d]];
-  F.S[0][idx] = rkc - P.s * 0.25 * ih * div;
+  const double c_w = 0.5 * P.sigma * P.s, c_v = 0.5 * P.s * P.gamma * ih2, c_e = P.s * 0.5 * ih;
+  F.S[0][idx] = rkc - (P.s * 0.25 * ih) * div;
   double uc[3], wx[3];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) uc[d] = F.vel[d][n.c];
   cross<double, DIM>(w, uc, wx);
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    double sa = rkc * uc[a] - 0.5 * P.sigma * P.s * rkc * wx[a]
-              + 0.5 * P.s * P.gamma * (nbsum<double, DIM>(F.vel[a], n) - 2.0 * DIM * uc[a]) * ih2;
+    double sa = rkc * (uc[a] - c_w * wx[a]) + c_v * (nbsum<double, DIM>(F.vel[a], n) - 2.0 * DIM * uc[a]);
     if constexpr (KIND == KCDFT) {
       const double Ep = 2.0 * P.ce * F.rho[n.p[a]] + F.conv[n.p[a]];
       const double Em = 2.0 * P.ce * F.rho[n.m[a]] + F.conv[n.m[a]];
-      sa += P.s * rkc * 0.5 * ih * (Ep - Em);
+      sa += c_e * rkc * (Ep - Em);
     }
     F.S[1 + a][idx] = sa;
     F.g[1 + a][idx] = uc[a];
@@ -873,13 +873,13 @@ __device__ __forceinline__ void prepare_point(const Fields64& F, const Geo& G, d
 }
 
 template <int KIND, int DIM>
-__global__ void __launch_bounds__(TPB) k_prepare(Fields64 F, Geo G, double h, Phys<double> P) {
-  prepare_point<KIND, DIM>(F, G, h, P, blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void __launch_bounds__(TPB) k_prepare(Fields64 F, Geo G, double ih, Phys<double> P) {
+  prepare_point<KIND, DIM>(F, G, ih, P, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // PFC: mu^0 = psi^3/3 + alpha psi + Lap_h kappa^0 + S_mu (value of the mu row at rho^k).
 template <int DIM>
-__device__ __forceinline__ void prepare_mu_point(const Fields64& F, const Geo& G, double h,
+__device__ __forceinline__ void prepare_mu_point(const Fields64& F, const Geo& G, double ih,
                                                  const Phys<double>& P, int idx) {
   using LY = Layout<KPFC, DIM>;
   if (idx >= G.N) return;
@@ -888,13 +888,13 @@ __device__ __forceinline__ void prepare_mu_point(const Fields64& F, const Geo& G
   const Nb n = neighbours(i, j, k, G);
   const double psi = F.rho[idx] - 1.5;
   const double* ka = F.g[LY::IKA];
-  const double lapk = (nbsum<double, DIM>(ka, n) - 2.0 * DIM * ka[idx]) / (h * h);
+  const double lapk = (nbsum<double, DIM>(ka, n) - 2.0 * DIM * ka[idx]) * (ih * ih);
   F.g[LY::IMU][idx] = psi * psi * psi * (1.0 / 3.0) + P.alpha * psi + lapk + F.S[LY::IMU][idx];
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(TPB) k_prepare_mu(Fields64 F, Geo G, double h, Phys<double> P) {
-  prepare_mu_point<DIM>(F, G, h, P, blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void __launch_bounds__(TPB) k_prepare_mu(Fields64 F, Geo G, double ih, Phys<double> P) {
+  prepare_mu_point<DIM>(F, G, ih, P, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <int NQ>
@@ -1342,7 +1342,7 @@ __global__ void k_norm_ctl(const double* partials, int nblk, double w, Ctl* ctl,
 // rho^{k+1} = S1 - (s/4h) sum_d ([rho^k u_d]_{+d} - [rho^k u_d]_{-d}), projected,
 // into `out`; skipped unless the solve succeeded.
 template <int DIM>
-__device__ __forceinline__ void closure_point(const Fields64& F, const Geo& G, double h, const Phys<double>& P,
+__device__ __forceinline__ void closure_point(const Fields64& F, const Geo& G, double ih, const Phys<double>& P,
                                               double* out, int idx) {
   if (idx >= G.N) return;
   int i, j, k;
@@ -1352,15 +1352,15 @@ __device__ __forceinline__ void closure_point(const Fields64& F, const Geo& G, d
 #pragma unroll
   for (int d = 0; d < DIM; ++d)
     div += F.rho[n.p[d]] * F.g[1 + d][n.p[d]] - F.rho[n.m[d]] * F.g[1 + d][n.m[d]];
-  const double r = F.S[0][idx] - P.s * 0.25 / h * div;
+  const double r = F.S[0][idx] - (P.s * 0.25 * ih) * div;
   out[idx] = (P.delta > 0.0) ? sqrt(r * r + P.delta * P.delta) : fabs(r);
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(TPB) k_closure(Fields64 F, Geo G, double h, Phys<double> P, double* out,
+__global__ void __launch_bounds__(TPB) k_closure(Fields64 F, Geo G, double ih, Phys<double> P, double* out,
                                                  const Ctl* ctl) {
   if (ctl->status != FM_OK) return;
-  closure_point<DIM>(F, G, h, P, out, blockIdx.x * blockDim.x + threadIdx.x);
+  closure_point<DIM>(F, G, ih, P, out, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // New time level: rho <- closure result, u <- converged velocity (if the

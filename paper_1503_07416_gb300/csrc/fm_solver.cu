@@ -273,10 +273,10 @@ struct Solver {
       if (rc) return rc;
     }
     Fields64 F = make_fields(st);
-    k_prepare<KIND, DIM><<<nblocks(G.N), TPB, 0, s>>>(F, G, h, P);
+    k_prepare<KIND, DIM><<<nblocks(G.N), TPB, 0, s>>>(F, G, 1.0 / h, P);
     FM_LAUNCHED();
     if (KIND == KPFC) {
-      k_prepare_mu<DIM><<<nblocks(G.N), TPB, 0, s>>>(F, G, h, P);
+      k_prepare_mu<DIM><<<nblocks(G.N), TPB, 0, s>>>(F, G, 1.0 / h, P);
       FM_LAUNCHED();
     }
     return inject_all(st, false);
@@ -446,7 +446,7 @@ struct Solver {
     Fields64 F = make_fields(st);
     Phys<double> P64 = make_phys<double>(st);
     const Ctl* ctl = (const Ctl*)st->ctl;
-    k_closure<DIM><<<nblocks(G.N), TPB, 0, st->stream>>>(F, G, st->lv[0].h, P64, st->tmp, ctl);
+    k_closure<DIM><<<nblocks(G.N), TPB, 0, st->stream>>>(F, G, 1.0 / st->lv[0].h, P64, st->tmp, ctl);
     FM_LAUNCHED();
     Vel3W vw{{st->vel[0], st->vel[1], st->vel[2]}};
     Vel3 gv{{st->g[1], st->g[2], DIM == 3 ? st->g[3] : nullptr}};
