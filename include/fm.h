@@ -179,6 +179,24 @@ int fm_prolong_add(fm_state* st, const double* coarse, double* fine, int where);
 /* Number of multigrid levels of the state. */
 int fm_levels(const fm_state* st);
 
+/* Smoother row (App. G.1-G.3 and the red-black ordering of the solver):
+ * `sweeps` red-black sweeps of the damped point-block Gauss-Seidel smoother,
+ * in the state's precision, on the finest grid for the correction equation
+ * M(e) = N(g + e) - N(g) = f, with g the iterate of the last fm_prepare or
+ * fm_step as coefficient.  e (in/out) and f are nu float64 arrays each
+ * (nu = 1 + dim, +2 for PFC; host or device per `where`), rounded to the
+ * state's precision on entry.  variant: FM_SWEEP_AUTO runs the sweeps exactly
+ * as fm_step does (2-D: the autotuned fused tile sweep, in pairs, an odd last
+ * sweep as two colour launches); FM_SWEEP_TWO_COLOUR runs every sweep as a
+ * red launch and a black launch; 0 .. 11 fixes the fused variant (2-D only,
+ * encoding as fm_tuning).  FM_EINVAL before the first fm_prepare, for
+ * sweeps < 0, an unknown variant, a fused variant in 3-D or one that does not
+ * fit in shared memory. */
+#define FM_SWEEP_AUTO (-1)
+#define FM_SWEEP_TWO_COLOUR (-2)
+int fm_smooth(fm_state* st, double* const* e, const double* const* f, int sweeps, int variant,
+              int where);
+
 /* ---- Batched ensembles (2-D) ---- */
 
 /* A set of independent 2-D instances (uneven grid sizes allowed) stepped

@@ -91,7 +91,7 @@ __device__ __forceinline__ void smem_copy(S* dst, const S* src) {
 template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
 __global__ void __launch_bounds__(rb_threads(TX, TY)) kb_smooth_rb2d(const WorkItem* items, int nitems, const InstDev<T>* D,
                                                              const Phys<T>* P, const Ctl* ctl, int level,
-                                                             int ntiles) {
+                                                             int ntiles, int dir) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* buf0 = reinterpret_cast<T*>(smraw);
   constexpr int BUFSTRIDE = rb_arrays<KIND, SF>() * RBGeom<TX, TY>::SN;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(rb_threads(TX, TY)) kb_smooth_rb2d(const WorkI
     if (s_inst[slot] >= 0) {
       smem_copy(&Gs[slot], &D[s_inst[slot]].lv[level]);
       __syncthreads();
-      rb2d_issue<T, KIND, TX, TY, SF>(Gs[slot], buf0 + slot * BUFSTRIDE, s_x0[slot], s_y0[slot]);
+      rb2d_issue<T, KIND, TX, TY, SF>(Gs[slot], buf0 + slot * BUFSTRIDE, s_x0[slot], s_y0[slot], dir);
     }
     cp_async_commit();
   };
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(rb_threads(TX, TY)) kb_smooth_rb2d(const WorkI
     fetch(t, 0);
     cp_async_wait_all();
     __syncthreads();
-    if (s_inst[0] >= 0) rb2d_compute<T, KIND, TX, TY, SF>(Gs[0], P[s_inst[0]], 0, s_x0[0], s_y0[0]);
+    if (s_inst[0] >= 0) rb2d_compute<T, KIND, TX, TY, SF>(Gs[0], P[s_inst[0]], 0, s_x0[0], s_y0[0], dir);
   } else {
     fetch(t, 0);
     for (int k = 0;; ++k) {
@@ -133,12 +133,26 @@ __global__ void __launch_bounds__(rb_threads(TX, TY)) kb_smooth_rb2d(const WorkI
       __syncthreads();
       const int slot = k & 1;
       if (s_inst[slot] >= 0)
-        rb2d_compute<T, KIND, TX, TY, SF>(Gs[slot], P[s_inst[slot]], slot * BUFSTRIDE, s_x0[slot], s_y0[slot]);
+        rb2d_compute<T, KIND, TX, TY, SF>(Gs[slot], P[s_inst[slot]], slot * BUFSTRIDE, s_x0[slot], s_y0[slot],
+                                          dir);
       __syncthreads();
       if (!next) break;
       t = tn;
     }
   }
+}
+
+// e = r at every point of level `level` (after an odd number of fused sweeps).
+template <typename T, int NU>
+__global__ void __launch_bounds__(TPB) kb_copy_back(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                    const Ctl* ctl, int level) {
+  FM_BATCH_HEAD();
+  if (!inst_active(ctl, inst)) return;
+  const Lvl<T>& L = D[inst].lv[level];
+  const int idx = lb * TPB + threadIdx.x;
+  if (idx >= L.g.N) return;
+#pragma unroll
+  for (int q = 0; q < NU; ++q) L.e[q][idx] = L.r[q][idx];
 }
 
 template <typename T, int KIND>
@@ -469,7 +483,7 @@ struct Batch {
   static const WorkItem* it(fm_batch* b, const WList& w) { return b->items + w.off; }
 
   template <int TX, int TY, bool SF, bool PIPE>
-  static int launch_v(fm_batch* b, int l) {
+  static int launch_v(fm_batch* b, int l, int dir) {
     constexpr size_t smem = rb_smem_bytes<T, KIND, TX, TY, SF, PIPE>();
     if (smem + 4096 > (size_t)b->inst[0]->smem_optin) return FM_EINVAL;  // does not fit: skip
     static int per_sm = 0;
@@ -484,33 +498,40 @@ struct Batch {
     int grid = w.nblocks;
     if (PIPE && grid > per_sm * b->inst[0]->sms) grid = per_sm * b->inst[0]->sms;
     kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE><<<grid, rb_threads(TX, TY), smem, b->stream>>>(
-        it(b, w), w.n, (const InstDev<T>*)b->D, (const Phys<T>*)b->P, b->ctl, l, w.nblocks);
+        it(b, w), w.n, (const InstDev<T>*)b->D, (const Phys<T>*)b->P, b->ctl, l, w.nblocks, dir);
     FMB_LAUNCHED();
     return FM_OK;
   }
 
-  static int launch_variant(fm_batch* b, int v, int l) {
+  static int launch_variant(fm_batch* b, int v, int l, int dir = 0) {
     switch (v) {
-      case 0: return launch_v<32, 16, false, false>(b, l);
-      case 1: return launch_v<32, 16, false, true>(b, l);
-      case 2: return launch_v<32, 16, true, false>(b, l);
-      case 3: return launch_v<32, 16, true, true>(b, l);
-      case 4: return launch_v<64, 8, false, false>(b, l);
-      case 5: return launch_v<64, 8, false, true>(b, l);
-      case 6: return launch_v<64, 8, true, false>(b, l);
-      case 7: return launch_v<64, 8, true, true>(b, l);
-      case 8: return launch_v<32, 32, false, false>(b, l);
-      case 9: return launch_v<32, 32, false, true>(b, l);
-      case 10: return launch_v<32, 32, true, false>(b, l);
-      default: return launch_v<32, 32, true, true>(b, l);
+      case 0: return launch_v<32, 16, false, false>(b, l, dir);
+      case 1: return launch_v<32, 16, false, true>(b, l, dir);
+      case 2: return launch_v<32, 16, true, false>(b, l, dir);
+      case 3: return launch_v<32, 16, true, true>(b, l, dir);
+      case 4: return launch_v<64, 8, false, false>(b, l, dir);
+      case 5: return launch_v<64, 8, false, true>(b, l, dir);
+      case 6: return launch_v<64, 8, true, false>(b, l, dir);
+      case 7: return launch_v<64, 8, true, true>(b, l, dir);
+      case 8: return launch_v<32, 32, false, false>(b, l, dir);
+      case 9: return launch_v<32, 32, false, true>(b, l, dir);
+      case 10: return launch_v<32, 32, true, false>(b, l, dir);
+      default: return launch_v<32, 32, true, true>(b, l, dir);
     }
   }
 
+  // Sweeps alternate e -> r and r -> e; after an odd count the correction is
+  // copied back from r.
   static int smooth(fm_batch* b, int l, int iters) {
     if (b->w_smooth[0][l].n == 0) return FM_OK;
     for (int k = 0; k < iters; ++k) {
-      const int rc = launch_variant(b, b->rbv[l], l);
+      const int rc = launch_variant(b, b->rbv[l], l, k & 1);
       if (rc) return rc;
+    }
+    if (iters & 1) {
+      const WList& w = b->w_resid[l];
+      kb_copy_back<T, LY::NU><<<w.nblocks, TPB, 0, b->stream>>>(it(b, w), w.n, (const InstDev<T>*)b->D, b->ctl, l);
+      FMB_LAUNCHED();
     }
     return FM_OK;
   }

@@ -417,9 +417,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Start the copies of tile (x0, y0) of level G into buf: 16-byte chunks when
 // the row length is a multiple of the chunk (chunks then never straddle the
-// periodic wrap), single elements otherwise.
+// periodic wrap), single elements otherwise.  The correction is read from G.e
+// (dir = 0) or from G.r (dir = 1).
 template <typename T, int KIND, int TX, int TY, bool SF>
-__device__ __forceinline__ void rb2d_issue(const Lvl<T>& G, T* buf, int x0, int y0) {
+__device__ __forceinline__ void rb2d_issue(const Lvl<T>& G, T* buf, int x0, int y0, int dir) {
   using Gm = RBGeom<TX, TY>;
   constexpr int NU = Layout<KIND, 2>::NU;
   constexpr int NA = rb_arrays<KIND, SF>();
@@ -427,7 +428,7 @@ __device__ __forceinline__ void rb2d_issue(const Lvl<T>& G, T* buf, int x0, int 
   const int nx = G.g.nx, ny = G.g.ny;
   const T* src[NA];
 #pragma unroll
-  for (int q = 0; q < NU; ++q) src[q] = G.e[q];
+  for (int q = 0; q < NU; ++q) src[q] = dir ? G.r[q] : G.e[q];
   src[NU + 0] = G.rk;
   src[NU + 1] = G.cr;
   src[NU + 2] = G.cv[0];
@@ -457,10 +458,12 @@ __device__ __forceinline__ void rb2d_issue(const Lvl<T>& G, T* buf, int x0, int 
   }
 }
 
-// Red pass on tile + ring 1, black pass on the tile, write-back of the tile;
-// the staged tile starts at element `base` of the dynamic shared memory.
+// Red pass on tile + ring 1, black pass on the tile, write-back of the tile
+// to G.r (dir = 0) or G.e (dir = 1); the staged tile starts at element `base`
+// of the dynamic shared memory.
 template <typename T, int KIND, int TX, int TY, bool SF>
-__device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, int base, int x0, int y0) {
+__device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, int base, int x0, int y0,
+                                             int dir) {
   using Gm = RBGeom<TX, TY>;
   constexpr int NU = Layout<KIND, 2>::NU;
   constexpr int SN = Gm::SN, SW = Gm::SW;
@@ -496,7 +499,7 @@ __device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, 
     if (gx < nx && gy < ny) {
       const int sidx = (ty + RB_H) * SW + tx + RB_XO;
 #pragma unroll
-      for (int q = 0; q < NU; ++q) G.e[q][gy * nx + gx] = acc.e(q, sidx);
+      for (int q = 0; q < NU; ++q) (dir ? G.e[q] : G.r[q])[gy * nx + gx] = acc.e(q, sidx);
     }
   }
 }
@@ -504,30 +507,39 @@ __device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, 
 // Single level.  PIPE: persistent blocks over tiles t = blockIdx.x,
 // blockIdx.x + gridDim.x, ..., the next tile's copies in flight while the
 // current one is computed; otherwise one tile per block.
+//
+// The sweep reads the correction from one buffer and writes it to the other
+// (G.e -> G.r for dir = 0, G.r -> G.e for dir = 1; the residual buffer of a
+// level is free while the level is smoothed).  A tile's halo therefore always
+// holds values from before the sweep, whichever tiles have already been
+// written, so the result is exactly one red-black sweep for any block
+// schedule.
 template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
-__global__ void __launch_bounds__(rb_threads(TX, TY)) k_smooth_rb2d(Lvl<T> G, Phys<T> P, int ntx, int ntiles) {
+__global__ void __launch_bounds__(rb_threads(TX, TY)) k_smooth_rb2d(Lvl<T> G, Phys<T> P, int ntx, int ntiles,
+                                                                    int dir) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* buf0 = reinterpret_cast<T*>(smraw);
   constexpr int BUFSTRIDE = rb_arrays<KIND, SF>() * RBGeom<TX, TY>::SN;
   int t = blockIdx.x;
   if (t >= ntiles) return;
   if constexpr (!PIPE) {
-    rb2d_issue<T, KIND, TX, TY, SF>(G, buf0, (t % ntx) * TX, (t / ntx) * TY);
+    rb2d_issue<T, KIND, TX, TY, SF>(G, buf0, (t % ntx) * TX, (t / ntx) * TY, dir);
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    rb2d_compute<T, KIND, TX, TY, SF>(G, P, 0, (t % ntx) * TX, (t / ntx) * TY);
+    rb2d_compute<T, KIND, TX, TY, SF>(G, P, 0, (t % ntx) * TX, (t / ntx) * TY, dir);
   } else {
-    rb2d_issue<T, KIND, TX, TY, SF>(G, buf0, (t % ntx) * TX, (t / ntx) * TY);
+    rb2d_issue<T, KIND, TX, TY, SF>(G, buf0, (t % ntx) * TX, (t / ntx) * TY, dir);
     cp_async_commit();
     for (int k = 0;; ++k) {
       const int tn = t + gridDim.x;
       const bool next = tn < ntiles;
-      if (next) rb2d_issue<T, KIND, TX, TY, SF>(G, buf0 + ((k + 1) & 1) * BUFSTRIDE, (tn % ntx) * TX, (tn / ntx) * TY);
+      if (next)
+        rb2d_issue<T, KIND, TX, TY, SF>(G, buf0 + ((k + 1) & 1) * BUFSTRIDE, (tn % ntx) * TX, (tn / ntx) * TY, dir);
       cp_async_commit();
       cp_async_wait_one();
       __syncthreads();
-      rb2d_compute<T, KIND, TX, TY, SF>(G, P, (k & 1) * BUFSTRIDE, (t % ntx) * TX, (t / ntx) * TY);
+      rb2d_compute<T, KIND, TX, TY, SF>(G, P, (k & 1) * BUFSTRIDE, (t % ntx) * TX, (t / ntx) * TY, dir);
       __syncthreads();
       if (!next) break;
       t = tn;

@@ -39,6 +39,13 @@ __global__ void __launch_bounds__(TPB) k_mass(const double* rho, int N, double* 
 }
 
 // Standalone float64 transfers (row-level entry points).
+// out = in, converted element by element.
+template <typename A, typename B>
+__global__ void __launch_bounds__(TPB) k_convert(const A* in, B* out, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) out[i] = (B)in[i];
+}
+
 __global__ void k_restrict_one(const double* fine, double* coarse, Geo F, Geo C, int dim) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= C.N) return;
@@ -90,6 +97,13 @@ __global__ void k_prolong_one(const double* coarse, double* fine, Geo F, Geo C, 
 // --------------------------------------------------------------------------
 // Host driver
 // --------------------------------------------------------------------------
+static cudaMemcpyKind kind_in(int where) {
+  return where == FM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+static cudaMemcpyKind kind_out(int where) {
+  return where == FM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
 #define FM_CUDA(call)                                   \
   do {                                                  \
     cudaError_t err__ = (call);                         \
@@ -107,9 +121,10 @@ __global__ void k_prolong_one(const double* coarse, double* fine, Geo F, Geo C, 
 
 // Launch variant (TX, TY, SF, PIPE) of the 2-D fused sweep on level L.
 template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
-static int launch_rb_v(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s) {
+static int launch_rb_v(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int dir) {
   constexpr size_t smem = rb_smem_bytes<T, KIND, TX, TY, SF, PIPE>();
   if (smem + 4096 > (size_t)st->smem_optin) return FM_EINVAL;  // variant does not fit on this device
+  if (!L.r[0]) return FM_EINVAL;                               // no second correction buffer
   static int per_sm = 0;
   if (!per_sm) {
     if (cudaFuncSetAttribute(k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -125,25 +140,25 @@ static int launch_rb_v(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStre
   const int ntiles = ntx * ((L.g.ny + TY - 1) / TY);
   int grid = ntiles;
   if (PIPE && grid > per_sm * st->sms) grid = per_sm * st->sms;
-  k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE><<<grid, rb_threads(TX, TY), smem, s>>>(L, P, ntx, ntiles);
+  k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE><<<grid, rb_threads(TX, TY), smem, s>>>(L, P, ntx, ntiles, dir);
   return FM_OK;
 }
 
 template <typename T, int KIND>
-static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s) {
+static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int dir = 0) {
   switch (v) {
-    case 0: return launch_rb_v<T, KIND, 32, 16, false, false>(st, L, P, s);
-    case 1: return launch_rb_v<T, KIND, 32, 16, false, true>(st, L, P, s);
-    case 2: return launch_rb_v<T, KIND, 32, 16, true, false>(st, L, P, s);
-    case 3: return launch_rb_v<T, KIND, 32, 16, true, true>(st, L, P, s);
-    case 4: return launch_rb_v<T, KIND, 64, 8, false, false>(st, L, P, s);
-    case 5: return launch_rb_v<T, KIND, 64, 8, false, true>(st, L, P, s);
-    case 6: return launch_rb_v<T, KIND, 64, 8, true, false>(st, L, P, s);
-    case 7: return launch_rb_v<T, KIND, 64, 8, true, true>(st, L, P, s);
-    case 8: return launch_rb_v<T, KIND, 32, 32, false, false>(st, L, P, s);
-    case 9: return launch_rb_v<T, KIND, 32, 32, false, true>(st, L, P, s);
-    case 10: return launch_rb_v<T, KIND, 32, 32, true, false>(st, L, P, s);
-    default: return launch_rb_v<T, KIND, 32, 32, true, true>(st, L, P, s);
+    case 0: return launch_rb_v<T, KIND, 32, 16, false, false>(st, L, P, s, dir);
+    case 1: return launch_rb_v<T, KIND, 32, 16, false, true>(st, L, P, s, dir);
+    case 2: return launch_rb_v<T, KIND, 32, 16, true, false>(st, L, P, s, dir);
+    case 3: return launch_rb_v<T, KIND, 32, 16, true, true>(st, L, P, s, dir);
+    case 4: return launch_rb_v<T, KIND, 64, 8, false, false>(st, L, P, s, dir);
+    case 5: return launch_rb_v<T, KIND, 64, 8, false, true>(st, L, P, s, dir);
+    case 6: return launch_rb_v<T, KIND, 64, 8, true, false>(st, L, P, s, dir);
+    case 7: return launch_rb_v<T, KIND, 64, 8, true, true>(st, L, P, s, dir);
+    case 8: return launch_rb_v<T, KIND, 32, 32, false, false>(st, L, P, s, dir);
+    case 9: return launch_rb_v<T, KIND, 32, 32, false, true>(st, L, P, s, dir);
+    case 10: return launch_rb_v<T, KIND, 32, 32, true, false>(st, L, P, s, dir);
+    default: return launch_rb_v<T, KIND, 32, 32, true, true>(st, L, P, s, dir);
   }
 }
 
@@ -361,19 +376,72 @@ struct Solver {
     return FM_OK;
   }
 
+  // Smoother row: sweeps on level 0 for caller-supplied e and f (float64,
+  // staged through the float64 scratch r64 and rounded to T).
+  static int smooth_row(fm_state* st, double* const* e, const double* const* f, int sweeps, int variant,
+                        int where) {
+    if (variant < FM_SWEEP_TWO_COLOUR || variant >= RB_NVAR || (DIM == 3 && variant >= 0)) return FM_EINVAL;
+    const Geo G = st->lv[0].g;
+    cudaStream_t s = st->stream;
+    // coefficient copies of the iterate (mixed path), as at the start of a cycle
+    Fields64 F = make_fields(st);
+    Resid64Out O = resid_out(st, true, nullptr);
+    int rc = launch_resid64(st, F, O, G, st->lv[0].h, make_phys<double>(st));
+    if (rc) return rc;
+    Lvl<T> L = make_lvl<T>(st, 0);
+    const size_t bytes = (size_t)G.N * sizeof(double);
+    for (int q = 0; q < LY::NU; ++q) {
+      FM_CUDA(cudaMemcpyAsync(st->r64[q], e[q], bytes, kind_in(where), s));
+      k_convert<double, T><<<nblocks(G.N), TPB, 0, s>>>(st->r64[q], L.e[q], G.N);
+      FM_LAUNCHED();
+      FM_CUDA(cudaMemcpyAsync(st->r64[q], f[q], bytes, kind_in(where), s));
+      k_convert<double, T><<<nblocks(G.N), TPB, 0, s>>>(st->r64[q], L.f[q], G.N);
+      FM_LAUNCHED();
+    }
+    const Phys<T> P = make_phys<T>(st);
+    const int v = variant >= 0 ? variant : st->rbv[0];
+    const int nfused = (DIM == 2 && variant != FM_SWEEP_TWO_COLOUR && (st->fused_rb || variant >= 0))
+                           ? (sweeps & ~1) : 0;
+    for (int it = 0; it < sweeps; ++it) {
+      if (it < nfused) {
+        if constexpr (DIM == 2) {
+          rc = launch_rb<T, KIND>(st, v, L, P, s, it & 1);
+          if (rc) return rc;
+        }
+        FM_LAUNCHED();
+      } else {
+        for (int color = 0; color < 2; ++color) {
+          k_smooth<T, KIND, DIM><<<nblocks(G.N / 2), TPB, 0, s>>>(L, P, color);
+          FM_LAUNCHED();
+        }
+      }
+    }
+    for (int q = 0; q < LY::NU; ++q) {
+      k_convert<T, double><<<nblocks(G.N), TPB, 0, s>>>(L.e[q], st->r64[q], G.N);
+      FM_LAUNCHED();
+      FM_CUDA(cudaMemcpyAsync(e[q], st->r64[q], bytes, kind_out(where), s));
+    }
+    FM_CUDA(cudaStreamSynchronize(s));
+    return FM_OK;
+  }
+
   static int smooth(fm_state* st, int l, const Phys<T>& P, int iters) {
     cudaStream_t s = st->stream;
     Lvl<T> L = make_lvl<T>(st, l);
     const int half = L.g.N / 2;
     const bool prof = st->prof && !st->capturing && l == 0;
-    const bool fused = DIM == 2 && st->fused_rb;
+    // Fused sweeps run in pairs (e -> r, then r -> e), so the correction is
+    // back in e after each pair; an odd last sweep runs in place as two
+    // colour launches.
+    const int nfused = (DIM == 2 && st->fused_rb) ? (iters & ~1) : 0;
     for (int it = 0; it < iters; ++it) {
+      const bool fused = it < nfused;
       const int nlaunch = fused ? 1 : 2;
       for (int color = 0; color < nlaunch; ++color) {
         if (prof && st->npev + 2 <= MAXEV) FM_CUDA(cudaEventRecord(st->pev[st->npev], s));
         if (fused) {
           if constexpr (DIM == 2) {
-            const int rc = launch_rb<T, KIND>(st, st->rbv[l], L, P, s);
+            const int rc = launch_rb<T, KIND>(st, st->rbv[l], L, P, s, it & 1);
             if (rc) return rc;
           }
         } else {
@@ -604,6 +672,16 @@ static int dispatch_prepare(fm_state* st) {
 }
 
 template <typename T>
+static int dispatch_smooth_row(fm_state* st, double* const* e, const double* const* f, int sweeps, int variant,
+                               int where) {
+  if (st->kind == FM_PFC)
+    return st->dim == 2 ? Solver<T, KPFC, 2>::smooth_row(st, e, f, sweeps, variant, where)
+                        : Solver<T, KPFC, 3>::smooth_row(st, e, f, sweeps, variant, where);
+  return st->dim == 2 ? Solver<T, KCDFT, 2>::smooth_row(st, e, f, sweeps, variant, where)
+                      : Solver<T, KCDFT, 3>::smooth_row(st, e, f, sweeps, variant, where);
+}
+
+template <typename T>
 static int dispatch_resid(fm_state* st, double* const* r, double* nr) {
   if (st->kind == FM_PFC)
     return st->dim == 2 ? Solver<T, KPFC, 2>::residual64(st, r, nr) : Solver<T, KPFC, 3>::residual64(st, r, nr);
@@ -652,7 +730,7 @@ static size_t carve(fm_state* st, char* base) {
     for (int q = 0; q < MAXU; ++q) {
       B.e[q] = q < st->nu ? C.take(N * es) : nullptr;
       B.f[q] = q < st->nu ? C.take(N * es) : nullptr;
-      B.r[q] = (q < st->nu && l + 1 < st->nlev) ? C.take(N * es) : nullptr;
+      B.r[q] = q < st->nu ? C.take(N * es) : nullptr;  // also the second buffer of the fused sweep
       B.eh[q] = (q < st->nu && l > 0) ? C.take(N * es) : nullptr;
     }
     const bool alias = (l == 0 && st->prm.precision == FM_FP64);
@@ -906,13 +984,6 @@ int fm_profile_read(const fm_state* st, double* smoother_ms, long long* smoother
   return FM_OK;
 }
 
-static cudaMemcpyKind kind_in(int where) {
-  return where == FM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-}
-static cudaMemcpyKind kind_out(int where) {
-  return where == FM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-}
-
 int fm_set_fields(fm_state* st, const double* rho, const double* const* vel, int where) {
   if (!st || !rho || !vel || (where != FM_HOST && where != FM_DEVICE)) return FM_EINVAL;
   const size_t bytes = (size_t)st->lv[0].g.N * sizeof(double);
@@ -982,6 +1053,15 @@ int fm_residual(fm_state* st, const double* const* g, double* const* r, double* 
     FM_CUDA(cudaStreamSynchronize(st->stream));
   }
   return rc;
+}
+
+int fm_smooth(fm_state* st, double* const* e, const double* const* f, int sweeps, int variant, int where) {
+  if (!st || !e || !f || sweeps < 0 || (where != FM_HOST && where != FM_DEVICE)) return FM_EINVAL;
+  if (!st->prepared) return FM_EINVAL;
+  for (int q = 0; q < st->nu; ++q)
+    if (!e[q] || !f[q]) return FM_EINVAL;
+  return st->prm.precision == FM_MIXED ? dispatch_smooth_row<float>(st, e, f, sweeps, variant, where)
+                                       : dispatch_smooth_row<double>(st, e, f, sweeps, variant, where);
 }
 
 int fm_energy(fm_state* st, double* E, double* F, double* KE) {

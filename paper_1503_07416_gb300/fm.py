@@ -82,6 +82,7 @@ _SIGS = {
     "fm_restrict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "fm_prolong_add": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "fm_levels": (C.c_int, [C.c_void_p]),
+    "fm_smooth": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int]),
     "fm_create_batch": (C.c_int, [C.c_int, C.POINTER(fm_grid), C.POINTER(fm_params), C.POINTER(fm_functional),
                                   C.POINTER(C.c_void_p)]),
     "fm_destroy_batch": (None, [C.c_void_p]),
@@ -221,6 +222,17 @@ def fm_residual(st, g, r=None):
     rv = _vec(r) if r is not None else None
     _check(lib().fm_residual(st, _vec(g), rv, C.byref(nrm), w), "fm_residual")
     return nrm.value
+
+
+FM_SWEEP_AUTO = -1
+FM_SWEEP_TWO_COLOUR = -2
+
+
+def fm_smooth(st, e, f, sweeps, variant=FM_SWEEP_AUTO):
+    """Smoother row: `sweeps` red-black sweeps on the finest grid; e (list of
+    nu float64 arrays) is updated in place."""
+    w = _where(list(e) + list(f))
+    _check(lib().fm_smooth(st, _vec(e), _vec(f), int(sweeps), int(variant), w), "fm_smooth")
 
 
 def fm_convolve(st, rho, out):

@@ -114,3 +114,36 @@ def test_batch_failure_is_isolated():
         r, _ = b.get_fields(i)
         assert not np.array_equal(r, ens[i][0])
     b.close()
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_batch_odd_sweep_counts(precision):
+    """V(1,3): every smoothing stage has an odd number of fused sweeps, so the
+    batch copies the correction back after the last one; two instances (one
+    of them several tile waves large) against the oracle with the same cycle
+    and against the single-instance solver."""
+    sizes = [32, (256, 192)]
+    ens = _ensemble("pfc", sizes, 11)
+    h, tol = 0.9, 1e-12
+    prm = dict(kind="pfc", dim=2, h=h, alpha=0.6, tol=tol)
+    b = fm.Batch("pfc", sizes, h, alpha=0.6, precision=precision, tol=tol, w_damp=0.0, max_cycles=80,
+                 nu1=1, nu2=3)
+    for i, (rho, vel, dt) in enumerate(ens):
+        b.set_fields(i, rho, vel)
+    info = b.step([dt for _, _, dt in ens])
+    bound = 1e-10 if precision == fm.FM_FP64 else 1e-8
+    for i, (rho, vel, dt) in enumerate(ens):
+        assert info[i].res <= tol
+        rg, vg = b.get_fields(i)
+        P, opts, J = oracle_setup(rho, dict(prm, dt=dt), w_damp=0.0, tol=tol)
+        opts.nu1, opts.nu2 = 1, 3
+        ro, vo, _ = S.step(rho, vel, P, opts, J=J)
+        errs = [rel(rg, ro)] + [rel(a, c) for a, c in zip(vg, vo)]
+        assert max(errs) <= bound, (i, errs)
+        sol = gpu_solver(rho, dict(prm, dt=dt), precision=precision, w_damp=0.0, tol=tol, nu1=1, nu2=3)
+        sol.set_fields(rho, vel)
+        sol.step(dt)
+        rs, vs = sol.get_fields()
+        sol.close()
+        assert rel(rg, rs) <= 1e-12 and all(rel(a, c) <= 1e-12 for a, c in zip(vg, vs))
+    b.close()

@@ -1,0 +1,153 @@
+"""Smoother row (App. G.1-G.3): red-black point-block Gauss-Seidel sweeps
+through fm_smooth, on the coefficient iterate g^0 of a prepared step and a
+right-hand side f = S - N(g^0) computed by the oracle, against the oracle's own
+red-black sweeps of N(g) = S from g^0 (the correction e and the oracle's
+increment g - g^0 solve the same point systems).
+
+CDFT is compared with the oracle directly: its point block is linear in the
+point's own unknowns, so both sides solve identical systems.  The PFC point
+block differs by design (the oracle linearises the cubic as App. G.2 prints
+it, the CUDA update evaluates it exactly), so for PFC every fused tile
+variant is compared with the red launch + black launch pair instead.  Sizes
+are chosen so that every variant runs its tiles in several waves: a fused
+sweep that read a neighbour tile's already updated values would show here.
+
+Tolerances: float64 1e-11 of max |increment| (the increments are O(1e-2),
+the fields O(1), so this is a few hundred ulps of the fields); mixed 2e-5
+(float32 point solves of a float32-rounded f and coefficients)."""
+import numpy as np
+import pytest
+
+from oracle import scheme as S
+from paper_1503_07416_gb300 import fm
+from tests.helpers import gpu_solver, oracle_setup
+
+pytestmark = pytest.mark.gpu
+
+TOL = {fm.FM_FP64: 1e-11, fm.FM_MIXED: 2e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_07416_gb300 import build
+    build.build_library()
+    fm.lib()
+
+
+def _case(kind, shape, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "cdft":
+        rho = 0.3 + 0.05 * rng.uniform(0, 1, shape)
+        prm = dict(kind="cdft", dim=2, h=34.0 / shape[1], dt=0.02, nu=2.362, delta=1e-10)
+    else:
+        rho = 0.8 + 0.05 * rng.uniform(-1, 1, shape)
+        prm = dict(kind="pfc", dim=2, h=0.9, dt=0.02, alpha=0.6)
+    vel = [0.05 * rng.standard_normal(shape) for _ in range(2)]
+    return rho, vel, prm
+
+
+def _oracle(rho, vel, prm, w, sweeps):
+    """g^0, f = S - N(g^0) and the increment of `sweeps` oracle sweeps."""
+    P, _, J = oracle_setup(rho, prm, w_damp=w)
+    om = S.vorticity(vel, P.h)
+    C = S.conv_fft(J, rho, P.h) if P.kind == S.CDFT else None
+    Sx = S.source(rho, vel, om, P, C)
+    c = S.Coeffs(rho, om)
+    g0 = S.initial_iterate(rho, vel, P)
+    f = S.residual(g0, Sx, c, P)
+    g = [x.copy() for x in g0]
+    for _ in range(sweeps):
+        S.smooth(g, Sx, c, P)
+    return f, [a - b for a, b in zip(g, g0)]
+
+
+def _gpu(rho, vel, prm, f, precision, w, sweeps, variant):
+    sol = gpu_solver(rho, prm, precision=precision, w_damp=w)
+    try:
+        sol.set_fields(rho, vel)
+        fm.fm_prepare(sol.handle, prm["dt"])
+        e = [np.zeros_like(rho) for _ in f]
+        fm.fm_smooth(sol.handle, e, [np.ascontiguousarray(x) for x in f], sweeps, variant)
+        return e
+    finally:
+        sol.close()
+
+
+def _close(a, b, tol):
+    for q, (x, y) in enumerate(zip(a, b)):
+        scale = float(np.max(np.abs(y)))
+        err = float(np.max(np.abs(x - y)))
+        assert err <= tol * scale, (q, err, scale)
+
+
+@pytest.mark.parametrize("w", [0.0, 0.5])
+@pytest.mark.parametrize("sweeps", [1, 2, 3])
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_cdft_sweeps_match_oracle(precision, sweeps, w):
+    """As fm_step runs them (fused pairs, an odd last sweep as two launches),
+    on a 64 x 32 grid (CDFT sizes are powers of two for the FFT)."""
+    rho, vel, prm = _case("cdft", (32, 64), 3)
+    f, de = _oracle(rho, vel, prm, w, sweeps)
+    e = _gpu(rho, vel, prm, f, precision, w, sweeps, fm.FM_SWEEP_AUTO)
+    _close(e, de, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_cdft_two_colour_sweeps_match_oracle(precision):
+    rho, vel, prm = _case("cdft", (64, 32), 4)
+    f, de = _oracle(rho, vel, prm, 0.5, 2)
+    e = _gpu(rho, vel, prm, f, precision, 0.5, 2, fm.FM_SWEEP_TWO_COLOUR)
+    _close(e, de, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_cdft_every_fused_variant_matches_oracle_over_many_waves(precision):
+    """512 x 1024: 512 to 1024 tiles per sweep, more than the device holds at
+    once for every variant."""
+    rho, vel, prm = _case("cdft", (512, 1024), 5)
+    f, de = _oracle(rho, vel, prm, 0.0, 2)
+    for v in range(12):
+        try:
+            e = _gpu(rho, vel, prm, f, precision, 0.0, 2, v)
+        except fm.FMError as err:  # variant too large for shared memory
+            assert err.code == fm.FM_EINVAL and precision == fm.FM_FP64
+            continue
+        _close(e, de, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_pfc_every_fused_variant_matches_two_colour_launches(precision):
+    """PFC, 1002 x 1000 points (sides not multiples of any tile; rows not a
+    whole number of 16-byte chunks, so the tiles are staged element by
+    element), 4 sweeps."""
+    rho, vel, prm = _case("pfc", (1000, 1002), 6)
+    f, _ = _oracle(rho, vel, prm, 0.0, 0)
+    ref = _gpu(rho, vel, prm, f, precision, 0.0, 4, fm.FM_SWEEP_TWO_COLOUR)
+    tol = 1e-12 if precision == fm.FM_FP64 else 2e-5
+    for v in range(12):
+        try:
+            e = _gpu(rho, vel, prm, f, precision, 0.0, 4, v)
+        except fm.FMError as err:
+            assert err.code == fm.FM_EINVAL and precision == fm.FM_FP64
+            continue
+        _close(e, ref, tol)
+
+
+def test_smooth_row_rejects_bad_arguments():
+    rho, vel, prm = _case("cdft", (32, 32), 7)
+    sol = gpu_solver(rho, prm)
+    sol.set_fields(rho, vel)
+    e = [np.zeros_like(rho) for _ in range(3)]
+    with pytest.raises(fm.FMError):  # before fm_prepare
+        fm.fm_smooth(sol.handle, e, e, 1)
+    fm.fm_prepare(sol.handle, prm["dt"])
+    for variant in (-3, 12):
+        with pytest.raises(fm.FMError):
+            fm.fm_smooth(sol.handle, e, e, 1, variant)
+    with pytest.raises(fm.FMError):
+        fm.fm_smooth(sol.handle, e, e, -1)
+    fm.fm_smooth(sol.handle, e, e, 0)
+    sol.close()
