@@ -243,12 +243,18 @@ int fm_batch_time_smoother(fm_batch* b, int iters, double* ms_per_launch, long l
 
 /* ---- Measurement (no counterpart in the paper). ---- */
 
+/* Number of variants of the 2-D fused red-black sweep. */
+#define FM_SWEEP_VARIANTS 18
+
 /* Variant of the 2-D fused red-black sweep the autotuner chose for `level`
- * at fm_create (v >> 2: tile 32x16, 64x8 or 32x32; bit 1: right-hand side
- * staged in shared memory; bit 0: persistent double-buffered blocks), and its
- * timings of all 12 variants in ms per sweep (ms_per_variant may be null; 0
- * for levels that were not tuned).  Setting the environment variable
- * FM_RB_VARIANT=v before fm_create fixes the variant (no timing). */
+ * at fm_create, and its timings of all FM_SWEEP_VARIANTS variants in ms per
+ * sweep (ms_per_variant may be null; 0 for levels that were not tuned and for
+ * variants that do not fit in shared memory).  Variants 0..11 are the tile
+ * form (v >> 2: tile 32x16, 64x8 or 32x32; bit 1: right-hand side staged in
+ * shared memory; bit 0: persistent double-buffered blocks); 12..17 the
+ * row-marching form (strip width 64 for 12..14, 128 for 15..17; 16, 32 or 64
+ * rows per block).  Setting the environment variable FM_RB_VARIANT=v before
+ * fm_create fixes the variant (no timing). */
 int fm_tuning(const fm_state* st, int level, int* variant, float* ms_per_variant);
 
 /* Enable (1) or disable (0) CUDA-event timing of every finest-level smoother

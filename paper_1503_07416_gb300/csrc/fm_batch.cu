@@ -89,7 +89,7 @@ __device__ __forceinline__ void smem_copy(S* dst, const S* src) {
 // ..., two shared-memory buffers, the next tile's copies in flight while the
 // current one is computed; otherwise one tile per block.
 template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
-__global__ void __launch_bounds__(rb_threads(TX, TY)) kb_smooth_rb2d(const WorkItem* items, int nitems, const InstDev<T>* D,
+__global__ void __launch_bounds__(rb_threads(TX, TY), rb_minb<T>(TX, TY)) kb_smooth_rb2d(const WorkItem* items, int nitems, const InstDev<T>* D,
                                                              const Phys<T>* P, const Ctl* ctl, int level,
                                                              int ntiles, int dir) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -140,6 +140,24 @@ __global__ void __launch_bounds__(rb_threads(TX, TY)) kb_smooth_rb2d(const WorkI
       t = tn;
     }
   }
+}
+
+// Fused sweep in the row-marching form over the strips of level `level` of
+// all instances (work item aux = strips per row of blocks).
+template <typename T, int KIND, int TX>
+__global__ void __launch_bounds__(march_threads(TX)) kb_smooth_march(const WorkItem* items, int nitems,
+                                                                     const InstDev<T>* D, const Phys<T>* P,
+                                                                     const Ctl* ctl, int level, int ly, int dir) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ Lvl<T> Gs;
+  FM_BATCH_HEAD();
+  if (!inst_active(ctl, inst)) return;
+  smem_copy(&Gs, &D[inst].lv[level]);
+  __syncthreads();
+  const int nstrips = items[k_].aux;
+  const int strip = lb % nstrips, seg = lb / nstrips;
+  const int y0 = seg * ly;
+  march_sweep<T, KIND, TX>(Gs, P[inst], reinterpret_cast<T*>(smraw), strip * TX, y0, min(y0 + ly, Gs.g.ny), dir);
 }
 
 // e = r at every point of level `level` (after an odd number of fused sweeps).
@@ -313,10 +331,10 @@ struct fm_batch {
   // work lists
   std::vector<WorkItem> hitems;
   WList w_fine, w_resid64, w_inject;
-  WList w_smooth[3][MAXLEV];  // per tile shape (32x16, 64x8, 32x32)
+  WList w_smooth[3 + 6][MAXLEV];  // per tile shape (32x16, 64x8, 32x32), then per marching variant
   WList w_resid[MAXLEV], w_restrict[MAXLEV], w_crhs[MAXLEV], w_prolong[MAXLEV];
   int rbv[MAXLEV];           // chosen fused-sweep variant per level
-  float rbt[MAXLEV][12];     // autotuner timings (ms per launch)
+  float rbt[MAXLEV][RB_NVAR];  // autotuner timings (ms per launch)
   // graph
   cudaStream_t stream;
   cudaStream_t user_stream;
@@ -455,8 +473,8 @@ struct Batch {
     }
     b->w_inject = add_list(b, v);
     for (int l = 0; l < b->maxdepth; ++l) {
-      std::vector<std::pair<int, int>> ts[3], rs, rr, cr, pr;
-      std::vector<int> aux[3];
+      std::vector<std::pair<int, int>> ts[9], rs, rr, cr, pr;
+      std::vector<int> aux[9];
       for (int i = 0; i < b->count; ++i) {
         fm_state* st = b->inst[i];
         if (st->small_from <= l) continue;
@@ -467,12 +485,18 @@ struct Batch {
           ts[sh].push_back({i, ntx * nty});
           aux[sh].push_back(ntx);
         }
+        for (int m = 0; m < 6; ++m) {  // marching variants RB_NTILE + m
+          const int TX = march_tx(RB_NTILE + m), LYR = march_ly(RB_NTILE + m);
+          const int nstrips = (g.nx + TX - 1) / TX, nseg = (g.ny + LYR - 1) / LYR;
+          ts[3 + m].push_back({i, nstrips * nseg});
+          aux[3 + m].push_back(nstrips);
+        }
         rs.push_back({i, nblocks(g.N)});
         rr.push_back({i, nblocks(gc.N)});
         cr.push_back({i, nblocks(gc.N)});
         pr.push_back({i, nblocks(g.N)});
       }
-      for (int sh = 0; sh < 3; ++sh) b->w_smooth[sh][l] = add_list(b, ts[sh], &aux[sh]);
+      for (int sh = 0; sh < 9; ++sh) b->w_smooth[sh][l] = add_list(b, ts[sh], &aux[sh]);
       b->w_resid[l] = add_list(b, rs);
       b->w_restrict[l] = add_list(b, rr);
       b->w_crhs[l] = add_list(b, cr);
@@ -503,6 +527,24 @@ struct Batch {
     return FM_OK;
   }
 
+  // Marching form, variant v (strip width TX) over all instances.
+  template <int TX>
+  static int launch_m(fm_batch* b, int l, int dir, int v) {
+    constexpr size_t smem = march_smem_bytes<T, KIND, TX>();
+    if (smem + 4096 > (size_t)b->inst[0]->smem_optin) return FM_EINVAL;  // does not fit: skip
+    static bool attr = false;
+    if (!attr) {
+      FMB_CUDA(cudaFuncSetAttribute(kb_smooth_march<T, KIND, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      attr = true;
+    }
+    const WList& w = b->w_smooth[3 + v - RB_NTILE][l];
+    kb_smooth_march<T, KIND, TX><<<w.nblocks, march_threads(TX), smem, b->stream>>>(
+        it(b, w), w.n, (const InstDev<T>*)b->D, (const Phys<T>*)b->P, b->ctl, l, march_ly(v), dir);
+    FMB_LAUNCHED();
+    return FM_OK;
+  }
+
   static int launch_variant(fm_batch* b, int v, int l, int dir = 0) {
     switch (v) {
       case 0: return launch_v<32, 16, false, false>(b, l, dir);
@@ -516,7 +558,13 @@ struct Batch {
       case 8: return launch_v<32, 32, false, false>(b, l, dir);
       case 9: return launch_v<32, 32, false, true>(b, l, dir);
       case 10: return launch_v<32, 32, true, false>(b, l, dir);
-      default: return launch_v<32, 32, true, true>(b, l, dir);
+      case 11: return launch_v<32, 32, true, true>(b, l, dir);
+      case 12: return launch_m<64>(b, l, dir, 12);
+      case 13: return launch_m<64>(b, l, dir, 13);
+      case 14: return launch_m<64>(b, l, dir, 14);
+      case 15: return launch_m<128>(b, l, dir, 15);
+      case 16: return launch_m<128>(b, l, dir, 16);
+      default: return launch_m<128>(b, l, dir, 17);
     }
   }
 

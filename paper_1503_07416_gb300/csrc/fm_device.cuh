@@ -20,16 +20,47 @@ static inline int nblocks(long long work) { return (int)((work + TPB - 1) / TPB)
 // --------------------------------------------------------------------------
 // Smoother point update (correction form)
 // --------------------------------------------------------------------------
+// Constants of the point update on one level (grid spacing h), formed once
+// per thread outside the point loops.
+template <typename T>
+struct PtK {
+  T ih2;    // 1/h^2
+  T c_div;  // s/(4h): continuity flux difference
+  T c_sih;  // s/h: kinetic-energy and chemical-potential gradients (times rho^k)
+  T c_v;    // s gamma/(2h^2): viscous neighbour sum
+  T c_ad;   // s gamma d/h^2: viscous diagonal (reading R2)
+  T c_b;    // sigma s/2: vorticity coupling (times rho^k omega^k)
+};
+
+template <typename T, int DIM>
+__device__ __forceinline__ PtK<T> make_ptk(const Phys<T>& P, T h) {
+  PtK<T> K;
+  const T ih = T(1) / h;
+  K.ih2 = ih * ih;
+  K.c_div = P.s * T(0.25) * ih;
+  K.c_sih = P.s * ih;
+  K.c_v = T(0.5) * P.s * P.gamma * K.ih2;
+  K.c_ad = P.s * P.gamma * T(DIM) * K.ih2;
+  K.c_b = T(0.5) * P.sigma * P.s;
+  return K;
+}
+
+// Reciprocal of the point block's velocity determinant: the float32 smoother
+// uses the hardware approximate division (its errors only change how fast
+// the float64 outer iteration converges); float64 divides exactly.
+__device__ __forceinline__ float rcp_blk(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_blk(double x) { return 1.0 / x; }
+
 // Point-block update of one point, written against an accessor A that
-// provides e(q, i) / set_e(q, i, v), rk(i), cr(i), cv(d, i), f(q, fc),
-// om(d, fc) and h (A is a level descriptor in any memory, or a shared-memory
-// tile with compile-time strides).  Neighbours are at n.m / n.p; the
-// right-hand side and omega^k are read at index fc.
+// provides e(q, i) / set_e(q, i, v), rk(i), cr(i), cv(d, i), f(q, fc) and
+// om(d, fc) (A is a level descriptor in any memory, or a shared-memory tile
+// with compile-time strides); K holds the level constants.  Neighbours are
+// at n.m / n.p; the right-hand side and omega^k are read at index fc.
 template <typename T, int KIND, int DIM, class A>
-__device__ __forceinline__ void smooth_point_a(const A& a, const Phys<T>& P, const Nb& n, int fc) {
+__device__ __forceinline__ void smooth_point_a(const A& a, const Phys<T>& P, const PtK<T>& K, const Nb& n,
+                                               int fc) {
   using LY = Layout<KIND, DIM>;
-  const T ih = T(1) / a.h();
-  const T ih2 = ih * ih;
+  const T ih2 = K.ih2;
   const int c = n.c;
   const T rkc = a.rk(c);
   const T crc = a.cr(c);
@@ -42,7 +73,7 @@ __device__ __forceinline__ void smooth_point_a(const A& a, const Phys<T>& P, con
 #pragma unroll
   for (int d = 0; d < DIM; ++d)
     div += a.rk(n.p[d]) * a.e(1 + d, n.p[d]) - a.rk(n.m[d]) * a.e(1 + d, n.m[d]);
-  T er = a.f(0, fc) - P.s * T(0.25) * ih * div;
+  T er = a.f(0, fc) - K.c_div * div;
   {
     const T x = crc + er;
     if (x <= T(0)) er = sqrt_t(x * x + P.delta * P.delta) - crc;  // Sec. 6 projection
@@ -90,14 +121,13 @@ __device__ __forceinline__ void smooth_point_a(const A& a, const Phys<T>& P, con
   for (int d = 0; d < DIM; ++d) {
     const T dq = qc(n.p[d]) - qc(n.m[d]);
     const T dm = mc(n.p[d]) - mc(n.m[d]);
-    rhs[d] = a.f(1 + d, fc) - P.s * rkc * ih * (T(0.25) * dq + T(0.5) * dm)
-           + T(0.5) * P.s * P.gamma * ih2 * nbs(1 + d);
+    rhs[d] = a.f(1 + d, fc) - K.c_sih * rkc * (T(0.25) * dq + T(0.5) * dm) + K.c_v * nbs(1 + d);
   }
-  const T Ad = rkc + P.s * P.gamma * T(DIM) * ih2;
-  const T bs = T(0.5) * P.sigma * P.s * rkc;
+  const T Ad = rkc + K.c_ad;
+  const T bs = K.c_b * rkc;
   if constexpr (DIM == 2) {
     const T b = bs * a.om(0, fc);
-    const T inv = T(1) / (Ad * Ad + b * b);
+    const T inv = rcp_blk(Ad * Ad + b * b);
     eg[1] = (Ad * rhs[0] + b * rhs[1]) * inv;
     eg[2] = (Ad * rhs[1] - b * rhs[0]) * inv;
   } else {
@@ -106,7 +136,7 @@ __device__ __forceinline__ void smooth_point_a(const A& a, const Phys<T>& P, con
     for (int d = 0; d < 3; ++d) b[d] = bs * a.om(d, fc);
     cross<T, 3>(b, rhs, bx);
     const T bdy = b[0] * rhs[0] + b[1] * rhs[1] + b[2] * rhs[2];
-    const T inv = T(1) / (Ad * (Ad * Ad + b[0] * b[0] + b[1] * b[1] + b[2] * b[2]));
+    const T inv = rcp_blk(Ad * (Ad * Ad + b[0] * b[0] + b[1] * b[1] + b[2] * b[2]));
 #pragma unroll
     for (int d = 0; d < 3; ++d) eg[1 + d] = (Ad * Ad * rhs[d] - Ad * bx[d] + bdy * b[d]) * inv;
   }
@@ -133,15 +163,15 @@ struct LvlAcc {
 };
 
 template <typename T, int KIND, int DIM>
-__device__ __forceinline__ void smooth_point_ex(const Lvl<T>& L, const Phys<T>& P, const Nb& n,
+__device__ __forceinline__ void smooth_point_ex(const Lvl<T>& L, const Phys<T>& P, const PtK<T>& K, const Nb& n,
                                                 T* const* Fr, const T* const* Om, int fc) {
   LvlAcc<T> a{L, Fr, Om};
-  smooth_point_a<T, KIND, DIM>(a, P, n, fc);
+  smooth_point_a<T, KIND, DIM>(a, P, K, n, fc);
 }
 
 template <typename T, int KIND, int DIM>
-__device__ __forceinline__ void smooth_point(const Lvl<T>& L, const Phys<T>& P, const Nb& n) {
-  smooth_point_ex<T, KIND, DIM>(L, P, n, L.f, L.om, n.c);
+__device__ __forceinline__ void smooth_point(const Lvl<T>& L, const Phys<T>& P, const PtK<T>& K, const Nb& n) {
+  smooth_point_ex<T, KIND, DIM>(L, P, K, n, L.f, L.om, n.c);
 }
 
 // --------------------------------------------------------------------------
@@ -292,7 +322,7 @@ __global__ void __launch_bounds__(TPB) k_smooth(Lvl<T> L, Phys<T> P, int color) 
   int i, j, k;
   if (!colour_point(t, color, L.g, i, j, k)) return;
   const Nb n = neighbours(i, j, k, L.g);
-  smooth_point<T, KIND, DIM>(L, P, n);
+  smooth_point<T, KIND, DIM>(L, P, make_ptk<T, DIM>(P, L.h), n);
 }
 
 template <typename T, int KIND, int DIM>
@@ -330,9 +360,15 @@ __global__ void __launch_bounds__(TPB) k_prolong(Lvl<T> F, Lvl<T> C) {
 // tile in with cp.async (global -> shared, no register staging) while it
 // computes the current one.
 constexpr int RB_H = 2;
-// Threads of a tile block (measured: 256 beats sizing the block to the red
-// pass, which leaves fewer blocks per SM).
-__host__ __device__ constexpr int rb_threads(int tx, int ty) { return tx * ty >= 1024 ? 512 : 256; }
+// Threads of a tile block: enough whole warps for the red pass over the tile
+// and its first halo ring ((tx + 2)/2 x (ty + 2) points) in one round.
+__host__ __device__ constexpr int rb_threads(int tx, int ty) { return ((tx + 2) / 2 * (ty + 2) + 31) / 32 * 32; }
+// Minimum resident blocks per SM the float32 tile kernels are compiled for
+// (caps their registers so that four blocks fit; measured best on GB300).
+template <typename T>
+__host__ __device__ constexpr int rb_minb(int tx, int ty) {
+  return sizeof(T) == 4 ? (2048 / rb_threads(tx, ty) < 4 ? 2048 / rb_threads(tx, ty) : 4) : 1;
+}
 
 // The dynamic shared memory of the tile kernels (every extern __shared__
 // array of a kernel starts at the same address).
@@ -468,8 +504,9 @@ __device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, 
   constexpr int NU = Layout<KIND, 2>::NU;
   constexpr int SN = Gm::SN, SW = Gm::SW;
   const TileAcc<T, KIND, SN, SF> acc{base, G.h, &G};
+  const PtK<T> K = make_ptk<T, 2>(P, G.h);
   const int nx = G.g.nx, ny = G.g.ny;
-#pragma unroll 1
+#pragma unroll
   for (int pass = 0; pass < 2; ++pass) {
     const int color = pass;              // red (i + j even) first, then black
     const int ring = pass == 0 ? 1 : 0;  // red also on the first halo ring
@@ -489,7 +526,7 @@ __device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, 
       n.p[1] = n.c + SW;
       n.m[2] = n.p[2] = n.c;
       const int fc = SF ? n.c : wrapi(gy, ny) * nx + wrapi(x0 - ring + rx, nx);
-      smooth_point_a<T, KIND, 2>(acc, P, n, fc);
+      smooth_point_a<T, KIND, 2>(acc, P, K, n, fc);
     }
     __syncthreads();
   }
@@ -515,7 +552,7 @@ __device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, 
 // written, so the result is exactly one red-black sweep for any block
 // schedule.
 template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
-__global__ void __launch_bounds__(rb_threads(TX, TY)) k_smooth_rb2d(Lvl<T> G, Phys<T> P, int ntx, int ntiles,
+__global__ void __launch_bounds__(rb_threads(TX, TY), rb_minb<T>(TX, TY)) k_smooth_rb2d(Lvl<T> G, Phys<T> P, int ntx, int ntiles,
                                                                     int dir) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* buf0 = reinterpret_cast<T*>(smraw);
@@ -547,13 +584,201 @@ __global__ void __launch_bounds__(rb_threads(TX, TY)) k_smooth_rb2d(Lvl<T> G, Ph
   }
 }
 
-// Variants of the 2-D fused sweep (tile shape, staging of f/omega,
-// pipelining), chosen per level by the autotuner.
-struct RBVariant {
-  int tx, ty;
-  bool sf, pipe;
+// --------------------------------------------------------------------------
+// 2-D fused red-black sweep, row-marching form
+// --------------------------------------------------------------------------
+// A block owns the columns [x0, x0 + TX) of rows [y0, y1) of one level and
+// marches down them two rows per step.  Step s (ya = y0 - 2 + 2 s) updates
+// the red points of rows ya + 1 and ya + 2, then the black points of rows ya
+// and ya + 1, after which rows ya and ya + 1 are final and are written out.
+// Each thread owns one column (its red and its black point of every step),
+// so a step needs one barrier, between its red and its black half.
+//
+// The arrays the point update reads at neighbours -- e, rho^k, the
+// coefficient velocity and, for CDFT, the coefficient density -- are staged
+// by cp.async into a ring of MR row slots, two steps ahead of their use.  The
+// right-hand side, omega^k and (PFC) the coefficient density are read only
+// at the point itself: they go to registers, one step ahead.  The red points
+// of the columns x0 - 1 and x0 + TX (two lanes of an extra warp) and of the
+// rows y0 - 1 and y1 are computed again by the blocks that own them; as in
+// the tile form, e is read from one buffer and written to the other, so all
+// staged values are from before the sweep and the result is exactly one
+// red-black sweep.
+constexpr int MR = 10;  // row slots: rows ya - 1 .. ya + 7 are live in step s
+
+template <int KIND>
+__host__ __device__ constexpr int march_arrays() {
+  return Layout<KIND, 2>::NU + 3 + (KIND == KCDFT ? 1 : 0);  // e, rk, cv0, cv1 (, cr)
+}
+template <typename T, int KIND, int TX>
+__host__ __device__ constexpr size_t march_smem_bytes() {
+  return (size_t)MR * march_arrays<KIND>() * (TX + 2 * RB_XO) * sizeof(T);
+}
+__host__ __device__ constexpr int march_threads(int tx) { return tx + 32; }
+
+// Values of one point read only at that point.
+template <typename T, int KIND>
+struct MarchPt {
+  T fv[Layout<KIND, 2>::NU];
+  T omv, crv;
 };
-constexpr int RB_NVAR = 12;   // bits 0-1: PIPE, SF; v >> 2: tile 32x16, 64x8, 32x32
+
+template <typename T, int KIND>
+__device__ __forceinline__ void march_load_pt(const Lvl<T>& G, int gidx, MarchPt<T, KIND>& p) {
+#pragma unroll
+  for (int q = 0; q < Layout<KIND, 2>::NU; ++q) p.fv[q] = G.f[q][gidx];
+  p.omv = G.om[0][gidx];
+  p.crv = KIND == KPFC ? G.cr[gidx] : T(0);
+}
+
+// Accessor of the point update over the row ring (index = slot * NA * SW +
+// staged column, array a at offset a * SW) and one point's register values.
+template <typename T, int KIND, int SW>
+struct MarchAcc {
+  static constexpr int NU = Layout<KIND, 2>::NU;
+  T* sm;
+  const MarchPt<T, KIND>& p;
+  __device__ __forceinline__ T e(int q, int i) const { return sm[i + q * SW]; }
+  __device__ __forceinline__ void set_e(int q, int i, T v) const { sm[i + q * SW] = v; }
+  __device__ __forceinline__ T rk(int i) const { return sm[i + NU * SW]; }
+  __device__ __forceinline__ T cv(int d, int i) const { return sm[i + (NU + 1 + d) * SW]; }
+  __device__ __forceinline__ T cr(int i) const {
+    if constexpr (KIND == KCDFT) return sm[i + (NU + 3) * SW];
+    else return p.crv;  // the PFC update reads the coefficient density at the point only
+  }
+  __device__ __forceinline__ T f(int q, int) const { return p.fv[q]; }
+  __device__ __forceinline__ T om(int, int) const { return p.omv; }
+};
+
+// Start the copies of rows row0 and row0 + 1 (local rows lrow0, lrow0 + 1,
+// counted from y0 - 2) into their ring slots.
+template <typename T, int KIND, int TX>
+__device__ __forceinline__ void march_issue2(const Lvl<T>& G, T* buf, int x0, int row0, int lrow0, int dir) {
+  constexpr int NU = Layout<KIND, 2>::NU;
+  constexpr int NA = march_arrays<KIND>();
+  constexpr int SW = TX + 2 * RB_XO;
+  constexpr int V = 16 / sizeof(T);
+  const int nx = G.g.nx, ny = G.g.ny;
+  const T* src[NA];
+#pragma unroll
+  for (int q = 0; q < NU; ++q) src[q] = dir ? G.r[q] : G.e[q];
+  src[NU] = G.rk;
+  src[NU + 1] = G.cv[0];
+  src[NU + 2] = G.cv[1];
+  if constexpr (KIND == KCDFT) src[NU + 3] = G.cr;
+  if (nx % V == 0) {
+    constexpr int CPR = SW / V;
+    for (int t = threadIdx.x; t < 2 * CPR; t += blockDim.x) {
+      const int k = t >= CPR, c = t - k * CPR;
+      const int gi = wrapi(row0 + k, ny) * nx + wrapi(x0 - RB_XO + c * V, nx);
+      T* d = buf + ((lrow0 + k) % MR) * NA * SW + c * V;
+#pragma unroll
+      for (int a = 0; a < NA; ++a) cp_async_16(d + a * SW, src[a] + gi);
+    }
+  } else {
+    for (int t = threadIdx.x; t < 2 * SW; t += blockDim.x) {
+      const int k = t >= SW, c = t - k * SW;
+      const int gi = wrapi(row0 + k, ny) * nx + wrapi(x0 - RB_XO + c, nx);
+      T* d = buf + ((lrow0 + k) % MR) * NA * SW + c;
+#pragma unroll
+      for (int a = 0; a < NA; ++a) cp_async_elem(d + a * SW, src[a] + gi);
+    }
+  }
+}
+
+// One fused sweep of the block's strip (see above); buf is the ring in
+// dynamic shared memory.
+template <typename T, int KIND, int TX>
+__device__ __forceinline__ void march_sweep(const Lvl<T>& G, const Phys<T>& P, T* buf, int x0, int y0, int y1,
+                                            int dir) {
+  constexpr int NU = Layout<KIND, 2>::NU;
+  constexpr int NA = march_arrays<KIND>();
+  constexpr int SW = TX + 2 * RB_XO;
+  constexpr int RS = NA * SW;  // stride of a row slot
+  const int nx = G.g.nx, ny = G.g.ny;
+  const int txe = min(TX, nx - x0);
+  const PtK<T> K = make_ptk<T, 2>(P, G.h);
+  // this thread's staged column: interior x0 + tid, or (lanes 0, 1 of the
+  // last warp) the red-only columns x0 - 1 and x0 + txe
+  const int tid = threadIdx.x;
+  const bool interior = tid < txe;
+  int lx = -1;
+  if (interior) lx = RB_XO + tid;
+  else if (tid == TX) lx = RB_XO - 1;
+  else if (tid == TX + 1) lx = RB_XO + txe;
+  const int gx = x0 - RB_XO + lx;  // unwrapped column: its parity is the colour's
+  const int gxw = wrapi(gx, nx);
+  T* const* dst = dir ? G.e : G.r;
+  const int nsteps = (y1 - y0) / 2 + 1;
+  auto slot = [&](int row) { return ((row - y0 + 2) % MR) * RS; };
+  auto red_row = [&](int ya) { return ((gx + ya + 1) & 1) == 0 ? ya + 1 : ya + 2; };
+  auto black_row = [&](int ya) { return ((gx + ya) & 1) ? ya : ya + 1; };
+  auto update = [&](int row, const MarchPt<T, KIND>& pt) {
+    const MarchAcc<T, KIND, SW> acc{buf, pt};
+    Nb n;
+    n.c = slot(row) + lx;
+    n.m[0] = n.c - 1;
+    n.p[0] = n.c + 1;
+    n.m[1] = slot(row - 1) + lx;
+    n.p[1] = slot(row + 1) + lx;
+    n.m[2] = n.p[2] = n.c;
+    smooth_point_a<T, KIND, 2>(acc, P, K, n, 0);
+  };
+
+  // rows y0 - 2 .. y0 + 3 (steps 0 and 1)
+  for (int k = 0; k < 3; ++k) march_issue2<T, KIND, TX>(G, buf, x0, y0 - 2 + 2 * k, 2 * k, dir);
+  cp_async_commit();
+  MarchPt<T, KIND> pr, pb, nr, nbk;
+  if (lx >= 0) march_load_pt<T, KIND>(G, wrapi(red_row(y0 - 2), ny) * nx + gxw, pr);
+  cp_async_wait_all();
+  __syncthreads();
+#pragma unroll 1
+  for (int s = 0; s < nsteps; ++s) {
+    const int ya = y0 - 2 + 2 * s;
+    if (lx >= 0) update(red_row(ya), pr);
+    cp_async_wait_all();
+    __syncthreads();
+    if (s + 2 < nsteps) march_issue2<T, KIND, TX>(G, buf, x0, ya + 6, 2 * s + 6, dir);  // rows of step s + 2
+    cp_async_commit();
+    const int rb = black_row(ya);
+    const bool do_black = interior && rb >= y0 && rb < y1;
+    // next step's point values
+    if (lx >= 0 && s + 1 < nsteps) march_load_pt<T, KIND>(G, wrapi(red_row(ya + 2), ny) * nx + gxw, nr);
+    const int rbn = black_row(ya + 2);
+    if (interior && s + 1 < nsteps && rbn >= y0 && rbn < y1) march_load_pt<T, KIND>(G, rbn * nx + gxw, nbk);
+    if (do_black) update(rb, pb);
+    if (interior) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int row = ya + k;
+        if (row >= y0 && row < y1) {
+          const int si = slot(row) + lx;
+#pragma unroll
+          for (int q = 0; q < NU; ++q) dst[q][row * nx + gxw] = buf[si + q * SW];
+        }
+      }
+    }
+    pr = nr;
+    pb = nbk;
+  }
+}
+
+template <typename T, int KIND, int TX>
+__global__ void __launch_bounds__(march_threads(TX)) k_smooth_march(Lvl<T> G, Phys<T> P, int nstrips, int ly,
+                                                                    int dir) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int strip = blockIdx.x % nstrips, seg = blockIdx.x / nstrips;
+  const int y0 = seg * ly;
+  march_sweep<T, KIND, TX>(G, P, reinterpret_cast<T*>(smraw), strip * TX, y0, min(y0 + ly, G.g.ny), dir);
+}
+
+// Variants of the 2-D fused sweep, chosen per level by the autotuner:
+// 0..11 tile form (bits 0-1: PIPE, SF; v >> 2: tile 32x16, 64x8, 32x32),
+// 12..17 marching form (strip width 64 or 128; rows per block 16, 32, 64).
+constexpr int RB_NVAR = FM_SWEEP_VARIANTS;
+constexpr int RB_NTILE = 12;
+__host__ __device__ constexpr int march_tx(int v) { return v < 15 ? 64 : 128; }
+__host__ __device__ constexpr int march_ly(int v) { return 16 << ((v - RB_NTILE) % 3); }
 
 // The whole V-cycle of the small levels (each at most SMALL_N points) in one
 // thread block: phases separated by __syncthreads, data in L1/L2.
@@ -572,13 +797,14 @@ struct SmallLv {
 template <typename T, int KIND, int DIM>
 __device__ __forceinline__ void block_smooth(const Lvl<T>& L, const Phys<T>& P, int iters) {
   const int half = L.g.N / 2;
+  const PtK<T> K = make_ptk<T, DIM>(P, L.h);
   for (int it = 0; it < iters; ++it)
     for (int color = 0; color < 2; ++color) {
       for (int t = threadIdx.x; t < half; t += blockDim.x) {
         int i, j, k;
         colour_point(t, color, L.g, i, j, k);
         const Nb n = neighbours(i, j, k, L.g);
-        smooth_point<T, KIND, DIM>(L, P, n);
+        smooth_point<T, KIND, DIM>(L, P, K, n);
       }
       __syncthreads();
     }
@@ -650,13 +876,14 @@ __device__ __forceinline__ void group_smooth(const Lvl<T>& L, const Phys<T>& P, 
   const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
   const int nth = WARP ? 32 : blockDim.x;
   const int half = L.g.N / 2;
+  const PtK<T> K = make_ptk<T, DIM>(P, L.h);
   for (int it = 0; it < iters; ++it)
     for (int color = 0; color < 2; ++color) {
       for (int t = tid; t < half; t += nth) {
         int i, j, k;
         colour_point(t, color, L.g, i, j, k);
         const Nb n = neighbours(i, j, k, L.g);
-        smooth_point<T, KIND, DIM>(L, P, n);
+        smooth_point<T, KIND, DIM>(L, P, K, n);
       }
       group_sync<T, KIND, DIM, WARP>();
     }

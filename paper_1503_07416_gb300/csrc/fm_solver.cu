@@ -144,6 +144,24 @@ static int launch_rb_v(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStre
   return FM_OK;
 }
 
+// Launch the row-marching form (strip width TX, ly rows per block) on level L.
+template <typename T, int KIND, int TX>
+static int launch_march(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int dir, int ly) {
+  constexpr size_t smem = march_smem_bytes<T, KIND, TX>();
+  if (smem + 4096 > (size_t)st->smem_optin) return FM_EINVAL;
+  if (!L.r[0]) return FM_EINVAL;
+  static bool attr = false;
+  if (!attr) {
+    FM_CUDA(cudaFuncSetAttribute(k_smooth_march<T, KIND, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    attr = true;
+  }
+  const int nstrips = (L.g.nx + TX - 1) / TX;
+  const int nseg = (L.g.ny + ly - 1) / ly;
+  k_smooth_march<T, KIND, TX><<<nstrips * nseg, march_threads(TX), smem, s>>>(L, P, nstrips, ly, dir);
+  return FM_OK;
+}
+
 template <typename T, int KIND>
 static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int dir = 0) {
   switch (v) {
@@ -158,7 +176,13 @@ static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cud
     case 8: return launch_rb_v<T, KIND, 32, 32, false, false>(st, L, P, s, dir);
     case 9: return launch_rb_v<T, KIND, 32, 32, false, true>(st, L, P, s, dir);
     case 10: return launch_rb_v<T, KIND, 32, 32, true, false>(st, L, P, s, dir);
-    default: return launch_rb_v<T, KIND, 32, 32, true, true>(st, L, P, s, dir);
+    case 11: return launch_rb_v<T, KIND, 32, 32, true, true>(st, L, P, s, dir);
+    case 12: return launch_march<T, KIND, 64>(st, L, P, s, dir, 16);
+    case 13: return launch_march<T, KIND, 64>(st, L, P, s, dir, 32);
+    case 14: return launch_march<T, KIND, 64>(st, L, P, s, dir, 64);
+    case 15: return launch_march<T, KIND, 128>(st, L, P, s, dir, 16);
+    case 16: return launch_march<T, KIND, 128>(st, L, P, s, dir, 32);
+    default: return launch_march<T, KIND, 128>(st, L, P, s, dir, 64);
   }
 }
 

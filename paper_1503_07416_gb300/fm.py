@@ -224,6 +224,7 @@ def fm_residual(st, g, r=None):
     return nrm.value
 
 
+FM_SWEEP_VARIANTS = 18
 FM_SWEEP_AUTO = -1
 FM_SWEEP_TWO_COLOUR = -2
 
@@ -288,7 +289,7 @@ def fm_batch_launches(b):
 
 def fm_batch_tuning(b, level):
     v = C.c_int()
-    ms = (C.c_float * 12)()
+    ms = (C.c_float * FM_SWEEP_VARIANTS)()
     _check(lib().fm_batch_tuning(b, level, C.byref(v), ms), "fm_batch_tuning")
     return v.value, list(ms)
 
@@ -311,9 +312,9 @@ def fm_mass_noalloc(rho, h, out, stream=0):
 
 
 def fm_tuning(st, level):
-    """(chosen variant, [ms of the 12 variants]) of the fused sweep at `level`."""
+    """(chosen variant, [ms of every variant]) of the fused sweep at `level`."""
     v = C.c_int()
-    ms = (C.c_float * 12)()
+    ms = (C.c_float * FM_SWEEP_VARIANTS)()
     _check(lib().fm_tuning(st, level, C.byref(v), ms), "fm_tuning")
     return v.value, list(ms)
 

@@ -109,7 +109,7 @@ def test_cdft_every_fused_variant_matches_oracle_over_many_waves(precision):
     once for every variant."""
     rho, vel, prm = _case("cdft", (512, 1024), 5)
     f, de = _oracle(rho, vel, prm, 0.0, 2)
-    for v in range(12):
+    for v in range(fm.FM_SWEEP_VARIANTS):
         try:
             e = _gpu(rho, vel, prm, f, precision, 0.0, 2, v)
         except fm.FMError as err:  # variant too large for shared memory
@@ -127,7 +127,7 @@ def test_pfc_every_fused_variant_matches_two_colour_launches(precision):
     f, _ = _oracle(rho, vel, prm, 0.0, 0)
     ref = _gpu(rho, vel, prm, f, precision, 0.0, 4, fm.FM_SWEEP_TWO_COLOUR)
     tol = 1e-12 if precision == fm.FM_FP64 else 2e-5
-    for v in range(12):
+    for v in range(fm.FM_SWEEP_VARIANTS):
         try:
             e = _gpu(rho, vel, prm, f, precision, 0.0, 4, v)
         except fm.FMError as err:
@@ -144,7 +144,7 @@ def test_smooth_row_rejects_bad_arguments():
     with pytest.raises(fm.FMError):  # before fm_prepare
         fm.fm_smooth(sol.handle, e, e, 1)
     fm.fm_prepare(sol.handle, prm["dt"])
-    for variant in (-3, 12):
+    for variant in (-3, fm.FM_SWEEP_VARIANTS):
         with pytest.raises(fm.FMError):
             fm.fm_smooth(sol.handle, e, e, 1, variant)
     with pytest.raises(fm.FMError):
