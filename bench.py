@@ -129,17 +129,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def sweep_kernel(variant, batched):
+    """Name of the fused-sweep kernel that variant `variant` launches."""
+    pre = "kb_" if batched else "k_"
+    if variant >= 12:
+        tx = 64 if variant < 15 else 128
+        ly = 16 << ((variant - 12) % 3)
+        return f"{pre}smooth_march<float,PFC,{tx}> ({ly} rows per block)"
+    tile = ["32x16", "64x8", "32x32"][variant >> 2]
+    return (f"{pre}smooth_rb2d<float,PFC,{tile}> (f staged: {bool(variant & 2)}, "
+            f"persistent: {bool(variant & 1)})")
+
+
 def profiled_traffic(key, variant):
-    """DRAM bytes per launch from the committed ncu summary of this kernel, or
-    None when the variant timed here is not the profiled one."""
+    """DRAM bytes per launch of fused-sweep variant `variant` from the
+    committed ncu capture (profiles/traffic.json), or None when that variant
+    has not been captured."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             ent = json.load(f).get(key)
     except (OSError, ValueError):
         return None
-    if not ent or ent.get("variant") != variant:
+    if not ent:
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent.get("per_variant", {}).get(str(variant))
 
 
 def load_peaks():
@@ -297,7 +310,7 @@ def run_ours(args):
     bytes_launch = words * 4 * N
     avg_ms = sm_ms / max(1, sm_n)
     achieved = bytes_launch / (avg_ms * 1e-3) / 1e9 if sm_n else None
-    traffic = profiled_traffic("k_smooth_rb2d_pfc512_level0", tuning["mixed"][0][0])
+    traffic = profiled_traffic("k_smooth_pfc512_level0", tuning["mixed"][0][0])
     f64_sm_ms, f64_sm_n = f64["prof"]
     f64_avg = f64_sm_ms / max(1, f64_sm_n)
     out = {
@@ -332,7 +345,7 @@ def run_ours(args):
                                    for l, v in enumerate(vals)] for k, vals in tuning.items()},
         },
         "roofline": {
-            "kernel": "k_smooth_rb2d<float,PFC> (finest level, one red-black sweep)",
+            "kernel": sweep_kernel(tuning["mixed"][0][0], False) + ", finest level, one red-black sweep",
             "bound": "hbm",
             "achieved": round(achieved, 1) if achieved else None,
             "peak": peak,
@@ -415,12 +428,12 @@ def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2):
         "ms_per_batch_step": round(total / steps, 3),
         "cycles_mean": round(sum(cyc) / len(cyc), 3), "cycles_max": max(cyc),
         "gpu_launches": launches,
-        "smoother_roofline": {"kernel": "kb_smooth_rb2d<float,PFC> (finest level of all instances)",
+        "smoother_roofline": {"kernel": sweep_kernel(tune0[0], True) + ", finest level of all instances",
                               "bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                               "frac": round(gbs / peak, 4), "launch_ms": round(ms_sm, 5),
                               "algorithmic_bytes_per_launch": words * 4 * pts,
                               "timing": "20 back-to-back launches after a warm-up, CUDA events",
-                              "traffic": profiled_traffic("kb_smooth_rb2d_batch48", tune0[0]),
+                              "traffic": profiled_traffic("kb_smooth_batch48", tune0[0]),
                               "autotuned_variant": tune0[0],
                               "variant_ms": [round(x, 4) for x in tune0[1]]},
     }

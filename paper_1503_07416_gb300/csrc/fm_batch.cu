@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(rb_threads(TX, TY), rb_minb<T>(TX, TY)) kb_smo
 // Fused sweep in the row-marching form over the strips of level `level` of
 // all instances (work item aux = strips per row of blocks).
 template <typename T, int KIND, int TX>
-__global__ void __launch_bounds__(march_threads(TX)) kb_smooth_march(const WorkItem* items, int nitems,
+__global__ void __launch_bounds__(march_threads(TX), march_minb<T>(TX)) kb_smooth_march(const WorkItem* items, int nitems,
                                                                      const InstDev<T>* D, const Phys<T>* P,
                                                                      const Ctl* ctl, int level, int ly, int dir) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -585,7 +585,8 @@ struct Batch {
   }
 
   // Per level, time every variant of the fused sweep over all instances
-  // (one warm-up and three timed launches, CUDA events) and keep the fastest.
+  // (one warm-up and TUNE_REPS timed launches, CUDA events) and keep the
+  // fastest; a later variant replaces the choice only if it is 2% faster.
   static int autotune(fm_batch* b) {
     for (int l = 0; l < MAXLEV; ++l) b->rbv[l] = 0;
     const char* fixed = getenv("FM_RB_VARIANT");
@@ -610,7 +611,7 @@ struct Batch {
         }
         if (rc) break;
         if (cudaEventRecord(e0, b->stream) != cudaSuccess) { rc = FM_ECUDA; break; }
-        for (int k = 0; k < 3 && rc == FM_OK; ++k) rc = launch_variant(b, v, l);
+        for (int k = 0; k < TUNE_REPS && rc == FM_OK; ++k) rc = launch_variant(b, v, l);
         if (rc) break;
         float ms = 0.f;
         if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -618,8 +619,8 @@ struct Batch {
           rc = FM_ECUDA;
           break;
         }
-        b->rbt[l][v] = ms / 3.f;
-        if (ms < best) {
+        b->rbt[l][v] = ms / TUNE_REPS;
+        if (ms < best * 0.98f) {  // a later variant must be clearly faster
           best = ms;
           b->rbv[l] = v;
         }

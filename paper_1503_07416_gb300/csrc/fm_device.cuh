@@ -615,6 +615,10 @@ __host__ __device__ constexpr size_t march_smem_bytes() {
   return (size_t)MR * march_arrays<KIND>() * (TX + 2 * RB_XO) * sizeof(T);
 }
 __host__ __device__ constexpr int march_threads(int tx) { return tx + 32; }
+// Minimum resident blocks the float32 128-wide marching kernel is compiled
+// for (registers capped so that five blocks fit; measured best on GB300).
+template <typename T>
+__host__ __device__ constexpr int march_minb(int tx) { return (sizeof(T) == 4 && tx == 128) ? 5 : 1; }
 
 // Values of one point read only at that point.
 template <typename T, int KIND>
@@ -764,7 +768,7 @@ __device__ __forceinline__ void march_sweep(const Lvl<T>& G, const Phys<T>& P, T
 }
 
 template <typename T, int KIND, int TX>
-__global__ void __launch_bounds__(march_threads(TX)) k_smooth_march(Lvl<T> G, Phys<T> P, int nstrips, int ly,
+__global__ void __launch_bounds__(march_threads(TX), march_minb<T>(TX)) k_smooth_march(Lvl<T> G, Phys<T> P, int nstrips, int ly,
                                                                     int dir) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int strip = blockIdx.x % nstrips, seg = blockIdx.x / nstrips;
@@ -776,6 +780,7 @@ __global__ void __launch_bounds__(march_threads(TX)) k_smooth_march(Lvl<T> G, Ph
 // 0..11 tile form (bits 0-1: PIPE, SF; v >> 2: tile 32x16, 64x8, 32x32),
 // 12..17 marching form (strip width 64 or 128; rows per block 16, 32, 64).
 constexpr int RB_NVAR = FM_SWEEP_VARIANTS;
+constexpr int TUNE_REPS = 10;  // timed launches per variant and level in the autotuners
 constexpr int RB_NTILE = 12;
 __host__ __device__ constexpr int march_tx(int v) { return v < 15 ? 64 : 128; }
 __host__ __device__ constexpr int march_ly(int v) { return 16 << ((v - RB_NTILE) % 3); }

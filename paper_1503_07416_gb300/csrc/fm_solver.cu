@@ -250,8 +250,9 @@ struct Solver {
   }
 
   // Choose, per multi-kernel level, the fastest variant of the fused 2-D
-  // sweep: each variant is timed with CUDA events (one warm-up and three timed
-  // launches) on the level itself.  The sweeps only touch solver scratch.
+  // sweep: each variant is timed with CUDA events (one warm-up and TUNE_REPS
+  // timed launches) on the level itself; a later variant replaces the choice
+  // only if it is 2% faster.  The sweeps only touch solver scratch.
   static int autotune(fm_state* st) {
     if constexpr (DIM != 2) {
       return FM_OK;
@@ -280,7 +281,7 @@ struct Solver {
           }
           if (rc) break;
           if (cudaEventRecord(e0, st->stream) != cudaSuccess) { rc = FM_ECUDA; break; }
-          for (int k = 0; k < 3 && rc == FM_OK; ++k) rc = launch_rb<T, KIND>(st, v, L, P, st->stream);
+          for (int k = 0; k < TUNE_REPS && rc == FM_OK; ++k) rc = launch_rb<T, KIND>(st, v, L, P, st->stream);
           if (rc) break;
           if (cudaEventRecord(e1, st->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
             rc = FM_ECUDA;
@@ -288,8 +289,8 @@ struct Solver {
           }
           float ms = 0.f;
           if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = FM_ECUDA; break; }
-          st->rbt[l][v] = ms / 3.f;
-          if (ms < best) {
+          st->rbt[l][v] = ms / TUNE_REPS;
+          if (ms < best * 0.98f) {  // a later variant must be clearly faster
             best = ms;
             st->rbv[l] = v;
           }
