@@ -231,25 +231,26 @@ __global__ void __launch_bounds__(TPB) kb_inject(const WorkItem* items, int nite
 
 template <typename T, int KIND>
 __global__ void __launch_bounds__(TPB) kb_prepare(const WorkItem* items, int nitems, const InstDev<T>* D,
-                                                  const Phys<double>* P64) {
+                                                  const Phys<double>* P64, const Step64* K64) {
   FM_BATCH_HEAD();
-  prepare_point<KIND, 2>(D[inst].F, D[inst].g0, D[inst].ih0, P64[inst], lb * TPB + threadIdx.x);
+  prepare_point<KIND, 2>(D[inst].F, D[inst].g0, K64[inst], P64[inst], lb * TPB + threadIdx.x);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(TPB) kb_prepare_mu(const WorkItem* items, int nitems, const InstDev<T>* D,
-                                                     const Phys<double>* P64) {
+                                                     const Phys<double>* P64, const Step64* K64) {
   FM_BATCH_HEAD();
-  prepare_mu_point<2>(D[inst].F, D[inst].g0, D[inst].ih0, P64[inst], lb * TPB + threadIdx.x);
+  prepare_mu_point<2>(D[inst].F, D[inst].g0, K64[inst], P64[inst], lb * TPB + threadIdx.x);
 }
 
 template <typename T, int KIND>
 __global__ void __launch_bounds__(TPB) kb_resid64(const WorkItem* items, int nitems, const InstDev<T>* D,
-                                                  const Phys<double>* P64, const Ctl* ctl, int check_active) {
+                                                  const Phys<double>* P64, const Step64* K64, const Ctl* ctl,
+                                                  int check_active) {
   FM_BATCH_HEAD();
   if (check_active && !inst_active(ctl, inst)) return;
   const InstDev<T>& I = D[inst];
-  resid64_tile_body<KIND, T>(I.F, I.O, I.g0, I.h0, P64[inst], I.partials, lb, I.nblk64);
+  resid64_tile_body<KIND, T>(I.F, I.O, I.g0, K64[inst], P64[inst], I.partials, lb, I.nblk64);
 }
 
 // one block per instance: norm, cycles, status, active flag
@@ -289,11 +290,11 @@ __global__ void __launch_bounds__(TPB) kb_update64(const WorkItem* items, int ni
 
 template <typename T>
 __global__ void __launch_bounds__(TPB) kb_closure(const WorkItem* items, int nitems, const InstDev<T>* D,
-                                                  const Phys<double>* P64, const Ctl* ctl) {
+                                                  const Phys<double>* P64, const Step64* K64, const Ctl* ctl) {
   FM_BATCH_HEAD();
   if (ctl[inst].status != FM_OK) return;
   const InstDev<T>& I = D[inst];
-  closure_point<2>(I.F, I.g0, I.ih0, P64[inst], I.tmp, lb * TPB + threadIdx.x);
+  closure_point<2>(I.F, I.g0, K64[inst], P64[inst], I.tmp, lb * TPB + threadIdx.x);
 }
 
 template <typename T>
@@ -322,11 +323,13 @@ struct fm_batch {
   void* D;                   // InstDev<T>[count]
   void* P;                   // Phys<T>[count]
   Phys<double>* P64;
+  Step64* K64;               // float64 step constants per instance
   Ctl* ctl;
   WorkItem* items;
   // host staging (pinned)
   void* hP;
   Phys<double>* hP64;
+  Step64* hK64;
   Ctl* hctl;
   // work lists
   std::vector<WorkItem> hitems;
@@ -663,7 +666,7 @@ struct Batch {
   static int resid_norm(fm_batch* b, int in_body, cudaGraphConditionalHandle hdl) {
     const InstDev<T>* D = (const InstDev<T>*)b->D;
     const WList& w = b->w_resid64;
-    kb_resid64<T, KIND><<<w.nblocks, TPB, 0, b->stream>>>(it(b, w), w.n, D, b->P64, b->ctl, in_body);
+    kb_resid64<T, KIND><<<w.nblocks, TPB, 0, b->stream>>>(it(b, w), w.n, D, b->P64, b->K64, b->ctl, in_body);
     FMB_LAUNCHED();
     kb_norm<T, LY::NU><<<b->count, TPB, 0, b->stream>>>(D, b->ctl, b->prm.tol, b->prm.max_cycles, in_body);
     FMB_LAUNCHED();
@@ -687,10 +690,10 @@ struct Batch {
       }
     }
     const WList& w = b->w_fine;
-    kb_prepare<T, KIND><<<w.nblocks, TPB, 0, s>>>(it(b, w), w.n, D, b->P64);
+    kb_prepare<T, KIND><<<w.nblocks, TPB, 0, s>>>(it(b, w), w.n, D, b->P64, b->K64);
     FMB_LAUNCHED();
     if (KIND == KPFC) {
-      kb_prepare_mu<T><<<w.nblocks, TPB, 0, s>>>(it(b, w), w.n, D, b->P64);
+      kb_prepare_mu<T><<<w.nblocks, TPB, 0, s>>>(it(b, w), w.n, D, b->P64, b->K64);
       FMB_LAUNCHED();
     }
     const WList& wi = b->w_inject;
@@ -719,7 +722,7 @@ struct Batch {
   static int post(fm_batch* b) {
     const InstDev<T>* D = (const InstDev<T>*)b->D;
     const WList& w = b->w_fine;
-    kb_closure<T><<<w.nblocks, TPB, 0, b->stream>>>(it(b, w), w.n, D, b->P64, b->ctl);
+    kb_closure<T><<<w.nblocks, TPB, 0, b->stream>>>(it(b, w), w.n, D, b->P64, b->K64, b->ctl);
     FMB_LAUNCHED();
     kb_commit<T><<<w.nblocks, TPB, 0, b->stream>>>(it(b, w), w.n, D, b->ctl);
     FMB_LAUNCHED();
@@ -794,15 +797,17 @@ struct Batch {
     const size_t szD = sizeof(InstDev<T>) * b->count;
     const size_t szP = sizeof(Phys<T>) * b->count;
     const size_t szP64 = sizeof(Phys<double>) * b->count;
+    const size_t szK64 = sizeof(Step64) * b->count;
     const size_t szC = sizeof(Ctl) * b->count;
     const size_t szI = sizeof(WorkItem) * (b->hitems.size() + 1);
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t total = al(szD) + al(szP) + al(szP64) + al(szC) + al(szI);
+    const size_t total = al(szD) + al(szP) + al(szP64) + al(szK64) + al(szC) + al(szI);
     FMB_CUDA(cudaMalloc(&b->dev, total));
     char* p = (char*)b->dev;
     b->D = p; p += al(szD);
     b->P = p; p += al(szP);
     b->P64 = (Phys<double>*)p; p += al(szP64);
+    b->K64 = (Step64*)p; p += al(szK64);
     b->ctl = (Ctl*)p; p += al(szC);
     b->items = (WorkItem*)p;
     FMB_CUDA(cudaMemcpy(b->D, H.data(), szD, cudaMemcpyHostToDevice));
@@ -811,6 +816,7 @@ struct Batch {
     FMB_CUDA(cudaMemset(b->ctl, 0, szC));
     FMB_CUDA(cudaMallocHost(&b->hP, szP));
     FMB_CUDA(cudaMallocHost((void**)&b->hP64, szP64));
+    FMB_CUDA(cudaMallocHost((void**)&b->hK64, szK64));
     FMB_CUDA(cudaMallocHost((void**)&b->hctl, szC));
     if (b->small_smem > (size_t)SMALL_SMEM_MAX) return FM_EINVAL;
     FMB_CUDA(cudaFuncSetAttribute(kb_small<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -848,9 +854,11 @@ struct Batch {
       b->inst[i]->dt = dt[i];
       hp[i] = make_phys<T>(b->inst[i]);
       b->hP64[i] = make_phys<double>(b->inst[i]);
+      b->hK64[i] = make_step64(b->hP64[i], 1.0 / b->inst[i]->lv[0].h);
     }
     FMB_CUDA(cudaMemcpyAsync(b->P, hp, sizeof(Phys<T>) * b->count, cudaMemcpyHostToDevice, b->stream));
     FMB_CUDA(cudaMemcpyAsync(b->P64, b->hP64, sizeof(Phys<double>) * b->count, cudaMemcpyHostToDevice, b->stream));
+    FMB_CUDA(cudaMemcpyAsync(b->K64, b->hK64, sizeof(Step64) * b->count, cudaMemcpyHostToDevice, b->stream));
     if (!b->gexec) {
       const int rc = build_graph(b);
       if (rc) return rc;
@@ -887,6 +895,7 @@ void fm_destroy_batch(fm_batch* b) {
   if (b->dev) cudaFree(b->dev);
   if (b->hP) cudaFreeHost(b->hP);
   if (b->hP64) cudaFreeHost(b->hP64);
+  if (b->hK64) cudaFreeHost(b->hK64);
   if (b->hctl) cudaFreeHost(b->hctl);
   if (b->inst) {
     for (int i = 0; i < b->count; ++i) fm_destroy(b->inst[i]);

@@ -1046,6 +1046,30 @@ struct Vel3W {
   double* p[3];
 };
 
+// Step constants of the float64 kernels (grid spacing h, step s), formed once
+// per step on the host (per instance for a batch) instead of per thread.
+struct Step64 {
+  double ih;     // 1/h
+  double ih2;    // 1/h^2
+  double hih;    // 1/(2h): centred differences of the vorticity
+  double c_div;  // s/(4h): continuity flux difference, kinetic-energy gradient
+  double c_w;    // sigma s/2: vorticity term
+  double c_m;    // s/(2h): chemical-potential gradient (non-local source term)
+  double c_v;    // s gamma/(2h^2): viscous Laplacian
+};
+
+__host__ __device__ inline Step64 make_step64(const Phys<double>& P, double ih) {
+  Step64 K;
+  K.ih = ih;
+  K.ih2 = ih * ih;
+  K.hih = 0.5 * ih;
+  K.c_div = P.s * 0.25 * ih;
+  K.c_w = 0.5 * P.sigma * P.s;
+  K.c_m = 0.5 * P.s * ih;
+  K.c_v = 0.5 * P.s * P.gamma * K.ih2;
+  return K;
+}
+
 struct Fields64 {
   const double* rho;          // rho^k
   const double* vel[3];       // u^k
@@ -1059,32 +1083,32 @@ struct Fields64 {
 
 // omega^k, S and the initial iterate g^0 (kappa^0 = Lap_h rho^k for PFC).
 template <int KIND, int DIM>
-__device__ __forceinline__ void prepare_point(const Fields64& F, const Geo& G, double ih, const Phys<double>& P,
-                                              int idx) {
+__device__ __forceinline__ void prepare_point(const Fields64& F, const Geo& G, const Step64& K,
+                                              const Phys<double>& P, int idx) {
   using LY = Layout<KIND, DIM>;
   if (idx >= G.N) return;
   int i, j, k;
   coords(idx, G, i, j, k);
   const Nb n = neighbours(i, j, k, G);
-  const double ih2 = ih * ih;
+  const double ih2 = K.ih2;
   const double* u = F.vel[0];
   const double* v = F.vel[1];
   double w[3];
   if constexpr (DIM == 2) {
-    w[0] = 0.5 * ih * ((v[n.p[0]] - v[n.m[0]]) - (u[n.p[1]] - u[n.m[1]]));
+    w[0] = K.hih * ((v[n.p[0]] - v[n.m[0]]) - (u[n.p[1]] - u[n.m[1]]));
   } else {
     const double* ww = F.vel[2];
-    w[0] = 0.5 * ih * ((ww[n.p[1]] - ww[n.m[1]]) - (v[n.p[2]] - v[n.m[2]]));
-    w[1] = 0.5 * ih * ((u[n.p[2]] - u[n.m[2]]) - (ww[n.p[0]] - ww[n.m[0]]));
-    w[2] = 0.5 * ih * ((v[n.p[0]] - v[n.m[0]]) - (u[n.p[1]] - u[n.m[1]]));
+    w[0] = K.hih * ((ww[n.p[1]] - ww[n.m[1]]) - (v[n.p[2]] - v[n.m[2]]));
+    w[1] = K.hih * ((u[n.p[2]] - u[n.m[2]]) - (ww[n.p[0]] - ww[n.m[0]]));
+    w[2] = K.hih * ((v[n.p[0]] - v[n.m[0]]) - (u[n.p[1]] - u[n.m[1]]));
   }
   const double rkc = F.rho[n.c];
   double div = 0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d)
     div += F.rho[n.p[d]] * F.vel[d][n.p[d]] - F.rho[n.m[d]] * F.vel[d][n.m[d]];
-  const double c_w = 0.5 * P.sigma * P.s, c_v = 0.5 * P.s * P.gamma * ih2, c_e = P.s * 0.5 * ih;
-  F.S[0][idx] = rkc - (P.s * 0.25 * ih) * div;
+  const double c_w = K.c_w, c_v = K.c_v, c_e = K.c_m;
+  F.S[0][idx] = rkc - K.c_div * div;
   double uc[3], wx[3];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) uc[d] = F.vel[d][n.c];
@@ -1117,13 +1141,13 @@ __device__ __forceinline__ void prepare_point(const Fields64& F, const Geo& G, d
 }
 
 template <int KIND, int DIM>
-__global__ void __launch_bounds__(TPB) k_prepare(Fields64 F, Geo G, double ih, Phys<double> P) {
-  prepare_point<KIND, DIM>(F, G, ih, P, blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void __launch_bounds__(TPB) k_prepare(Fields64 F, Geo G, Step64 K, Phys<double> P) {
+  prepare_point<KIND, DIM>(F, G, K, P, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // PFC: mu^0 = psi^3/3 + alpha psi + Lap_h kappa^0 + S_mu (value of the mu row at rho^k).
 template <int DIM>
-__device__ __forceinline__ void prepare_mu_point(const Fields64& F, const Geo& G, double ih,
+__device__ __forceinline__ void prepare_mu_point(const Fields64& F, const Geo& G, const Step64& K,
                                                  const Phys<double>& P, int idx) {
   using LY = Layout<KPFC, DIM>;
   if (idx >= G.N) return;
@@ -1132,13 +1156,13 @@ __device__ __forceinline__ void prepare_mu_point(const Fields64& F, const Geo& G
   const Nb n = neighbours(i, j, k, G);
   const double psi = F.rho[idx] - 1.5;
   const double* ka = F.g[LY::IKA];
-  const double lapk = (nbsum<double, DIM>(ka, n) - 2.0 * DIM * ka[idx]) * (ih * ih);
+  const double lapk = (nbsum<double, DIM>(ka, n) - 2.0 * DIM * ka[idx]) * K.ih2;
   F.g[LY::IMU][idx] = psi * psi * psi * (1.0 / 3.0) + P.alpha * psi + lapk + F.S[LY::IMU][idx];
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(TPB) k_prepare_mu(Fields64 F, Geo G, double ih, Phys<double> P) {
-  prepare_mu_point<DIM>(F, G, ih, P, blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void __launch_bounds__(TPB) k_prepare_mu(Fields64 F, Geo G, Step64 K, Phys<double> P) {
+  prepare_mu_point<DIM>(F, G, K, P, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <int NQ>
@@ -1235,15 +1259,14 @@ struct Resid64Out {
 // Block `lb` of `nb` blocks: strided loop over the points, partial sums of
 // r^2 into partials[lb][q].
 template <int KIND, int DIM, typename T>
-__device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out& O, const Geo& G, double h,
+__device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out& O, const Geo& G, const Step64& K,
                                              const Phys<double>& P, double* partials, int lb, int nb) {
   using LY = Layout<KIND, DIM>;
   double acc[LY::NU];
 #pragma unroll
   for (int q = 0; q < LY::NU; ++q) acc[q] = 0.0;
-  const double ih = 1.0 / h, ih2 = ih * ih;
-  const double c_div = P.s * 0.25 * ih, c_w = 0.5 * P.sigma * P.s, c_q = 0.25 * P.s * ih;
-  const double c_m = 0.5 * P.s * ih, c_v = 0.5 * P.s * P.gamma * ih2, third = 1.0 / 3.0;
+  const double ih2 = K.ih2, c_div = K.c_div, c_w = K.c_w, c_q = K.c_div, c_m = K.c_m, c_v = K.c_v;
+  const double third = 1.0 / 3.0;
   for (int idx = lb * blockDim.x + threadIdx.x; idx < G.N; idx += nb * blockDim.x) {
     int i, j, k;
     coords(idx, G, i, j, k);
@@ -1319,20 +1342,15 @@ constexpr int R64_TX = 32, R64_TY = 8;
 constexpr int R64_SW = R64_TX + 2, R64_SN = R64_SW * (R64_TY + 2);
 
 template <int KIND, typename T>
-__device__ __forceinline__ void resid64_tile_body(const Fields64& F, const Resid64Out& O, const Geo& G, double h,
+__device__ __forceinline__ void resid64_tile_body(const Fields64& F, const Resid64Out& O, const Geo& G,
+                                                  const Step64& K,
                                                   const Phys<double>& P, double* partials, int lb, int nb) {
   using LY = Layout<KIND, 2>;
   __shared__ double sQ[R64_SN], sM[R64_SN], sRU[R64_SN], sRV[R64_SN];
   double acc[LY::NU];
 #pragma unroll
   for (int q = 0; q < LY::NU; ++q) acc[q] = 0.0;
-  const double ih = 1.0 / h, ih2 = ih * ih;
-  // step constants, formed once per thread
-  const double c_div = P.s * 0.25 * ih;          // continuity flux difference
-  const double c_w = 0.5 * P.sigma * P.s;        // vorticity term
-  const double c_q = 0.25 * P.s * ih;            // kinetic-energy gradient
-  const double c_m = 0.5 * P.s * ih;             // chemical-potential gradient
-  const double c_v = 0.5 * P.s * P.gamma * ih2;  // viscous Laplacian
+  const double ih2 = K.ih2, c_div = K.c_div, c_w = K.c_w, c_q = K.c_div, c_m = K.c_m, c_v = K.c_v;
   const double third = 1.0 / 3.0;
   const int nx = G.nx, ny = G.ny;
   const int ntx = (nx + R64_TX - 1) / R64_TX;
@@ -1407,9 +1425,9 @@ __device__ __forceinline__ void resid64_tile_body(const Fields64& F, const Resid
 }
 
 template <int KIND, typename T>
-__global__ void __launch_bounds__(TPB) k_resid64_tile(Fields64 F, Resid64Out O, Geo G, double h,
+__global__ void __launch_bounds__(TPB) k_resid64_tile(Fields64 F, Resid64Out O, Geo G, Step64 K,
                                                       Phys<double> P, double* partials) {
-  resid64_tile_body<KIND, T>(F, O, G, h, P, partials, blockIdx.x, gridDim.x);
+  resid64_tile_body<KIND, T>(F, O, G, K, P, partials, blockIdx.x, gridDim.x);
 }
 
 // Per-point quantities every point shares with its neighbours in the
@@ -1440,15 +1458,14 @@ __global__ void __launch_bounds__(TPB) k_shared64(Fields64 F, Shared64 X, int N,
 
 // Float64 residual reading the shared quantities of k_shared64.
 template <int KIND, int DIM, typename T>
-__global__ void __launch_bounds__(TPB) k_resid64_x(Fields64 F, Shared64 X, Resid64Out O, Geo G, double h,
+__global__ void __launch_bounds__(TPB) k_resid64_x(Fields64 F, Shared64 X, Resid64Out O, Geo G, Step64 K,
                                                    Phys<double> P, double* partials) {
   using LY = Layout<KIND, DIM>;
   double acc[LY::NU];
 #pragma unroll
   for (int q = 0; q < LY::NU; ++q) acc[q] = 0.0;
-  const double ih = 1.0 / h, ih2 = ih * ih;
-  const double c_div = P.s * 0.25 * ih, c_w = 0.5 * P.sigma * P.s, c_q = 0.25 * P.s * ih;
-  const double c_m = 0.5 * P.s * ih, c_v = 0.5 * P.s * P.gamma * ih2, third = 1.0 / 3.0;
+  const double ih2 = K.ih2, c_div = K.c_div, c_w = K.c_w, c_q = K.c_div, c_m = K.c_m, c_v = K.c_v;
+  const double third = 1.0 / 3.0;
   const double* const* g = F.g;
   const double* M = (KIND == KPFC) ? g[LY::IMU] : X.x[4];
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < G.N; idx += gridDim.x * blockDim.x) {
@@ -1499,9 +1516,9 @@ __global__ void __launch_bounds__(TPB) k_resid64_x(Fields64 F, Shared64 X, Resid
 }
 
 template <int KIND, int DIM, typename T>
-__global__ void __launch_bounds__(TPB) k_resid64(Fields64 F, Resid64Out O, Geo G, double h,
+__global__ void __launch_bounds__(TPB) k_resid64(Fields64 F, Resid64Out O, Geo G, Step64 K,
                                                  Phys<double> P, double* partials) {
-  resid64_body<KIND, DIM, T>(F, O, G, h, P, partials, blockIdx.x, gridDim.x);
+  resid64_body<KIND, DIM, T>(F, O, G, K, P, partials, blockIdx.x, gridDim.x);
 }
 
 // g += e (float64), then the projection of Sec. 6 on rho.
@@ -1586,7 +1603,7 @@ __global__ void k_norm_ctl(const double* partials, int nblk, double w, Ctl* ctl,
 // rho^{k+1} = S1 - (s/4h) sum_d ([rho^k u_d]_{+d} - [rho^k u_d]_{-d}), projected,
 // into `out`; skipped unless the solve succeeded.
 template <int DIM>
-__device__ __forceinline__ void closure_point(const Fields64& F, const Geo& G, double ih, const Phys<double>& P,
+__device__ __forceinline__ void closure_point(const Fields64& F, const Geo& G, const Step64& K, const Phys<double>& P,
                                               double* out, int idx) {
   if (idx >= G.N) return;
   int i, j, k;
@@ -1596,15 +1613,15 @@ __device__ __forceinline__ void closure_point(const Fields64& F, const Geo& G, d
 #pragma unroll
   for (int d = 0; d < DIM; ++d)
     div += F.rho[n.p[d]] * F.g[1 + d][n.p[d]] - F.rho[n.m[d]] * F.g[1 + d][n.m[d]];
-  const double r = F.S[0][idx] - (P.s * 0.25 * ih) * div;
+  const double r = F.S[0][idx] - K.c_div * div;
   out[idx] = (P.delta > 0.0) ? sqrt(r * r + P.delta * P.delta) : fabs(r);
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(TPB) k_closure(Fields64 F, Geo G, double ih, Phys<double> P, double* out,
+__global__ void __launch_bounds__(TPB) k_closure(Fields64 F, Geo G, Step64 K, Phys<double> P, double* out,
                                                  const Ctl* ctl) {
   if (ctl->status != FM_OK) return;
-  closure_point<DIM>(F, G, ih, P, out, blockIdx.x * blockDim.x + threadIdx.x);
+  closure_point<DIM>(F, G, K, P, out, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // New time level: rho <- closure result, u <- converged velocity (if the

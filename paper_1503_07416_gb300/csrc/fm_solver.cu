@@ -313,10 +313,11 @@ struct Solver {
       if (rc) return rc;
     }
     Fields64 F = make_fields(st);
-    k_prepare<KIND, DIM><<<nblocks(G.N), TPB, 0, s>>>(F, G, 1.0 / h, P);
+    const Step64 K = make_step64(P, 1.0 / h);
+    k_prepare<KIND, DIM><<<nblocks(G.N), TPB, 0, s>>>(F, G, K, P);
     FM_LAUNCHED();
     if (KIND == KPFC) {
-      k_prepare_mu<DIM><<<nblocks(G.N), TPB, 0, s>>>(F, G, 1.0 / h, P);
+      k_prepare_mu<DIM><<<nblocks(G.N), TPB, 0, s>>>(F, G, K, P);
       FM_LAUNCHED();
     }
     return inject_all(st, false);
@@ -351,14 +352,15 @@ struct Solver {
                             const Phys<double>& P) {
     cudaStream_t s = st->stream;
     if constexpr (DIM == 2) {
-      k_resid64_tile<KIND, T><<<st->nblk, TPB, 0, s>>>(F, O, G, h, P, st->partials);
+      k_resid64_tile<KIND, T><<<st->nblk, TPB, 0, s>>>(F, O, G, make_step64(P, 1.0 / h), P, st->partials);
       FM_LAUNCHED();
     } else {
       Shared64 X;
       for (int q = 0; q < 5; ++q) X.x[q] = st->x64[q];
       k_shared64<KIND, DIM><<<nblocks(G.N), TPB, 0, s>>>(F, X, G.N, P.ce);
       FM_LAUNCHED();
-      k_resid64_x<KIND, DIM, T><<<st->nblk, TPB, 0, s>>>(F, X, O, G, h, P, st->partials);
+      k_resid64_x<KIND, DIM, T><<<st->nblk, TPB, 0, s>>>(F, X, O, G, make_step64(P, 1.0 / h), P,
+                                                           st->partials);
       FM_LAUNCHED();
     }
     return FM_OK;
@@ -539,7 +541,8 @@ struct Solver {
     Fields64 F = make_fields(st);
     Phys<double> P64 = make_phys<double>(st);
     const Ctl* ctl = (const Ctl*)st->ctl;
-    k_closure<DIM><<<nblocks(G.N), TPB, 0, st->stream>>>(F, G, 1.0 / st->lv[0].h, P64, st->tmp, ctl);
+    k_closure<DIM><<<nblocks(G.N), TPB, 0, st->stream>>>(F, G, make_step64(P64, 1.0 / st->lv[0].h), P64, st->tmp,
+                                                         ctl);
     FM_LAUNCHED();
     Vel3W vw{{st->vel[0], st->vel[1], st->vel[2]}};
     Vel3 gv{{st->g[1], st->g[2], DIM == 3 ? st->g[3] : nullptr}};
