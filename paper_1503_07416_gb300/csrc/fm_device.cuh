@@ -281,9 +281,20 @@ __device__ __forceinline__ void prolong_point(const Lvl<T>& F, const Lvl<T>& C, 
 // M_C(eh) at the coarse point is evaluated on the fine arrays at the fine
 // indices 2I and 2I +- 2 with the coarse spacing.
 template <typename T, int KIND, int DIM>
+__device__ __forceinline__ void coarse_m_on_fine(const Lvl<T>& F, const Lvl<T>& C, const Phys<T>& P, int idx);
+
+template <typename T, int KIND, int DIM>
 __device__ __forceinline__ void restrict_rhs_point(const Lvl<T>& F, const Lvl<T>& C, const Phys<T>& P, int idx) {
   using LY = Layout<KIND, DIM>;
   restrict_point<T, LY::NU, DIM>(F, C, idx);
+  coarse_m_on_fine<T, KIND, DIM>(F, C, P, idx);
+}
+
+// f_C += M_C(eh_C) at coarse point idx, evaluated on the fine arrays (see
+// restrict_rhs_point).
+template <typename T, int KIND, int DIM>
+__device__ __forceinline__ void coarse_m_on_fine(const Lvl<T>& F, const Lvl<T>& C, const Phys<T>& P, int idx) {
+  using LY = Layout<KIND, DIM>;
   int I, J, K;
   coords(idx, C.g, I, J, K);
   const int fnx = F.g.nx, fny = F.g.ny, fnz = F.g.nz;
@@ -314,6 +325,52 @@ template <typename T, int KIND, int DIM>
 __global__ void __launch_bounds__(TPB) k_restrict_rhs(Lvl<T> F, Lvl<T> C, Phys<T> P) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < C.g.N) restrict_rhs_point<T, KIND, DIM>(F, C, P, idx);
+}
+
+// 2-D, one launch in place of k_resid + k_restrict_rhs: a block takes a
+// tile of RR_TX x RR_TY coarse points, computes the fine residual
+// r = f - M(e) on the (2 RR_TX + 1) x (2 RR_TY + 1) fine points their full
+// weighting reads into shared memory (r is not written to the level), then
+// f_C = FW(r) + M_C(eh_C) and e_C = eh_C = inject(e_F) on the tile.
+constexpr int RR_TX = 16, RR_TY = 8;
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(TPB) k_resid_restrict2(Lvl<T> F, Lvl<T> C, Phys<T> P, int ntx) {
+  constexpr int NU = Layout<KIND, 2>::NU;
+  constexpr int FW = 2 * RR_TX + 1, FN = FW * (2 * RR_TY + 1);
+  __shared__ T sr[NU * FN];
+  const int I0 = (blockIdx.x % ntx) * RR_TX, J0 = (blockIdx.x / ntx) * RR_TY;
+  for (int t = threadIdx.x; t < FN; t += blockDim.x) {
+    const int ly = t / FW, lx = t - ly * FW;
+    const int x = wrapi(2 * I0 - 1 + lx, F.g.nx), y = wrapi(2 * J0 - 1 + ly, F.g.ny);
+    const Nb n = neighbours(x, y, 0, F.g);
+    T M[NU];
+    applyM<T, KIND, 2>(F, P, n, F.e, M);
+#pragma unroll
+    for (int q = 0; q < NU; ++q) sr[q * FN + t] = F.f[q][n.c] - M[q];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < RR_TX * RR_TY; t += blockDim.x) {
+    const int ty = t / RR_TX, tx = t - ty * RR_TX;
+    const int I = I0 + tx, J = J0 + ty;
+    if (I >= C.g.nx || J >= C.g.ny) continue;
+    const int cidx = J * C.g.nx + I;
+    const int c = (2 * ty + 1) * FW + 2 * tx + 1;
+    const int ctr = 2 * J * F.g.nx + 2 * I;
+#pragma unroll
+    for (int q = 0; q < NU; ++q) {
+      const T* r = sr + q * FN;
+      T acc = T(0);
+      acc += r[c - FW - 1] + T(2) * r[c - FW] + r[c - FW + 1];
+      acc += T(2) * (r[c - 1] + T(2) * r[c] + r[c + 1]);
+      acc += r[c + FW - 1] + T(2) * r[c + FW] + r[c + FW + 1];
+      C.f[q][cidx] = acc * T(1.0 / 16.0);
+      const T ev = F.e[q][ctr];
+      C.e[q][cidx] = ev;
+      C.eh[q][cidx] = ev;
+    }
+    coarse_m_on_fine<T, KIND, 2>(F, C, P, cidx);
+  }
 }
 
 template <typename T, int KIND, int DIM>
@@ -424,15 +481,6 @@ __host__ __device__ constexpr size_t rb_smem_bytes() {
   return (PIPE ? 2 : 1) * (size_t)rb_arrays<KIND, SF>() * RBGeom<TX, TY>::SN * sizeof(T);
 }
 
-__device__ __forceinline__ int wrapi(int x, int n) {
-  if (x < 0) x += n;
-  else if (x >= n) x -= n;
-  if ((unsigned)x >= (unsigned)n) {
-    x %= n;
-    if (x < 0) x += n;
-  }
-  return x;
-}
 
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {

@@ -70,6 +70,17 @@ __device__ __forceinline__ Nb neighbours(int i, int j, int k, const Geo& g) {
   return n;
 }
 
+// x mod n for any int x (periodic index).
+__device__ __forceinline__ int wrapi(int x, int n) {
+  if (x < 0) x += n;
+  else if (x >= n) x -= n;
+  if ((unsigned)x >= (unsigned)n) {
+    x %= n;
+    if (x < 0) x += n;
+  }
+  return x;
+}
+
 __device__ __forceinline__ void coords(int idx, const Geo& g, int& i, int& j, int& k) {
   i = idx % g.nx;
   const int t = idx / g.nx;

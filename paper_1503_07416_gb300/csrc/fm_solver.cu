@@ -511,10 +511,16 @@ struct Solver {
     if (rc) return rc;
     Lvl<T> F = make_lvl<T>(st, l);
     Lvl<T> C = make_lvl<T>(st, l + 1);
-    k_resid<T, KIND, DIM><<<nblocks(F.g.N), TPB, 0, s>>>(F, P);
-    FM_LAUNCHED();
-    k_restrict_rhs<T, KIND, DIM><<<nblocks(C.g.N), TPB, 0, s>>>(F, C, P);
-    FM_LAUNCHED();
+    if constexpr (DIM == 2) {
+      const int ntx = (C.g.nx + RR_TX - 1) / RR_TX, nty = (C.g.ny + RR_TY - 1) / RR_TY;
+      k_resid_restrict2<T, KIND><<<ntx * nty, TPB, 0, s>>>(F, C, P, ntx);
+      FM_LAUNCHED();
+    } else {
+      k_resid<T, KIND, DIM><<<nblocks(F.g.N), TPB, 0, s>>>(F, P);
+      FM_LAUNCHED();
+      k_restrict_rhs<T, KIND, DIM><<<nblocks(C.g.N), TPB, 0, s>>>(F, C, P);
+      FM_LAUNCHED();
+    }
     rc = vcycle(st, l + 1, P);
     if (rc) return rc;
     k_prolong<T, LY::NU, DIM><<<nblocks(F.g.N), TPB, 0, s>>>(F, C);
