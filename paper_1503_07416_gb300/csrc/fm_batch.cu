@@ -173,29 +173,20 @@ __global__ void __launch_bounds__(TPB) kb_copy_back(const WorkItem* items, int n
   for (int q = 0; q < NU; ++q) L.e[q][idx] = L.r[q][idx];
 }
 
+// Fine residual and restriction of level `level` in one launch (see
+// k_resid_restrict2); work item aux = coarse tiles per row.
 template <typename T, int KIND>
-__global__ void __launch_bounds__(TPB) kb_resid(const WorkItem* items, int nitems, const InstDev<T>* D,
-                                                const Phys<T>* P, const Ctl* ctl, int level) {
-  FM_BATCH_HEAD();
-  if (!inst_active(ctl, inst)) return;
-  __shared__ Lvl<T> L;
-  smem_copy(&L, &D[inst].lv[level]);
-  __syncthreads();
-  const int idx = lb * TPB + threadIdx.x;
-  if (idx < L.g.N) resid_point<T, KIND, 2>(L, P[inst], idx);
-}
-
-template <typename T, int KIND>
-__global__ void __launch_bounds__(TPB) kb_restrict_rhs(const WorkItem* items, int nitems, const InstDev<T>* D,
-                                                       const Phys<T>* P, const Ctl* ctl, int level) {
+__global__ void __launch_bounds__(TPB) kb_resid_restrict2(const WorkItem* items, int nitems, const InstDev<T>* D,
+                                                          const Phys<T>* P, const Ctl* ctl, int level) {
   FM_BATCH_HEAD();
   if (!inst_active(ctl, inst)) return;
   __shared__ Lvl<T> F, Cc;
+  __shared__ T sr[Layout<KIND, 2>::NU * RR_FN];
   smem_copy(&F, &D[inst].lv[level]);
   smem_copy(&Cc, &D[inst].lv[level + 1]);
   __syncthreads();
-  const int idx = lb * TPB + threadIdx.x;
-  if (idx < Cc.g.N) restrict_rhs_point<T, KIND, 2>(F, Cc, P[inst], idx);
+  const int ntx = items[k_].aux;
+  resid_restrict2_tile<T, KIND>(F, Cc, P[inst], (lb % ntx) * RR_TX, (lb / ntx) * RR_TY, sr);
 }
 
 template <typename T, int NU>
@@ -335,7 +326,7 @@ struct fm_batch {
   std::vector<WorkItem> hitems;
   WList w_fine, w_resid64, w_inject;
   WList w_smooth[3 + 6][MAXLEV];  // per tile shape (32x16, 64x8, 32x32), then per marching variant
-  WList w_resid[MAXLEV], w_restrict[MAXLEV], w_crhs[MAXLEV], w_prolong[MAXLEV];
+  WList w_resid[MAXLEV], w_rr[MAXLEV], w_prolong[MAXLEV];
   int rbv[MAXLEV];           // chosen fused-sweep variant per level
   float rbt[MAXLEV][RB_NVAR];  // autotuner timings (ms per launch)
   // graph
@@ -476,8 +467,8 @@ struct Batch {
     }
     b->w_inject = add_list(b, v);
     for (int l = 0; l < b->maxdepth; ++l) {
-      std::vector<std::pair<int, int>> ts[9], rs, rr, cr, pr;
-      std::vector<int> aux[9];
+      std::vector<std::pair<int, int>> ts[9], rs, cr, pr;
+      std::vector<int> aux[9], craux;
       for (int i = 0; i < b->count; ++i) {
         fm_state* st = b->inst[i];
         if (st->small_from <= l) continue;
@@ -495,14 +486,14 @@ struct Batch {
           aux[3 + m].push_back(nstrips);
         }
         rs.push_back({i, nblocks(g.N)});
-        rr.push_back({i, nblocks(gc.N)});
-        cr.push_back({i, nblocks(gc.N)});
+        const int ctx = (gc.nx + RR_TX - 1) / RR_TX, cty = (gc.ny + RR_TY - 1) / RR_TY;
+        cr.push_back({i, ctx * cty});  // coarse tiles of the fused residual + restriction
+        craux.push_back(ctx);
         pr.push_back({i, nblocks(g.N)});
       }
       for (int sh = 0; sh < 9; ++sh) b->w_smooth[sh][l] = add_list(b, ts[sh], &aux[sh]);
       b->w_resid[l] = add_list(b, rs);
-      b->w_restrict[l] = add_list(b, rr);
-      b->w_crhs[l] = add_list(b, cr);
+      b->w_rr[l] = add_list(b, cr, &craux);
       b->w_prolong[l] = add_list(b, pr);
     }
   }
@@ -642,11 +633,9 @@ struct Batch {
     for (int l = 0; l < b->maxdepth; ++l) {
       int rc = smooth(b, l, b->prm.nu1);
       if (rc) return rc;
-      const WList &wr = b->w_resid[l], &wq = b->w_restrict[l];
-      if (wr.n == 0) continue;
-      kb_resid<T, KIND><<<wr.nblocks, TPB, 0, s>>>(it(b, wr), wr.n, D, P, b->ctl, l);
-      FMB_LAUNCHED();
-      kb_restrict_rhs<T, KIND><<<wq.nblocks, TPB, 0, s>>>(it(b, wq), wq.n, D, P, b->ctl, l);
+      const WList& wq = b->w_rr[l];
+      if (wq.n == 0) continue;
+      kb_resid_restrict2<T, KIND><<<wq.nblocks, TPB, 0, s>>>(it(b, wq), wq.n, D, P, b->ctl, l);
       FMB_LAUNCHED();
     }
     kb_small<T, KIND><<<b->count, SMALL_TPB, b->small_smem, s>>>(D, P, b->ctl, b->prm.nu1, b->prm.nu2,

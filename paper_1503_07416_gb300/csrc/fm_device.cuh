@@ -334,12 +334,14 @@ __global__ void __launch_bounds__(TPB) k_restrict_rhs(Lvl<T> F, Lvl<T> C, Phys<T
 // f_C = FW(r) + M_C(eh_C) and e_C = eh_C = inject(e_F) on the tile.
 constexpr int RR_TX = 16, RR_TY = 8;
 
+constexpr int RR_FN = (2 * RR_TX + 1) * (2 * RR_TY + 1);  // fine points per tile
+
+// Coarse tile (I0, J0); sr: shared memory for NU x RR_FN values.
 template <typename T, int KIND>
-__global__ void __launch_bounds__(TPB) k_resid_restrict2(Lvl<T> F, Lvl<T> C, Phys<T> P, int ntx) {
+__device__ __forceinline__ void resid_restrict2_tile(const Lvl<T>& F, const Lvl<T>& C, const Phys<T>& P, int I0,
+                                                     int J0, T* sr) {
   constexpr int NU = Layout<KIND, 2>::NU;
-  constexpr int FW = 2 * RR_TX + 1, FN = FW * (2 * RR_TY + 1);
-  __shared__ T sr[NU * FN];
-  const int I0 = (blockIdx.x % ntx) * RR_TX, J0 = (blockIdx.x / ntx) * RR_TY;
+  constexpr int FW = 2 * RR_TX + 1, FN = RR_FN;
   for (int t = threadIdx.x; t < FN; t += blockDim.x) {
     const int ly = t / FW, lx = t - ly * FW;
     const int x = wrapi(2 * I0 - 1 + lx, F.g.nx), y = wrapi(2 * J0 - 1 + ly, F.g.ny);
@@ -371,6 +373,12 @@ __global__ void __launch_bounds__(TPB) k_resid_restrict2(Lvl<T> F, Lvl<T> C, Phy
     }
     coarse_m_on_fine<T, KIND, 2>(F, C, P, cidx);
   }
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(TPB) k_resid_restrict2(Lvl<T> F, Lvl<T> C, Phys<T> P, int ntx) {
+  __shared__ T sr[Layout<KIND, 2>::NU * RR_FN];
+  resid_restrict2_tile<T, KIND>(F, C, P, (blockIdx.x % ntx) * RR_TX, (blockIdx.x / ntx) * RR_TY, sr);
 }
 
 template <typename T, int KIND, int DIM>
