@@ -184,10 +184,14 @@ __device__ __forceinline__ void resid_point(const Lvl<T>& L, const Phys<T>& P, i
   int i, j, k;
   coords(idx, L.g, i, j, k);
   const Nb n = neighbours(i, j, k, L.g);
-  T M[LY::NU];
+  T M[LY::NU], fv[LY::NU];
+  // all loads before the first store: the arrays may alias as far as the
+  // compiler knows, so interleaving would serialise them
+#pragma unroll
+  for (int q = 0; q < LY::NU; ++q) fv[q] = L.f[q][idx];
   applyM<T, KIND, DIM>(L, P, n, L.e, M);
 #pragma unroll
-  for (int q = 0; q < LY::NU; ++q) L.r[q][idx] = L.f[q][idx] - M[q];
+  for (int q = 0; q < LY::NU; ++q) L.r[q][idx] = fv[q] - M[q];
 }
 
 // coarse point idx: f_C = FW(r_F); e_C = eh_C = inject(e_F)
@@ -207,6 +211,7 @@ __device__ __forceinline__ void restrict_point(const Lvl<T>& F, const Lvl<T>& C,
   }
   constexpr int KZ = (DIM == 3) ? 3 : 1;
   const T norm = (DIM == 3) ? T(1.0 / 64.0) : T(1.0 / 16.0);
+  T fr[NU], ev[NU];  // all loads before the first store
 #pragma unroll
   for (int q = 0; q < NU; ++q) {
     T acc = 0;
@@ -221,10 +226,14 @@ __device__ __forceinline__ void restrict_point(const Lvl<T>& F, const Lvl<T>& C,
         acc += wy * (F.r[q][rowb + xs[0]] + T(2) * F.r[q][rowb + xs[1]] + F.r[q][rowb + xs[2]]);
       }
     }
-    C.f[q][idx] = acc * norm;
-    const T ev = F.e[q][ctr];
-    C.e[q][idx] = ev;
-    C.eh[q][idx] = ev;
+    fr[q] = acc * norm;
+    ev[q] = F.e[q][ctr];
+  }
+#pragma unroll
+  for (int q = 0; q < NU; ++q) {
+    C.f[q][idx] = fr[q];
+    C.e[q][idx] = ev[q];
+    C.eh[q][idx] = ev[q];
   }
 }
 
@@ -263,6 +272,7 @@ __device__ __forceinline__ void prolong_point(const Lvl<T>& F, const Lvl<T>& C, 
     zw = (k & 1) ? T(0.5) : T(1);
   }
   const T w = xw * yw * zw;
+  T ev[NU];  // all loads before the first store
 #pragma unroll
   for (int q = 0; q < NU; ++q) {
     T acc = 0;
@@ -272,8 +282,10 @@ __device__ __forceinline__ void prolong_point(const Lvl<T>& F, const Lvl<T>& C, 
           const int ci = (zi[c] * C.g.ny + yi[b]) * C.g.nx + xi[a];
           acc += C.e[q][ci] - C.eh[q][ci];
         }
-    F.e[q][idx] += w * acc;
+    ev[q] = F.e[q][idx] + w * acc;
   }
+#pragma unroll
+  for (int q = 0; q < NU; ++q) F.e[q][idx] = ev[q];
 }
 
 // Coarse point idx: f_C = FW(r_F) + M_C(eh_C), e_C = eh_C = inject(e_F), in
@@ -316,9 +328,12 @@ __device__ __forceinline__ void coarse_m_on_fine(const Lvl<T>& F, const Lvl<T>& 
   Lvl<T> V = F;
   V.h = C.h;
   T M[LY::NU];
+  T fv[LY::NU];
+#pragma unroll
+  for (int q = 0; q < LY::NU; ++q) fv[q] = C.f[q][idx];
   applyM<T, KIND, DIM>(V, P, n, F.e, M);
 #pragma unroll
-  for (int q = 0; q < LY::NU; ++q) C.f[q][idx] += M[q];
+  for (int q = 0; q < LY::NU; ++q) C.f[q][idx] = fv[q] + M[q];
 }
 
 template <typename T, int KIND, int DIM>
@@ -359,6 +374,9 @@ __device__ __forceinline__ void resid_restrict2_tile(const Lvl<T>& F, const Lvl<
     const int cidx = J * C.g.nx + I;
     const int c = (2 * ty + 1) * FW + 2 * tx + 1;
     const int ctr = 2 * J * F.g.nx + 2 * I;
+    T ev[NU];
+#pragma unroll
+    for (int q = 0; q < NU; ++q) ev[q] = F.e[q][ctr];
 #pragma unroll
     for (int q = 0; q < NU; ++q) {
       const T* r = sr + q * FN;
@@ -367,9 +385,8 @@ __device__ __forceinline__ void resid_restrict2_tile(const Lvl<T>& F, const Lvl<
       acc += T(2) * (r[c - 1] + T(2) * r[c] + r[c + 1]);
       acc += r[c + FW - 1] + T(2) * r[c + FW] + r[c + FW + 1];
       C.f[q][cidx] = acc * T(1.0 / 16.0);
-      const T ev = F.e[q][ctr];
-      C.e[q][cidx] = ev;
-      C.eh[q][cidx] = ev;
+      C.e[q][cidx] = ev[q];
+      C.eh[q][cidx] = ev[q];
     }
     coarse_m_on_fine<T, KIND, 2>(F, C, P, cidx);
   }
@@ -1164,8 +1181,8 @@ __device__ __forceinline__ void prepare_point(const Fields64& F, const Geo& G, c
   for (int d = 0; d < DIM; ++d)
     div += F.rho[n.p[d]] * F.vel[d][n.p[d]] - F.rho[n.m[d]] * F.vel[d][n.m[d]];
   const double c_w = K.c_w, c_v = K.c_v, c_e = K.c_m;
-  F.S[0][idx] = rkc - K.c_div * div;
-  double uc[3], wx[3];
+  const double s0 = rkc - K.c_div * div;
+  double uc[3], wx[3], sv[3];  // all loads before the first store
 #pragma unroll
   for (int d = 0; d < DIM; ++d) uc[d] = F.vel[d][n.c];
   cross<double, DIM>(w, uc, wx);
@@ -1177,12 +1194,17 @@ __device__ __forceinline__ void prepare_point(const Fields64& F, const Geo& G, c
       const double Em = 2.0 * P.ce * F.rho[n.m[a]] + F.conv[n.m[a]];
       sa += c_e * rkc * (Ep - Em);
     }
-    F.S[1 + a][idx] = sa;
+    sv[a] = sa;
+  }
+  const double lapr = (KIND == KPFC) ? (nbsum<double, DIM>(F.rho, n) - 2.0 * DIM * rkc) * ih2 : 0.0;
+  F.S[0][idx] = s0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    F.S[1 + a][idx] = sv[a];
     F.g[1 + a][idx] = uc[a];
   }
   F.g[0][idx] = rkc;
   if constexpr (KIND == KPFC) {
-    const double lapr = (nbsum<double, DIM>(F.rho, n) - 2.0 * DIM * rkc) * ih2;
     F.S[LY::IMU][idx] = 2.0 * lapr;
     F.S[LY::IKA][idx] = 0.0;
     F.g[LY::IKA][idx] = lapr;
@@ -1371,18 +1393,22 @@ __device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out
       N[LY::IMU] = g[LY::IMU][n.c] - psi * psi * psi * third - P.alpha * psi - lapk;
       N[LY::IKA] = kc - lapr;
     }
+    double rv[LY::NU];  // all loads (S, rho) before the first store
+#pragma unroll
+    for (int q = 0; q < LY::NU; ++q) rv[q] = F.S[q][idx] - N[q];
+    const double g0c = g[0][idx];
 #pragma unroll
     for (int q = 0; q < LY::NU; ++q) {
-      const double r = F.S[q][idx] - N[q];
+      const double r = rv[q];
       acc[q] += r * r;
       if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = (T)r;
       if (O.e0[q]) static_cast<T*>(O.e0[q])[idx] = T(0);
       if (O.r64[q]) O.r64[q][idx] = r;
     }
     if (O.cr32) {
-      O.cr32[idx] = (float)g[0][idx];
+      O.cr32[idx] = (float)g0c;
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) O.cv32[d][idx] = (float)g[1 + d][idx];
+      for (int d = 0; d < DIM; ++d) O.cv32[d][idx] = (float)uc[d];
     }
   }
   block_partials<LY::NU>(acc, partials, lb);
@@ -1460,16 +1486,20 @@ __device__ __forceinline__ void resid64_tile_body(const Fields64& F, const Resid
           N[LY::IMU] = g[LY::IMU][idx] - psi * psi * psi * third - P.alpha * psi - lapk;
           N[LY::IKA] = kc - lapr;
         }
+        double rv[LY::NU];  // all loads (S, rho) before the first store
+#pragma unroll
+        for (int q = 0; q < LY::NU; ++q) rv[q] = F.S[q][idx] - N[q];
+        const double g0c = g[0][idx];
 #pragma unroll
         for (int q = 0; q < LY::NU; ++q) {
-          const double r = F.S[q][idx] - N[q];
+          const double r = rv[q];
           acc[q] += r * r;
           if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = (T)r;
           if (O.e0[q]) static_cast<T*>(O.e0[q])[idx] = T(0);
           if (O.r64[q]) O.r64[q][idx] = r;
         }
         if (O.cr32) {
-          O.cr32[idx] = (float)g[0][idx];
+          O.cr32[idx] = (float)g0c;
           O.cv32[0][idx] = (float)uc;
           O.cv32[1][idx] = (float)vc;
         }
@@ -1498,18 +1528,18 @@ __global__ void __launch_bounds__(TPB) k_shared64(Fields64 F, Shared64 X, int N,
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N) return;
   const double rk = F.rho[idx];
+  double u[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) u[d] = F.g[1 + d][idx];
+  const double r = F.g[0][idx];
   double q = 0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
-    const double u = F.g[1 + d][idx];
-    q += u * u;
-    X.x[1 + d][idx] = rk * u;
+    q += u[d] * u[d];
+    X.x[1 + d][idx] = rk * u[d];
   }
   X.x[0][idx] = q;
-  if constexpr (KIND == KCDFT) {
-    const double r = F.g[0][idx];
-    X.x[4][idx] = log(r) + 2.0 * ce * r;
-  }
+  if constexpr (KIND == KCDFT) X.x[4][idx] = log(r) + 2.0 * ce * r;
 }
 
 // Float64 residual reading the shared quantities of k_shared64.
@@ -1554,16 +1584,20 @@ __global__ void __launch_bounds__(TPB) k_resid64_x(Fields64 F, Shared64 X, Resid
       N[LY::IMU] = g[LY::IMU][n.c] - psi * psi * psi * third - P.alpha * psi - lapk;
       N[LY::IKA] = kc - lapr;
     }
+    double rv[LY::NU];  // all loads (S, rho) before the first store
+#pragma unroll
+    for (int q = 0; q < LY::NU; ++q) rv[q] = F.S[q][idx] - N[q];
+    const double g0c = g[0][idx];
 #pragma unroll
     for (int q = 0; q < LY::NU; ++q) {
-      const double r = F.S[q][idx] - N[q];
+      const double r = rv[q];
       acc[q] += r * r;
       if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = (T)r;
       if (O.e0[q]) static_cast<T*>(O.e0[q])[idx] = T(0);
       if (O.r64[q]) O.r64[q][idx] = r;
     }
     if (O.cr32) {
-      O.cr32[idx] = (float)g[0][idx];
+      O.cr32[idx] = (float)g0c;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) O.cv32[d][idx] = (float)uc[d];
     }
@@ -1582,10 +1616,18 @@ template <int NU, typename T>
 __device__ __forceinline__ void update64_point(const Fields64& F, const Resid64Out& O, int N, double delta,
                                                int idx) {
   if (idx >= N) return;
+  double gv[NU];
+  T ev[NU];  // all loads before the first store
 #pragma unroll
-  for (int q = 0; q < NU; ++q) F.g[q][idx] += (double)static_cast<const T*>(O.e0[q])[idx];
-  const double r = F.g[0][idx];
-  F.g[0][idx] = (delta > 0.0) ? sqrt(r * r + delta * delta) : fabs(r);
+  for (int q = 0; q < NU; ++q) {
+    gv[q] = F.g[q][idx];
+    ev[q] = static_cast<const T*>(O.e0[q])[idx];
+  }
+#pragma unroll
+  for (int q = 0; q < NU; ++q) gv[q] += (double)ev[q];
+  gv[0] = (delta > 0.0) ? sqrt(gv[0] * gv[0] + delta * delta) : fabs(gv[0]);
+#pragma unroll
+  for (int q = 0; q < NU; ++q) F.g[q][idx] = gv[q];
 }
 
 template <int NU, typename T>
@@ -1686,9 +1728,13 @@ template <int DIM>
 __device__ __forceinline__ void commit_point(double* rho, const Vel3W& vel, const double* rnew, const Vel3& gvel,
                                              int N, int idx) {
   if (idx >= N) return;
-  rho[idx] = rnew[idx];
+  double v[DIM];
+  const double r = rnew[idx];
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) vel.p[d][idx] = gvel.p[d][idx];
+  for (int d = 0; d < DIM; ++d) v[d] = gvel.p[d][idx];
+  rho[idx] = r;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) vel.p[d][idx] = v[d];
 }
 
 template <int DIM>
