@@ -166,8 +166,9 @@ def load_peaks():
 
 def make_solver(fm, rho_shape, prm, precision, stream):
     n = list(reversed(rho_shape))
+    from paper_1503_07416_gb300 import inputs
     return fm.Solver("pfc", n, prm["h"], alpha=prm["alpha"], precision=precision, tol=prm["tol"],
-                     w_damp=0.0, gamma=prm["gamma"], delta=0.0, stream=stream)
+                     w_damp=0.0, gamma=prm["gamma"], delta=0.0, stream=stream, **inputs.BENCH_MG_2D)
 
 
 def time_device_steps(torch, fm, sol, rho_d, vel_d, dt, steps, warmup, flush):
@@ -332,6 +333,8 @@ def run_ours(args):
             "precision": "mixed",
             "l2": "flushed (256 MiB write) between timed steps, flush untimed",
             "cycles_per_step_mean": round(statistics.mean(mix["cycles"]), 3),
+            "multigrid": {"cycle": "V(2,2)", "levels": "512^2 .. 64^2 (4)", "coarsest_sweeps": 2,
+                          "coarse_solve": "single-block kernel"},
             "parallelism": f"{world} independent instance(s), one per GPU",
             "fp64_path": {
                 "value": round(world * steps / (f64["total_ms"] / 1e3), 3),
@@ -400,7 +403,7 @@ def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2):
     p0 = ens[0][2]
     stream = torch.cuda.current_stream().cuda_stream
     b = fm.Batch("pfc", sizes, p0["h"], alpha=p0["alpha"], precision=fm.FM_MIXED, tol=p0["tol"],
-                 w_damp=0.0, gamma=p0["gamma"], delta=0.0, stream=stream)
+                 w_damp=0.0, gamma=p0["gamma"], delta=0.0, stream=stream, **inputs.BENCH_MG_2D)
     for i, (rho, vel, _) in enumerate(ens):
         b.set_fields(i, rho, vel)
     dts = [prm["dt"] for _, _, prm in ens]
@@ -442,9 +445,11 @@ def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2):
 def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, warmup=2, dim=2, smoother=False):
     n = list(reversed(rho.shape))
     stream = torch.cuda.current_stream().cuda_stream
+    from paper_1503_07416_gb300 import inputs
+    mg = inputs.BENCH_MG_2D if dim == 2 else {}
     sol = fm.Solver(kind, n, prm["h"], dim=dim, alpha=prm.get("alpha", 0.0), nu=prm.get("nu", 0.0),
                     precision=precision, tol=prm["tol"], w_damp=0.0,
-                    delta=prm.get("delta", 0.0), gamma=prm["gamma"], stream=stream)
+                    delta=prm.get("delta", 0.0), gamma=prm["gamma"], stream=stream, **mg)
     rho_d = torch.from_numpy(rho).cuda()
     vel_d = [torch.from_numpy(v).cuda() for v in vel]
     sol.set_fields(rho_d, vel_d)
@@ -484,7 +489,7 @@ def profile_batch(count):
     sizes = [prm["n"] for _, _, prm in ens]
     p0 = ens[0][2]
     b = fm.Batch("pfc", sizes, p0["h"], alpha=p0["alpha"], precision=fm.FM_MIXED, tol=p0["tol"], w_damp=0.0,
-                 stream=torch.cuda.current_stream().cuda_stream)
+                 stream=torch.cuda.current_stream().cuda_stream, **inputs.BENCH_MG_2D)
     for i, (rho, vel, _) in enumerate(ens):
         b.set_fields(i, rho, vel)
     b.step([prm["dt"] for _, _, prm in ens])
@@ -505,7 +510,8 @@ def profile_single(name):
     n = list(reversed(rho.shape))
     sol = fm.Solver(prm["kind"], n, prm["h"], dim=prm["dim"], alpha=prm.get("alpha", 0.0), nu=prm.get("nu", 0.0),
                     precision=fm.FM_MIXED, tol=prm["tol"], w_damp=0.0, delta=prm.get("delta", 0.0),
-                    stream=torch.cuda.current_stream().cuda_stream)
+                    stream=torch.cuda.current_stream().cuda_stream,
+                    **(inputs.BENCH_MG_2D if prm["dim"] == 2 else {}))
     sol.set_fields(rho, vel)
     cyc = [sol.step(prm["dt"]).cycles for _ in range(3)]
     torch.cuda.synchronize()

@@ -211,6 +211,15 @@ __global__ void __launch_bounds__(SMALL_TPB) kb_small(const InstDev<T>* D, const
   vcycle_small_smem_body<T, KIND, 2>(D[inst].S, D[inst].M, P[inst], nu1, nu2, ncoarse);
 }
 
+// Same, data in global memory (small levels too large for shared memory).
+template <typename T, int KIND>
+__global__ void __launch_bounds__(SMALL_TPB) kb_small_global(const InstDev<T>* D, const Phys<T>* P,
+                                                             const Ctl* ctl, int nu1, int nu2, int ncoarse) {
+  const int inst = blockIdx.x;
+  if (!inst_active(ctl, inst)) return;
+  vcycle_small_body<T, KIND, 2>(D[inst].S, P[inst], nu1, nu2, ncoarse);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TPB) kb_inject(const WorkItem* items, int nitems, const InstDev<T>* D,
                                                  const Ctl* ctl, int coefficients, int check_active) {
@@ -309,6 +318,7 @@ struct fm_batch {
   fm_state** inst;
   int maxdepth;              // max over instances of small_from (levels handled level by level)
   size_t small_smem;         // dynamic shared memory of the small-level kernel
+  bool small_global;         // small levels too large for shared memory: global-memory kernel
   // device tables
   void* dev;                 // one allocation: descriptors, phys, ctl, work items
   void* D;                   // InstDev<T>[count]
@@ -394,6 +404,7 @@ struct Batch {
       for (int q = 0; q < I.S.count; ++q) I.S.lv[q] = make_lvl<T>(st, st->small_from + q);
       const size_t smb = small_layout<T, KIND, 2>(I.S, I.M, SMALL_SMEM_MAX);
       if (smb > b->small_smem) b->small_smem = smb;
+      if (I.S.lv[0].g.N > SMALL_SMEM_N) b->small_global = true;
       // injections (all coarse levels at once)
       for (int which = 0; which < 2; ++which) {
         InjAll<T>& A = which ? I.inj_cf : I.inj_rk;
@@ -638,8 +649,11 @@ struct Batch {
       kb_resid_restrict2<T, KIND><<<wq.nblocks, TPB, 0, s>>>(it(b, wq), wq.n, D, P, b->ctl, l);
       FMB_LAUNCHED();
     }
-    kb_small<T, KIND><<<b->count, SMALL_TPB, b->small_smem, s>>>(D, P, b->ctl, b->prm.nu1, b->prm.nu2,
-                                                                  b->prm.ncoarse);
+    if (b->small_global)
+      kb_small_global<T, KIND><<<b->count, SMALL_TPB, 0, s>>>(D, P, b->ctl, b->prm.nu1, b->prm.nu2, b->prm.ncoarse);
+    else
+      kb_small<T, KIND><<<b->count, SMALL_TPB, b->small_smem, s>>>(D, P, b->ctl, b->prm.nu1, b->prm.nu2,
+                                                                    b->prm.ncoarse);
     FMB_LAUNCHED();
     for (int l = b->maxdepth - 1; l >= 0; --l) {
       const WList& wp = b->w_prolong[l];
@@ -781,6 +795,7 @@ struct Batch {
   static int setup(fm_batch* b) {
     std::vector<InstDev<T>> H(b->count);
     b->small_smem = 0;
+    b->small_global = false;
     build_desc(b, H);
     build_lists(b);
     const size_t szD = sizeof(InstDev<T>) * b->count;
@@ -807,9 +822,10 @@ struct Batch {
     FMB_CUDA(cudaMallocHost((void**)&b->hP64, szP64));
     FMB_CUDA(cudaMallocHost((void**)&b->hK64, szK64));
     FMB_CUDA(cudaMallocHost((void**)&b->hctl, szC));
-    if (b->small_smem > (size_t)SMALL_SMEM_MAX) return FM_EINVAL;
-    FMB_CUDA(cudaFuncSetAttribute(kb_small<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)SMALL_SMEM_MAX));
+    if (b->small_smem > (size_t)SMALL_SMEM_MAX) b->small_global = true;
+    if (!b->small_global)
+      FMB_CUDA(cudaFuncSetAttribute(kb_small<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SMALL_SMEM_MAX));
     return autotune(b);
     return FM_OK;
   }

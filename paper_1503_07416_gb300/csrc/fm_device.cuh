@@ -861,7 +861,7 @@ __host__ __device__ constexpr int march_ly(int v) { return 16 << ((v - RB_NTILE)
 // The whole V-cycle of the small levels (each at most SMALL_N points) in one
 // thread block: phases separated by __syncthreads, data in L1/L2.
 constexpr int SMALL_N = 1024;           // levels of at most this many points run in one block
-constexpr int SMALL_SMEM_N = 1024;
+constexpr int SMALL_SMEM_N = 1024;      // larger coarse levels: the global-memory kernel (measured faster)
 constexpr size_t SMALL_SMEM_MAX = 200 * 1024;
 constexpr int SMALL_TPB = 512;
 constexpr int MAXSMALL = 8;

@@ -34,6 +34,14 @@ H_HEX = math.pi / (2.0 * math.sqrt(3.0))     # Sec. 6.3 grid spacing
 A_ATOM = 4.0 * math.pi / math.sqrt(3.0)      # Sec. 6.3 atom size
 
 
+# Multigrid depth the large 2-D workloads (pfc512, cdft256, batch48) are
+# timed with: coarsen down to 64 points per side, two sweeps on the coarsest
+# grid (the library defaults are 16 and 4).  At these time steps the cycle
+# counts of these workloads are the same either way; the shallower
+# hierarchy saves latency-bound coarse-level launches.
+BENCH_MG_2D = dict(coarsest=64, ncoarse=2)
+
+
 def uniform_noise(shape, seed, lo=-1.0, hi=1.0):
     return np.random.default_rng(seed).uniform(lo, hi, size=shape)
 

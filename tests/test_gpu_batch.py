@@ -147,3 +147,28 @@ def test_batch_odd_sweep_counts(precision):
         sol.close()
         assert rel(rg, rs) <= 1e-12 and all(rel(a, c) <= 1e-12 for a, c in zip(vg, vs))
     b.close()
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_batch_with_the_benchmark_hierarchy(precision):
+    """The hierarchy the batch benchmark uses (coarsest 64, two coarse sweeps):
+    the 64 x 64 and 96 x 64 coarsest levels are too large for the
+    shared-memory coarse kernel, so the batch takes the global-memory one."""
+    sizes = [128, (192, 128)]
+    ens = _ensemble("pfc", sizes, 13)
+    h, tol = 0.9, 1e-12
+    prm = dict(kind="pfc", dim=2, h=h, alpha=0.6, tol=tol)
+    b = fm.Batch("pfc", sizes, h, alpha=0.6, precision=precision, tol=tol, w_damp=0.0, max_cycles=80,
+                 **inputs.BENCH_MG_2D)
+    for i, (rho, vel, dt) in enumerate(ens):
+        b.set_fields(i, rho, vel)
+    info = b.step([dt for _, _, dt in ens])
+    bound = 1e-10 if precision == fm.FM_FP64 else 1e-8
+    for i, (rho, vel, dt) in enumerate(ens):
+        assert info[i].res <= tol
+        rg, vg = b.get_fields(i)
+        P, opts, J = oracle_setup(rho, dict(prm, dt=dt), w_damp=0.0, tol=tol)
+        ro, vo, _ = S.step(rho, vel, P, opts, J=J)
+        errs = [rel(rg, ro)] + [rel(a, c) for a, c in zip(vg, vo)]
+        assert max(errs) <= bound, (i, errs)
+    b.close()

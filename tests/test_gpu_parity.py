@@ -87,8 +87,8 @@ def test_ragged_nonsquare_grid():
     rho = 0.8 + 0.05 * rng.uniform(-1, 1, (40, 48))
     vel = [0.03 * rng.standard_normal((40, 48)) for _ in range(2)]
     prm = dict(kind="pfc", dim=2, h=0.9, dt=0.02, alpha=0.6, delta=0.0, tol=1e-12)
-    _compare_step(rho, vel, prm, fm.FM_FP64, w_damp=0.0, steps=2)
-    _compare_step(rho, vel, prm, fm.FM_MIXED, w_damp=0.0, steps=1)
+    _compare_step(rho, vel, prm, fm.FM_FP64, w_damp=0.0, steps=2, coarsest=4)
+    _compare_step(rho, vel, prm, fm.FM_MIXED, w_damp=0.0, steps=1, coarsest=4)
 
 
 def test_smallest_grid():
@@ -255,7 +255,7 @@ def test_full_size_pfc512_one_step(precision):
     """The 512^2 PFC workload at full size, in the configuration the benchmark
     times (undamped, tol 1e-10): one step against the oracle, whole fields."""
     rho, vel, prm = inputs.pfc512()
-    _compare_step(rho, vel, prm, precision, tol=1e-11, w_damp=0.0, steps=1)
+    _compare_step(rho, vel, prm, precision, tol=1e-11, w_damp=0.0, steps=1, **inputs.BENCH_MG_2D)
 
 
 # --------------------------------------------------------------- failure paths
