@@ -26,6 +26,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -358,6 +359,7 @@ def run_ours(args):
             "traffic": traffic,
             "algorithmic_bytes_per_launch": bytes_launch,
             "launch_ms": round(avg_ms, 6),
+            "dof_sweeps_per_s": round(5 * N / (avg_ms * 1e-3), 1) if sm_n else None,  # 5 unknowns per point
             "launches_timed": sm_n,
             "launch_timing": "CUDA events around each finest-level smoother launch, in a pass of "
                              "the same steps run launch by launch (the timed steps run as graphs)",
@@ -434,6 +436,7 @@ def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2):
         "smoother_roofline": {"kernel": sweep_kernel(tune0[0], True) + ", finest level of all instances",
                               "bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                               "frac": round(gbs / peak, 4), "launch_ms": round(ms_sm, 5),
+                              "dof_sweeps_per_s": round(5 * pts / (ms_sm * 1e-3), 1),
                               "algorithmic_bytes_per_launch": words * 4 * pts,
                               "timing": "20 back-to-back launches after a warm-up, CUDA events",
                               "traffic": profiled_traffic("kb_smooth_batch48", tune0[0]),
@@ -468,7 +471,9 @@ def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, wa
         pts = rho.size // 2 if dim == 3 else rho.size
         words = 26 if dim == 3 else 20  # 3-D PFC: e 6, f 6, rho^k, omega 3, rho, u 3 read; e 6 written
         wb = 4 if precision == fm.FM_MIXED else 8
+        nu = (5 if kind == "pfc" else 3) + (1 if dim == 3 else 0)
         out["smoother"] = {"launch_ms": round(per, 5), "points_per_launch": pts,
+                           "dof_sweeps_per_s": round(nu * pts / (per * 1e-3), 1),
                            "achieved_gbs": round(words * wb * pts / (per * 1e-3) / 1e9, 1),
                            "algorithmic_bytes_per_launch": words * wb * pts}
     sol.close()
@@ -556,10 +561,26 @@ def oracle_steps(nsteps, budget_s):
     return done, dt
 
 
+def host_info():
+    """Core count and CPU model of the host the oracle runs on."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model, "machine": platform.machine()}
+
+
 def cpu_baseline(nsteps):
     done, dt = oracle_steps(nsteps, 30.0)
     return {"value": round(done / dt, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} steps of the pfc512 workload (numpy FP64 oracle, single thread)"}
+            "sample": f"{done} steps of the pfc512 workload (numpy FP64 oracle, single thread)",
+            "host": host_info()}
 
 
 def run_reference(args):
@@ -575,7 +596,8 @@ def run_reference(args):
         "data": "synthetic (seeded)", "impl": "reference",
         "config": {"workload": WORKLOAD, "grid": [512, 512], "precision": "fp64 oracle"},
         "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{done} steps of the pfc512 workload (bounded to ~120 s)"},
+                         "sample": f"{done} steps of the pfc512 workload (bounded to ~120 s)",
+                         "host": host_info()},
         "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
