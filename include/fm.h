@@ -267,6 +267,14 @@ int fm_profile(fm_state* st, int enable);
 int fm_profile_read(const fm_state* st, double* smoother_ms, long long* smoother_launches,
                     long long* launches);
 
+/* Diagnostic (no counterpart in the paper): out[i] = in[i] narrowed from
+ * float64 to float32 exactly as the float64 residual kernels narrow the
+ * right-hand side and coefficients they hand to the float32 cycle (round to
+ * nearest, ties to even, computed with integer instructions); in and out are
+ * device arrays of n values, the work is issued on `stream` and synchronised.
+ * Exposed so that it can be compared bit for bit with the CUDA conversion. */
+int fm_narrow(const double* in, float* out, long long n, void* stream);
+
 /* ---- Allocation-free entry point (the paper has no counterpart). ---- */
 
 /* Largest grid fm_mass_noalloc accepts: 4096 blocks x 1024 points. */

@@ -1243,21 +1243,28 @@ __global__ void __launch_bounds__(TPB) k_prepare_mu(Fields64 F, Geo G, Step64 K,
   prepare_mu_point<DIM>(F, G, K, P, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// Fixed-order block sum of NQ per-thread values into partials[blk][q]: a
+// tree in shared memory down to one warp, then shuffles.  Few float64 warp
+// instructions (the float64 pipe is the bound of the residual kernels), and
+// the same order on every run.
 template <int NQ>
 __device__ __forceinline__ void block_partials(double (&v)[NQ], double* partials, int blk) {
-  __shared__ double sm[NQ][TPB / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ double sm[NQ][TPB];
+  const int tid = threadIdx.x, lane = tid & 31;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q)
-    for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) sm[q][warp] = v[q];
+  for (int q = 0; q < NQ; ++q) sm[q][tid] = v[q];
   __syncthreads();
-  if (warp == 0) {
+#pragma unroll
+  for (int s = TPB / 2; s >= 32; s >>= 1) {
+    if (tid < s)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) sm[q][tid] += sm[q][tid + s];
+    __syncthreads();
+  }
+  if (tid < 32) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      double x = (lane < TPB / 32) ? sm[q][lane] : 0.0;
+      double x = sm[q][lane];
       for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
       if (lane == 0) partials[blk * NQ + q] = x;
     }
@@ -1323,6 +1330,55 @@ __global__ void k_norm_final(const double* partials, int nblk, double w, double*
     }
     out[0] = finite ? mx : NAN;
   }
+}
+
+// float64 -> float32 rounded to nearest, ties to even, with integer
+// instructions only (IEEE 754 binary64 -> binary32 narrowing written from the
+// two formats' definitions).  The hardware conversion runs on the float64
+// pipe, which bounds the residual kernels that write the float32 right-hand
+// side; this one runs on the integer pipes.  Exact for every input: normal
+// and subnormal results, overflow to infinity, signed zeros; NaN stays NaN.
+__host__ __device__ inline float narrow_rn(double x) {
+  unsigned long long b;
+  memcpy(&b, &x, sizeof(b));
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  unsigned r;
+  if (ex == 0x7FF) {
+    r = 0x7F800000u | (m ? (0x400000u | (unsigned)(m >> 29)) : 0u);  // infinity, or a quiet NaN
+  } else {
+    const int E = ex - 1023 + 127;  // biased binary32 exponent of a normal result
+    unsigned long long mant;
+    int sh;
+    if (E > 0) {  // normal range: keep 23 of the 52 fraction bits
+      mant = ((unsigned long long)E << 52 | m) >> 0;  // exponent travels with the fraction
+      sh = 29;
+    } else {      // subnormal result (or zero): the implicit bit becomes explicit
+      mant = ex ? (m | (1ull << 52)) : m;
+      sh = 30 - E;
+    }
+    if (sh >= 64) {
+      r = 0u;  // below half the smallest subnormal
+    } else {
+      const unsigned long long keep = mant >> sh;
+      const unsigned long long rem = mant & ((1ull << sh) - 1ull);
+      const unsigned long long half = 1ull << (sh - 1);
+      unsigned long long q = keep + ((rem > half || (rem == half && (keep & 1ull))) ? 1ull : 0ull);
+      if (E > 0 && q >= (255ull << 23)) q = 255ull << 23;  // overflow: infinity
+      r = (unsigned)q;
+    }
+  }
+  r |= sign;
+  float f;
+  memcpy(&f, &r, sizeof(f));
+  return f;
+}
+
+template <typename T>
+__device__ __forceinline__ T to_t(double x) {
+  if constexpr (sizeof(T) == 4) return narrow_rn(x);
+  else return (T)x;
 }
 
 struct Resid64Out {
@@ -1401,14 +1457,14 @@ __device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out
     for (int q = 0; q < LY::NU; ++q) {
       const double r = rv[q];
       acc[q] += r * r;
-      if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = (T)r;
+      if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = to_t<T>(r);
       if (O.e0[q]) static_cast<T*>(O.e0[q])[idx] = T(0);
       if (O.r64[q]) O.r64[q][idx] = r;
     }
     if (O.cr32) {
-      O.cr32[idx] = (float)g0c;
+      O.cr32[idx] = narrow_rn(g0c);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) O.cv32[d][idx] = (float)uc[d];
+      for (int d = 0; d < DIM; ++d) O.cv32[d][idx] = narrow_rn(uc[d]);
     }
   }
   block_partials<LY::NU>(acc, partials, lb);
@@ -1494,14 +1550,14 @@ __device__ __forceinline__ void resid64_tile_body(const Fields64& F, const Resid
         for (int q = 0; q < LY::NU; ++q) {
           const double r = rv[q];
           acc[q] += r * r;
-          if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = (T)r;
+          if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = to_t<T>(r);
           if (O.e0[q]) static_cast<T*>(O.e0[q])[idx] = T(0);
           if (O.r64[q]) O.r64[q][idx] = r;
         }
         if (O.cr32) {
-          O.cr32[idx] = (float)g0c;
-          O.cv32[0][idx] = (float)uc;
-          O.cv32[1][idx] = (float)vc;
+          O.cr32[idx] = narrow_rn(g0c);
+          O.cv32[0][idx] = narrow_rn(uc);
+          O.cv32[1][idx] = narrow_rn(vc);
         }
       }
     }
@@ -1592,14 +1648,14 @@ __global__ void __launch_bounds__(TPB) k_resid64_x(Fields64 F, Shared64 X, Resid
     for (int q = 0; q < LY::NU; ++q) {
       const double r = rv[q];
       acc[q] += r * r;
-      if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = (T)r;
+      if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = to_t<T>(r);
       if (O.e0[q]) static_cast<T*>(O.e0[q])[idx] = T(0);
       if (O.r64[q]) O.r64[q][idx] = r;
     }
     if (O.cr32) {
-      O.cr32[idx] = (float)g0c;
+      O.cr32[idx] = narrow_rn(g0c);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) O.cv32[d][idx] = (float)uc[d];
+      for (int d = 0; d < DIM; ++d) O.cv32[d][idx] = narrow_rn(uc[d]);
     }
   }
   block_partials<LY::NU>(acc, partials, blockIdx.x);

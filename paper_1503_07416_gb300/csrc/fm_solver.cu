@@ -46,6 +46,11 @@ __global__ void __launch_bounds__(TPB) k_convert(const A* in, B* out, int N) {
   if (i < N) out[i] = (B)in[i];
 }
 
+__global__ void __launch_bounds__(TPB) k_narrow(const double* in, float* out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = narrow_rn(in[i]);
+}
+
 __global__ void k_restrict_one(const double* fine, double* coarse, Geo F, Geo C, int dim) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= C.N) return;
@@ -1096,6 +1101,18 @@ int fm_smooth(fm_state* st, double* const* e, const double* const* f, int sweeps
     if (!e[q] || !f[q]) return FM_EINVAL;
   return st->prm.precision == FM_MIXED ? dispatch_smooth_row<float>(st, e, f, sweeps, variant, where)
                                        : dispatch_smooth_row<double>(st, e, f, sweeps, variant, where);
+}
+
+int fm_narrow(const double* in, float* out, long long n, void* stream) {
+  if (!in || !out || n < 0) return FM_EINVAL;
+  if (n == 0) return FM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long nb = (n + TPB - 1) / TPB;
+  if (nb > 0x7fffffffLL) return FM_EINVAL;
+  k_narrow<<<(int)nb, TPB, 0, s>>>(in, out, n);
+  if (cudaGetLastError() != cudaSuccess) return FM_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FM_ECUDA;
+  return FM_OK;
 }
 
 int fm_energy(fm_state* st, double* E, double* F, double* KE) {

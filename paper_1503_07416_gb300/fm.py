@@ -82,6 +82,7 @@ _SIGS = {
     "fm_restrict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "fm_prolong_add": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "fm_levels": (C.c_int, [C.c_void_p]),
+    "fm_narrow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "fm_smooth": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int]),
     "fm_create_batch": (C.c_int, [C.c_int, C.POINTER(fm_grid), C.POINTER(fm_params), C.POINTER(fm_functional),
                                   C.POINTER(C.c_void_p)]),
@@ -234,6 +235,13 @@ def fm_smooth(st, e, f, sweeps, variant=FM_SWEEP_AUTO):
     nu float64 arrays) is updated in place."""
     w = _where(list(e) + list(f))
     _check(lib().fm_smooth(st, _vec(e), _vec(f), int(sweeps), int(variant), w), "fm_smooth")
+
+
+def fm_narrow(inp, out, stream=None):
+    """out (float32 CUDA tensor) = inp (float64 CUDA tensor) narrowed as the
+    residual kernels narrow the float32 right-hand side."""
+    _check(lib().fm_narrow(C.c_void_p(inp.data_ptr()), C.c_void_p(out.data_ptr()), inp.numel(),
+                           C.c_void_p(stream)), "fm_narrow")
 
 
 def fm_convolve(st, rho, out):

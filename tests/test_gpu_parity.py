@@ -377,3 +377,24 @@ def test_restart_continues_bitwise(precision, monkeypatch):
     assert ea == eb and a.mass() == c.mass()
     a.close()
     c.close()
+
+
+def test_narrowing_matches_cuda_conversion():
+    """The integer float64 -> float32 narrowing the residual kernels use for
+    the float32 right-hand side gives the same bits as the CUDA conversion
+    (round to nearest even) on edge cases and on random bit patterns."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(77)
+    edge = [0.0, -0.0, 1.0, -1.5, 2.0 ** -149, 2.0 ** -150, 3 * 2.0 ** -150, 2.0 ** -126,
+            2.0 ** -126 * (1 - 2.0 ** -30), 3.4028234663852886e38, 3.4028235677973366e38, 1e39, -1e39,
+            math.inf, -math.inf, 1 + 2.0 ** -24, 1 + 3 * 2.0 ** -24, 5e-324, 1e-310, 0.1, 1 / 3]
+    vals = np.concatenate([np.array(edge),
+                           rng.standard_normal(100000) * 10.0 ** rng.integers(-45, 40, 100000),
+                           rng.integers(0, 2 ** 63, 100000, dtype=np.int64).view(np.float64)])
+    x = torch.from_numpy(vals).cuda()
+    out = torch.empty(x.numel(), dtype=torch.float32, device="cuda")
+    fm.fm_narrow(x, out)
+    ref = x.to(torch.float32)
+    nan = torch.isnan(ref)
+    assert torch.equal(torch.isnan(out), nan)
+    assert torch.equal(out[~nan].view(torch.int32), ref[~nan].view(torch.int32))
