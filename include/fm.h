@@ -275,6 +275,13 @@ int fm_profile_read(const fm_state* st, double* smoother_ms, long long* smoother
  * Exposed so that it can be compared bit for bit with the CUDA conversion. */
 int fm_narrow(const double* in, float* out, long long n, void* stream);
 
+/* Diagnostic (no counterpart in the paper): out[i] = in[i] widened from
+ * float32 to float64 (exact) with integer instructions, as the float64
+ * update g += e widens the float32 correction; device arrays, n values, on
+ * `stream`, synchronised.  For a bit-for-bit comparison with the CUDA
+ * conversion. */
+int fm_widen(const float* in, double* out, long long n, void* stream);
+
 /* ---- Allocation-free entry point (the paper has no counterpart). ---- */
 
 /* Largest grid fm_mass_noalloc accepts: 4096 blocks x 1024 points. */

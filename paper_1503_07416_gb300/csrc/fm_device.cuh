@@ -1119,6 +1119,84 @@ struct Vel3W {
   double* p[3];
 };
 
+// float64 -> float32 rounded to nearest, ties to even, with integer
+// instructions only (IEEE 754 binary64 -> binary32 narrowing written from the
+// two formats' definitions).  The hardware conversion runs on the float64
+// pipe, which bounds the residual kernels that write the float32 right-hand
+// side; this one runs on the integer pipes.  Exact for every input: normal
+// and subnormal results, overflow to infinity, signed zeros; NaN stays NaN.
+__host__ __device__ inline float narrow_rn(double x) {
+  unsigned long long b;
+  memcpy(&b, &x, sizeof(b));
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  unsigned r;
+  if (ex == 0x7FF) {
+    r = 0x7F800000u | (m ? (0x400000u | (unsigned)(m >> 29)) : 0u);  // infinity, or a quiet NaN
+  } else {
+    const int E = ex - 1023 + 127;  // biased binary32 exponent of a normal result
+    unsigned long long mant;
+    int sh;
+    if (E > 0) {  // normal range: keep 23 of the 52 fraction bits
+      mant = ((unsigned long long)E << 52 | m) >> 0;  // exponent travels with the fraction
+      sh = 29;
+    } else {      // subnormal result (or zero): the implicit bit becomes explicit
+      mant = ex ? (m | (1ull << 52)) : m;
+      sh = 30 - E;
+    }
+    if (sh >= 64) {
+      r = 0u;  // below half the smallest subnormal
+    } else {
+      const unsigned long long keep = mant >> sh;
+      const unsigned long long rem = mant & ((1ull << sh) - 1ull);
+      const unsigned long long half = 1ull << (sh - 1);
+      unsigned long long q = keep + ((rem > half || (rem == half && (keep & 1ull))) ? 1ull : 0ull);
+      if (E > 0 && q >= (255ull << 23)) q = 255ull << 23;  // overflow: infinity
+      r = (unsigned)q;
+    }
+  }
+  r |= sign;
+  float f;
+  memcpy(&f, &r, sizeof(f));
+  return f;
+}
+
+// float32 -> float64 (exact) with integer instructions only, for the same
+// reason: every binary32 value is a binary64 value; subnormal inputs are
+// normalised with a leading-zero count.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  const unsigned ex = (b >> 23) & 0xFFu;
+  const unsigned m = b & 0x7FFFFFu;
+  unsigned long long r;
+  if (ex == 0xFFu) {
+    r = 0x7FF0000000000000ull | ((unsigned long long)m << 29);  // infinity or NaN (payload kept)
+  } else if (ex != 0u) {
+    r = ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)m << 29);
+  } else if (m == 0u) {
+    r = 0ull;
+  } else {  // subnormal: m * 2^-149 = 1.f * 2^(p - 149), p the position of m's leading one
+    const int lz = __clz(m) - 8;  // 23 - p
+    const unsigned mn = (m << lz) & 0x7FFFFFu;
+    r = ((unsigned long long)(897 - lz) << 52) | ((unsigned long long)mn << 29);
+  }
+  return __longlong_as_double((long long)(sign | r));
+}
+
+template <typename T>
+__device__ __forceinline__ double from_t(T x) {
+  if constexpr (sizeof(T) == 4) return widen(x);
+  else return (double)x;
+}
+
+template <typename T>
+__device__ __forceinline__ T to_t(double x) {
+  if constexpr (sizeof(T) == 4) return narrow_rn(x);
+  else return (T)x;
+}
+
 // Step constants of the float64 kernels (grid spacing h, step s), formed once
 // per step on the host (per instance for a batch) instead of per thread.
 struct Step64 {
@@ -1212,9 +1290,9 @@ __device__ __forceinline__ void prepare_point(const Fields64& F, const Geo& G, c
 #pragma unroll
   for (int d = 0; d < LY::NOM; ++d) F.om[d][idx] = w[d];
   if (F.rk32) {
-    F.rk32[idx] = (float)rkc;
+    F.rk32[idx] = narrow_rn(rkc);
 #pragma unroll
-    for (int d = 0; d < LY::NOM; ++d) F.om32[d][idx] = (float)w[d];
+    for (int d = 0; d < LY::NOM; ++d) F.om32[d][idx] = narrow_rn(w[d]);
   }
 }
 
@@ -1332,54 +1410,6 @@ __global__ void k_norm_final(const double* partials, int nblk, double w, double*
   }
 }
 
-// float64 -> float32 rounded to nearest, ties to even, with integer
-// instructions only (IEEE 754 binary64 -> binary32 narrowing written from the
-// two formats' definitions).  The hardware conversion runs on the float64
-// pipe, which bounds the residual kernels that write the float32 right-hand
-// side; this one runs on the integer pipes.  Exact for every input: normal
-// and subnormal results, overflow to infinity, signed zeros; NaN stays NaN.
-__host__ __device__ inline float narrow_rn(double x) {
-  unsigned long long b;
-  memcpy(&b, &x, sizeof(b));
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int ex = (int)((b >> 52) & 0x7FF);
-  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  unsigned r;
-  if (ex == 0x7FF) {
-    r = 0x7F800000u | (m ? (0x400000u | (unsigned)(m >> 29)) : 0u);  // infinity, or a quiet NaN
-  } else {
-    const int E = ex - 1023 + 127;  // biased binary32 exponent of a normal result
-    unsigned long long mant;
-    int sh;
-    if (E > 0) {  // normal range: keep 23 of the 52 fraction bits
-      mant = ((unsigned long long)E << 52 | m) >> 0;  // exponent travels with the fraction
-      sh = 29;
-    } else {      // subnormal result (or zero): the implicit bit becomes explicit
-      mant = ex ? (m | (1ull << 52)) : m;
-      sh = 30 - E;
-    }
-    if (sh >= 64) {
-      r = 0u;  // below half the smallest subnormal
-    } else {
-      const unsigned long long keep = mant >> sh;
-      const unsigned long long rem = mant & ((1ull << sh) - 1ull);
-      const unsigned long long half = 1ull << (sh - 1);
-      unsigned long long q = keep + ((rem > half || (rem == half && (keep & 1ull))) ? 1ull : 0ull);
-      if (E > 0 && q >= (255ull << 23)) q = 255ull << 23;  // overflow: infinity
-      r = (unsigned)q;
-    }
-  }
-  r |= sign;
-  float f;
-  memcpy(&f, &r, sizeof(f));
-  return f;
-}
-
-template <typename T>
-__device__ __forceinline__ T to_t(double x) {
-  if constexpr (sizeof(T) == 4) return narrow_rn(x);
-  else return (T)x;
-}
 
 struct Resid64Out {
   void* f0[MAXU];   // precision-T rhs of level 0 (or null)
@@ -1680,7 +1710,7 @@ __device__ __forceinline__ void update64_point(const Fields64& F, const Resid64O
     ev[q] = static_cast<const T*>(O.e0[q])[idx];
   }
 #pragma unroll
-  for (int q = 0; q < NU; ++q) gv[q] += (double)ev[q];
+  for (int q = 0; q < NU; ++q) gv[q] += from_t<T>(ev[q]);
   gv[0] = (delta > 0.0) ? sqrt(gv[0] * gv[0] + delta * delta) : fabs(gv[0]);
 #pragma unroll
   for (int q = 0; q < NU; ++q) F.g[q][idx] = gv[q];

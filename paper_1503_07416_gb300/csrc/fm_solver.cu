@@ -51,6 +51,11 @@ __global__ void __launch_bounds__(TPB) k_narrow(const double* in, float* out, lo
   if (i < n) out[i] = narrow_rn(in[i]);
 }
 
+__global__ void __launch_bounds__(TPB) k_widen(const float* in, double* out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = widen(in[i]);
+}
+
 __global__ void k_restrict_one(const double* fine, double* coarse, Geo F, Geo C, int dim) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= C.N) return;
@@ -1110,6 +1115,18 @@ int fm_narrow(const double* in, float* out, long long n, void* stream) {
   const long long nb = (n + TPB - 1) / TPB;
   if (nb > 0x7fffffffLL) return FM_EINVAL;
   k_narrow<<<(int)nb, TPB, 0, s>>>(in, out, n);
+  if (cudaGetLastError() != cudaSuccess) return FM_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FM_ECUDA;
+  return FM_OK;
+}
+
+int fm_widen(const float* in, double* out, long long n, void* stream) {
+  if (!in || !out || n < 0) return FM_EINVAL;
+  if (n == 0) return FM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long nb = (n + TPB - 1) / TPB;
+  if (nb > 0x7fffffffLL) return FM_EINVAL;
+  k_widen<<<(int)nb, TPB, 0, s>>>(in, out, n);
   if (cudaGetLastError() != cudaSuccess) return FM_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return FM_ECUDA;
   return FM_OK;

@@ -83,6 +83,7 @@ _SIGS = {
     "fm_prolong_add": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "fm_levels": (C.c_int, [C.c_void_p]),
     "fm_narrow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
+    "fm_widen": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "fm_smooth": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int]),
     "fm_create_batch": (C.c_int, [C.c_int, C.POINTER(fm_grid), C.POINTER(fm_params), C.POINTER(fm_functional),
                                   C.POINTER(C.c_void_p)]),
@@ -242,6 +243,13 @@ def fm_narrow(inp, out, stream=None):
     residual kernels narrow the float32 right-hand side."""
     _check(lib().fm_narrow(C.c_void_p(inp.data_ptr()), C.c_void_p(out.data_ptr()), inp.numel(),
                            C.c_void_p(stream)), "fm_narrow")
+
+
+def fm_widen(inp, out, stream=None):
+    """out (float64 CUDA tensor) = inp (float32 CUDA tensor) widened as the
+    float64 update widens the float32 correction."""
+    _check(lib().fm_widen(C.c_void_p(inp.data_ptr()), C.c_void_p(out.data_ptr()), inp.numel(),
+                          C.c_void_p(stream)), "fm_widen")
 
 
 def fm_convolve(st, rho, out):

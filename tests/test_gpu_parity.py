@@ -398,3 +398,21 @@ def test_narrowing_matches_cuda_conversion():
     nan = torch.isnan(ref)
     assert torch.equal(torch.isnan(out), nan)
     assert torch.equal(out[~nan].view(torch.int32), ref[~nan].view(torch.int32))
+
+
+def test_widening_matches_cuda_conversion():
+    """The integer float32 -> float64 widening of the float64 update gives the
+    same bits as the CUDA conversion on every class of input (random bit
+    patterns cover subnormals, infinities and NaNs)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(78)
+    bits = np.concatenate([np.array([0, 0x80000000, 1, 0x80000001, 0x7FFFFF, 0x400000, 0x100, 0x7F800000,
+                                     0xFF800000, 0x7F7FFFFF, 0x800000], dtype=np.uint32),
+                           rng.integers(0, 2 ** 32, 200000, dtype=np.uint64).astype(np.uint32)])
+    x = torch.from_numpy(bits.view(np.float32)).cuda()
+    out = torch.empty(x.numel(), dtype=torch.float64, device="cuda")
+    fm.fm_widen(x, out)
+    ref = x.to(torch.float64)
+    nan = torch.isnan(ref)
+    assert torch.equal(torch.isnan(out), nan)
+    assert torch.equal(out[~nan].view(torch.int64), ref[~nan].view(torch.int64))
