@@ -130,6 +130,16 @@ int fm_get_fields(fm_state* st, double* rho, double* const* vel, int where);
  * the state unchanged. */
 int fm_step(fm_state* st, double dt, fm_step_info* info);
 
+/* One step for a caller that keeps the fields in host memory: copies rho_in
+ * and vel_in[0..dim-1] (host arrays, nx*ny*nz float64 each; pinned memory
+ * lets the copies run asynchronously) into the state, runs fm_step's step on
+ * the state's stream and copies the new rho and velocity to rho_out and
+ * vel_out (host), with a single host synchronisation at the end.  The same
+ * arithmetic as fm_set_fields + fm_step + fm_get_fields.  On FM_ENOCONV /
+ * FM_ENAN the state and the outputs hold the inputs (time level k). */
+int fm_step_host(fm_state* st, double dt, const double* rho_in, const double* const* vel_in,
+                 double* rho_out, double* const* vel_out, fm_step_info* info);
+
 /* Total energy E = 1/2 (rho u || u) + F[rho] (Thm 5.1) of the current state,
  * with F the discrete PFC energy (Eq. CS_PFC_discrete) or the CDFT energy
  * (Eq. CS_DFT_discrete); F and KE separately.  Float64 deterministic

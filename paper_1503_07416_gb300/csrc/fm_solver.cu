@@ -678,6 +678,41 @@ struct Solver {
     return FM_OK;
   }
 
+  // One step for host-resident fields: the input copies, the step and the
+  // output copies on the state's stream, one host synchronisation (graph
+  // mode).  On failure the state and the outputs keep time level k.
+  static int step_host(fm_state* st, const double* rho_in, const double* const* vel_in, double* rho_out,
+                       double* const* vel_out, fm_step_info* info) {
+    const size_t bytes = (size_t)st->lv[0].g.N * sizeof(double);
+    const bool graph = !(st->prof || !st->use_graph);
+    if (graph && (!st->gexec || st->graph_dt != st->dt)) {
+      const int rc = build_graph(st);  // captured on private streams
+      if (rc) return rc;
+    }
+    FM_CUDA(cudaMemcpyAsync(st->rho, rho_in, bytes, cudaMemcpyHostToDevice, st->stream));
+    for (int d = 0; d < DIM; ++d)
+      FM_CUDA(cudaMemcpyAsync(st->vel[d], vel_in[d], bytes, cudaMemcpyHostToDevice, st->stream));
+    st->prepared = false;
+    int rc;
+    if (graph) {
+      FM_CUDA(cudaGraphLaunch(st->gexec, st->stream));
+      rc = FM_OK;
+    } else {
+      rc = step_hostloop(st, nullptr);  // synchronises; status read below
+      if (rc != FM_OK && rc != FM_ENOCONV && rc != FM_ENAN) return rc;
+    }
+    FM_CUDA(cudaMemcpyAsync(rho_out, st->rho, bytes, cudaMemcpyDeviceToHost, st->stream));
+    for (int d = 0; d < DIM; ++d)
+      FM_CUDA(cudaMemcpyAsync(vel_out[d], st->vel[d], bytes, cudaMemcpyDeviceToHost, st->stream));
+    FM_CUDA(cudaStreamSynchronize(st->stream));
+    if (graph) {
+      Ctl c;
+      memcpy(&c, st->hscal + 32, sizeof(Ctl));
+      st->launches += st->cnt_pre + (long long)c.cycles * st->cnt_body + st->cnt_post;
+    }
+    return finish(st, info);
+  }
+
   static int step(fm_state* st, fm_step_info* info) {
     if (st->prof || !st->use_graph) return step_hostloop(st, info);
     if (!st->gexec || st->graph_dt != st->dt) {
@@ -699,6 +734,17 @@ static int dispatch_step(fm_state* st, fm_step_info* info) {
     return st->dim == 2 ? Solver<T, KPFC, 2>::step(st, info) : Solver<T, KPFC, 3>::step(st, info);
   }
   return st->dim == 2 ? Solver<T, KCDFT, 2>::step(st, info) : Solver<T, KCDFT, 3>::step(st, info);
+}
+
+template <typename T>
+static int dispatch_step_host(fm_state* st, const double* ri, const double* const* vi, double* ro,
+                              double* const* vo, fm_step_info* info) {
+  if (st->kind == FM_PFC) {
+    return st->dim == 2 ? Solver<T, KPFC, 2>::step_host(st, ri, vi, ro, vo, info)
+                        : Solver<T, KPFC, 3>::step_host(st, ri, vi, ro, vo, info);
+  }
+  return st->dim == 2 ? Solver<T, KCDFT, 2>::step_host(st, ri, vi, ro, vo, info)
+                      : Solver<T, KCDFT, 3>::step_host(st, ri, vi, ro, vo, info);
 }
 
 template <typename T>
@@ -1050,6 +1096,16 @@ int fm_get_fields(fm_state* st, double* rho, double* const* vel, int where) {
       if (vel[d]) FM_CUDA(cudaMemcpyAsync(vel[d], st->vel[d], bytes, kind_out(where), st->stream));
   if (where == FM_HOST) FM_CUDA(cudaStreamSynchronize(st->stream));
   return FM_OK;
+}
+
+int fm_step_host(fm_state* st, double dt, const double* rho_in, const double* const* vel_in, double* rho_out,
+                 double* const* vel_out, fm_step_info* info) {
+  if (!st || !(dt > 0.0) || !rho_in || !vel_in || !rho_out || !vel_out) return FM_EINVAL;
+  for (int d = 0; d < st->dim; ++d)
+    if (!vel_in[d] || !vel_out[d]) return FM_EINVAL;
+  st->dt = dt;
+  return st->prm.precision == FM_MIXED ? dispatch_step_host<float>(st, rho_in, vel_in, rho_out, vel_out, info)
+                                       : dispatch_step_host<double>(st, rho_in, vel_in, rho_out, vel_out, info);
 }
 
 int fm_prepare(fm_state* st, double dt) {

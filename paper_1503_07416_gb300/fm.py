@@ -70,6 +70,8 @@ _SIGS = {
     "fm_set_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
     "fm_get_fields": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.c_int]),
     "fm_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(fm_step_info)]),
+    "fm_step_host": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.POINTER(C.c_void_p), C.c_void_p,
+                               C.POINTER(C.c_void_p), C.POINTER(fm_step_info)]),
     "fm_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                             C.POINTER(C.c_double)]),
     "fm_mass": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -188,6 +190,15 @@ def fm_step(st, dt):
     info = fm_step_info()
     _check(lib().fm_step(st, C.c_double(dt), C.byref(info)), "fm_step")
     return info
+
+
+def fm_step_host(st, dt, rho_in, vel_in, rho_out, vel_out):
+    """fm_step_host: one step of host-resident fields (numpy or CPU tensors,
+    float64, C-contiguous); returns (code, info) without raising."""
+    info = fm_step_info()
+    code = lib().fm_step_host(st, C.c_double(dt), C.c_void_p(_ptr(rho_in)[0]), _vec(vel_in),
+                              C.c_void_p(_ptr(rho_out)[0]), _vec(vel_out), C.byref(info))
+    return code, info
 
 
 def fm_step_raw(st, dt):
@@ -451,6 +462,15 @@ class Solver:
 
     def step(self, dt):
         return fm_step(self.handle, dt)
+
+    def step_host(self, dt, rho_in, vel_in, rho_out, vel_out):
+        """One step of host-resident fields (fm_step_host); raises on failure."""
+        for a in [rho_in, *vel_in, rho_out, *vel_out]:
+            if _ptr(a)[1] != FM_HOST:
+                raise ValueError("fm_step_host takes host arrays")
+        code, info = fm_step_host(self.handle, dt, rho_in, vel_in, rho_out, vel_out)
+        _check(code, "fm_step_host")
+        return info
 
     def energy(self):
         return fm_energy(self.handle)

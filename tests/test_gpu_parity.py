@@ -416,3 +416,32 @@ def test_widening_matches_cuda_conversion():
     nan = torch.isnan(ref)
     assert torch.equal(torch.isnan(out), nan)
     assert torch.equal(out[~nan].view(torch.int64), ref[~nan].view(torch.int64))
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_step_host_equals_set_step_get(precision):
+    """fm_step_host (host fields in and out, one synchronisation) gives the
+    same bits as fm_set_fields + fm_step + fm_get_fields, three steps in a
+    row, and leaves the inputs in the outputs on failure."""
+    rho, vel, prm = inputs.pfc_supercooled(128, seed=23)
+    a = gpu_solver(rho, prm, precision=precision, w_damp=0.0)
+    b = gpu_solver(rho, prm, precision=precision, w_damp=0.0)
+    ra, va = rho.copy(), [v.copy() for v in vel]
+    rb, vb = rho.copy(), [v.copy() for v in vel]
+    for _ in range(3):
+        a.set_fields(ra, va)
+        ia = a.step(prm["dt"])
+        ra, va = a.get_fields()
+        ro, vo = np.empty_like(rb), [np.empty_like(v) for v in vb]
+        ib = b.step_host(prm["dt"], rb, vb, ro, vo)
+        rb, vb = ro, vo
+        assert ia.cycles == ib.cycles
+        assert np.array_equal(ra, rb) and all(np.array_equal(x, y) for x, y in zip(va, vb))
+    bad = rb.copy()
+    bad[5, 7] = math.nan
+    ro, vo = np.empty_like(rb), [np.empty_like(v) for v in vb]
+    code, _ = fm.fm_step_host(b.handle, prm["dt"], bad, vb, ro, vo)
+    assert code == fm.FM_ENAN
+    assert np.isnan(ro[5, 7]) and np.array_equal(vo[0], vb[0])
+    a.close()
+    b.close()
