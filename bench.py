@@ -130,12 +130,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def sweeps_per_launch(variant):
+    """Red-black sweeps one launch of fused-sweep variant `variant` runs."""
+    return 2 if variant >= 18 else 1
+
+
 def sweep_kernel(variant, batched):
     """Name of the fused-sweep kernel that variant `variant` launches."""
     pre = "kb_" if batched else "k_"
     if variant >= 12:
-        tx = 64 if variant < 15 else 128
-        ly = 16 << ((variant - 12) % 3)
+        m = (variant - 12) % 6
+        tx = 64 if m < 3 else 128
+        ly = 16 << (m % 3)
+        if variant >= 18:
+            return f"{pre}smooth_march2<float,PFC,{tx}> ({ly} rows per block, two sweeps per launch)"
         return f"{pre}smooth_march<float,PFC,{tx}> ({ly} rows per block)"
     tile = ["32x16", "64x8", "32x32"][variant >> 2]
     return (f"{pre}smooth_rb2d<float,PFC,{tile}> (f staged: {bool(variant & 2)}, "
@@ -301,10 +309,12 @@ def run_ours(args):
     value = job_throughput(world, steps, mix["total_ms"])
     ms_per_step = mix["total_ms"] / steps
     peak, peak_kind = load_peaks()
-    # smoother roofline: one launch of the fused 2-D kernel is one red-black
-    # sweep of the finest level: algorithmic bytes = 20 words/point x N points
+    # smoother roofline: one launch of the fused 2-D kernel runs one (or, for
+    # the two-sweep variants, two) red-black sweeps of the finest level and
+    # moves the same algorithmic bytes either way: 20 words/point x N points
     # (float32): read e (5), f (5), rho^k, omega^k, rho, u, v (5); write e (5)
     sm_ms, sm_n = mix["prof"]
+    spl = sweeps_per_launch(tuning["mixed"][0][0])
     words = 20
     bytes_launch = words * 4 * N
     avg_ms = sm_ms / max(1, sm_n)
@@ -339,6 +349,7 @@ def run_ours(args):
                 "ms_per_step": round(f64["total_ms"] / steps, 5),
                 "cycles_per_step_mean": round(statistics.mean(f64["cycles"]), 3),
                 "smoother_launch_ms": round(f64_avg, 6),
+                "smoother_sweeps_per_launch": sweeps_per_launch(tuning["fp64"][0][0]),
                 "smoother_gbs": round(words * 8 * N / (f64_avg * 1e-3) / 1e9, 1) if f64_sm_n else None,
             },
             "speedup_mixed_over_fp64": round(f64["total_ms"] / mix["total_ms"], 3),
@@ -346,7 +357,8 @@ def run_ours(args):
                                    for l, v in enumerate(vals)] for k, vals in tuning.items()},
         },
         "roofline": {
-            "kernel": sweep_kernel(tuning["mixed"][0][0], False) + ", finest level, one red-black sweep",
+            "kernel": sweep_kernel(tuning["mixed"][0][0], False) + ", finest level",
+            "sweeps_per_launch": spl,
             "bound": "hbm",
             "achieved": round(achieved, 1) if achieved else None,
             "peak": peak,
@@ -356,7 +368,7 @@ def run_ours(args):
             "traffic": traffic,
             "algorithmic_bytes_per_launch": bytes_launch,
             "launch_ms": round(avg_ms, 6),
-            "dof_sweeps_per_s": round(5 * N / (avg_ms * 1e-3), 1) if sm_n else None,  # 5 unknowns per point
+            "dof_sweeps_per_s": round(5 * N * spl / (avg_ms * 1e-3), 1) if sm_n else None,  # 5 unknowns/point
             "launches_timed": sm_n,
             "launch_timing": "CUDA events around each finest-level smoother launch, in a pass of "
                              "the same steps run launch by launch (the timed steps run as graphs)",
@@ -434,7 +446,9 @@ def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2):
         "smoother_roofline": {"kernel": sweep_kernel(tune0[0], True) + ", finest level of all instances",
                               "bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                               "frac": round(gbs / peak, 4), "launch_ms": round(ms_sm, 5),
-                              "dof_sweeps_per_s": round(5 * pts / (ms_sm * 1e-3), 1),
+                              "sweeps_per_launch": sweeps_per_launch(tune0[0]),
+                              "dof_sweeps_per_s": round(5 * pts * sweeps_per_launch(tune0[0]) / (ms_sm * 1e-3),
+                                                        1),
                               "algorithmic_bytes_per_launch": words * 4 * pts,
                               "timing": "20 back-to-back launches after a warm-up, CUDA events",
                               "traffic": profiled_traffic("kb_smooth_batch48", tune0[0]),

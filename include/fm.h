@@ -196,10 +196,11 @@ int fm_levels(const fm_state* st);
  * fm_step as coefficient.  e (in/out) and f are nu float64 arrays each
  * (nu = 1 + dim, +2 for PFC; host or device per `where`), rounded to the
  * state's precision on entry.  variant: FM_SWEEP_AUTO runs the sweeps exactly
- * as fm_step does (2-D: the autotuned fused tile sweep, in pairs, an odd last
- * sweep as two colour launches); FM_SWEEP_TWO_COLOUR runs every sweep as a
- * red launch and a black launch; 0 .. 11 fixes the fused variant (2-D only,
- * encoding as fm_tuning).  FM_EINVAL before the first fm_prepare, for
+ * as fm_step does (2-D: the autotuned fused sweep over the largest even
+ * number of sweeps, an odd last sweep as two colour launches);
+ * FM_SWEEP_TWO_COLOUR runs every sweep as a red launch and a black launch;
+ * 0 .. FM_SWEEP_VARIANTS - 1 fixes the fused variant (2-D only, encoding as
+ * fm_tuning).  FM_EINVAL before the first fm_prepare, for
  * sweeps < 0, an unknown variant, a fused variant in 3-D or one that does not
  * fit in shared memory. */
 #define FM_SWEEP_AUTO (-1)
@@ -245,16 +246,18 @@ long long fm_batch_launches(const fm_batch* b);
 int fm_batch_tuning(const fm_batch* b, int level, int* variant, float* ms_per_variant);
 
 /* Measurement (no counterpart in the paper): mean duration (ms, CUDA events)
- * of one launch of the finest-level fused red-black sweep over all instances,
- * timed over `iters` back-to-back launches after one warm-up launch, and the
- * number of finest-level points one launch sweeps.  Overwrites only solver
- * scratch (the corrections), which the next fm_step_batch resets. */
+ * of one launch of the fused red-black sweep variant the autotuner chose for
+ * the finest level, over all instances (one sweep, or two for the two-sweep
+ * variants 18..23; see fm_batch_tuning), timed over `iters` back-to-back
+ * launches after one warm-up launch, and the number of finest-level points
+ * one launch covers.  Overwrites only solver scratch (the corrections), which
+ * the next fm_step_batch resets. */
 int fm_batch_time_smoother(fm_batch* b, int iters, double* ms_per_launch, long long* points);
 
 /* ---- Measurement (no counterpart in the paper). ---- */
 
 /* Number of variants of the 2-D fused red-black sweep. */
-#define FM_SWEEP_VARIANTS 18
+#define FM_SWEEP_VARIANTS 24
 
 /* Variant of the 2-D fused red-black sweep the autotuner chose for `level`
  * at fm_create, and its timings of all FM_SWEEP_VARIANTS variants in ms per
@@ -263,7 +266,9 @@ int fm_batch_time_smoother(fm_batch* b, int iters, double* ms_per_launch, long l
  * form (v >> 2: tile 32x16, 64x8 or 32x32; bit 1: right-hand side staged in
  * shared memory; bit 0: persistent double-buffered blocks); 12..17 the
  * row-marching form (strip width 64 for 12..14, 128 for 15..17; 16, 32 or 64
- * rows per block).  Setting the environment variable FM_RB_VARIANT=v before
+ * rows per block); 18..23 the row-marching form that runs two sweeps in one
+ * pass (strips and rows as 12..17; its time per launch is halved to give the
+ * time per sweep).  Setting the environment variable FM_RB_VARIANT=v before
  * fm_create fixes the variant (no timing). */
 int fm_tuning(const fm_state* st, int level, int* variant, float* ms_per_variant);
 

@@ -160,6 +160,37 @@ __global__ void __launch_bounds__(march_threads(TX), march_minb<T>(TX)) kb_smoot
   march_sweep<T, KIND, TX>(Gs, P[inst], reinterpret_cast<T*>(smraw), strip * TX, y0, min(y0 + ly, Gs.g.ny), dir);
 }
 
+// Two sweeps per pass in the row-marching form (see k_smooth_march2) over the
+// strips of level `level` of all instances (work item aux = strips per row).
+template <typename T, int KIND, int TX>
+__global__ void __launch_bounds__(march_threads(TX), march2_minb<T>(TX)) kb_smooth_march2(const WorkItem* items, int nitems,
+                                                                      const InstDev<T>* D, const Phys<T>* P,
+                                                                      const Ctl* ctl, int level, int ly, int dir) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ Lvl<T> Gs;
+  FM_BATCH_HEAD();
+  if (!inst_active(ctl, inst)) return;
+  smem_copy(&Gs, &D[inst].lv[level]);
+  __syncthreads();
+  const int nstrips = items[k_].aux;
+  const int strip = lb % nstrips, seg = lb / nstrips;
+  const int y0 = seg * ly;
+  march2_sweep<T, KIND, TX>(Gs, P[inst], reinterpret_cast<T*>(smraw), strip * TX, y0, min(y0 + ly, Gs.g.ny), dir);
+}
+
+// Exchange the correction and residual buffers of a level held in shared
+// memory (block-uniform `swap`; the correction is in r).
+template <typename T>
+__device__ __forceinline__ void lvl_swap_er(Lvl<T>& L, int swap) {
+  if (!swap) return;
+  if (threadIdx.x < MAXU) {
+    T* t = L.e[threadIdx.x];
+    L.e[threadIdx.x] = L.r[threadIdx.x];
+    L.r[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
 // e = r at every point of level `level` (after an odd number of fused sweeps).
 template <typename T, int NU>
 __global__ void __launch_bounds__(TPB) kb_copy_back(const WorkItem* items, int nitems, const InstDev<T>* D,
@@ -174,10 +205,11 @@ __global__ void __launch_bounds__(TPB) kb_copy_back(const WorkItem* items, int n
 }
 
 // Fine residual and restriction of level `level` in one launch (see
-// k_resid_restrict2); work item aux = coarse tiles per row.
+// k_resid_restrict2); work item aux = coarse tiles per row.  fswap: the fine
+// correction is in the level's r buffer.
 template <typename T, int KIND>
 __global__ void __launch_bounds__(TPB) kb_resid_restrict2(const WorkItem* items, int nitems, const InstDev<T>* D,
-                                                          const Phys<T>* P, const Ctl* ctl, int level) {
+                                                          const Phys<T>* P, const Ctl* ctl, int level, int fswap) {
   FM_BATCH_HEAD();
   if (!inst_active(ctl, inst)) return;
   __shared__ Lvl<T> F, Cc;
@@ -185,19 +217,21 @@ __global__ void __launch_bounds__(TPB) kb_resid_restrict2(const WorkItem* items,
   smem_copy(&F, &D[inst].lv[level]);
   smem_copy(&Cc, &D[inst].lv[level + 1]);
   __syncthreads();
+  lvl_swap_er(F, fswap);
   const int ntx = items[k_].aux;
   resid_restrict2_tile<T, KIND>(F, Cc, P[inst], (lb % ntx) * RR_TX, (lb / ntx) * RR_TY, sr);
 }
 
 template <typename T, int NU>
 __global__ void __launch_bounds__(TPB) kb_prolong(const WorkItem* items, int nitems, const InstDev<T>* D,
-                                                  const Ctl* ctl, int level) {
+                                                  const Ctl* ctl, int level, int fswap) {
   FM_BATCH_HEAD();
   if (!inst_active(ctl, inst)) return;
   __shared__ Lvl<T> F, Cc;
   smem_copy(&F, &D[inst].lv[level]);
   smem_copy(&Cc, &D[inst].lv[level + 1]);
   __syncthreads();
+  lvl_swap_er(F, fswap);
   const int idx = lb * TPB + threadIdx.x;
   if (idx < F.g.N) prolong_point<T, NU, 2>(F, Cc, idx);
 }
@@ -338,7 +372,7 @@ struct fm_batch {
   WList w_smooth[3 + 6][MAXLEV];  // per tile shape (32x16, 64x8, 32x32), then per marching variant
   WList w_resid[MAXLEV], w_rr[MAXLEV], w_prolong[MAXLEV];
   int rbv[MAXLEV];           // chosen fused-sweep variant per level
-  float rbt[MAXLEV][RB_NVAR];  // autotuner timings (ms per launch)
+  float rbt[MAXLEV][RB_NVAR];  // autotuner timings (ms per sweep)
   // graph
   cudaStream_t stream;
   cudaStream_t user_stream;
@@ -550,6 +584,24 @@ struct Batch {
     return FM_OK;
   }
 
+  // Two-sweep marching form, variant v (strip width TX) over all instances.
+  template <int TX>
+  static int launch_m2(fm_batch* b, int l, int dir, int v) {
+    constexpr size_t smem = march2_smem_bytes<T, KIND, TX>();
+    if (smem + 4096 > (size_t)b->inst[0]->smem_optin) return FM_EINVAL;  // does not fit: skip
+    static bool attr = false;
+    if (!attr) {
+      FMB_CUDA(cudaFuncSetAttribute(kb_smooth_march2<T, KIND, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      attr = true;
+    }
+    const WList& w = b->w_smooth[3 + (v - RB_NTILE) % RB_NMARCH][l];
+    kb_smooth_march2<T, KIND, TX><<<w.nblocks, march_threads(TX), smem, b->stream>>>(
+        it(b, w), w.n, (const InstDev<T>*)b->D, (const Phys<T>*)b->P, b->ctl, l, march_ly(v), dir);
+    FMB_LAUNCHED();
+    return FM_OK;
+  }
+
   static int launch_variant(fm_batch* b, int v, int l, int dir = 0) {
     switch (v) {
       case 0: return launch_v<32, 16, false, false>(b, l, dir);
@@ -569,23 +621,37 @@ struct Batch {
       case 14: return launch_m<64>(b, l, dir, 14);
       case 15: return launch_m<128>(b, l, dir, 15);
       case 16: return launch_m<128>(b, l, dir, 16);
-      default: return launch_m<128>(b, l, dir, 17);
+      case 17: return launch_m<128>(b, l, dir, 17);
+      case 18: return launch_m2<64>(b, l, dir, 18);
+      case 19: return launch_m2<64>(b, l, dir, 19);
+      case 20: return launch_m2<64>(b, l, dir, 20);
+      case 21: return launch_m2<128>(b, l, dir, 21);
+      case 22: return launch_m2<128>(b, l, dir, 22);
+      default: return launch_m2<128>(b, l, dir, 23);
     }
   }
 
-  // Sweeps alternate e -> r and r -> e; after an odd count the correction is
-  // copied back from r.
-  static int smooth(fm_batch* b, int l, int iters) {
+  // `iters` sweeps of level l.  Each launch reads the correction from one
+  // buffer and writes it to the other; *in_r says (and is updated to) whether
+  // it is in r.  A two-sweep variant runs the sweeps in pairs and an odd last
+  // sweep with the one-sweep variant of the same strips.
+  static int smooth(fm_batch* b, int l, int iters, int* in_r) {
     if (b->w_smooth[0][l].n == 0) return FM_OK;
-    for (int k = 0; k < iters; ++k) {
-      const int rc = launch_variant(b, b->rbv[l], l, k & 1);
+    const int v = b->rbv[l];
+    for (int k = 0; k < iters;) {
+      const int two = sweeps_per_launch(v) == 2 && k + 2 <= iters;
+      const int rc = launch_variant(b, (sweeps_per_launch(v) == 2 && !two) ? v - RB_NMARCH : v, l, *in_r);
       if (rc) return rc;
+      *in_r ^= 1;
+      k += two ? 2 : 1;
     }
-    if (iters & 1) {
-      const WList& w = b->w_resid[l];
-      kb_copy_back<T, LY::NU><<<w.nblocks, TPB, 0, b->stream>>>(it(b, w), w.n, (const InstDev<T>*)b->D, b->ctl, l);
-      FMB_LAUNCHED();
-    }
+    return FM_OK;
+  }
+
+  static int copy_back(fm_batch* b, int l) {
+    const WList& w = b->w_resid[l];
+    kb_copy_back<T, LY::NU><<<w.nblocks, TPB, 0, b->stream>>>(it(b, w), w.n, (const InstDev<T>*)b->D, b->ctl, l);
+    FMB_LAUNCHED();
     return FM_OK;
   }
 
@@ -624,6 +690,7 @@ struct Batch {
           rc = FM_ECUDA;
           break;
         }
+        ms /= sweeps_per_launch(v);  // compared per sweep
         b->rbt[l][v] = ms / TUNE_REPS;
         if (ms < best * 0.98f) {  // a later variant must be clearly faster
           best = ms;
@@ -641,12 +708,15 @@ struct Batch {
     const InstDev<T>* D = (const InstDev<T>*)b->D;
     const Phys<T>* P = (const Phys<T>*)b->P;
     cudaStream_t s = b->stream;
+    // in_r[l]: the correction of level l is in its r buffer (between the pre-
+    // and the post-smoothing after an odd number of fused launches)
+    int in_r[MAXLEV] = {0};
     for (int l = 0; l < b->maxdepth; ++l) {
-      int rc = smooth(b, l, b->prm.nu1);
+      int rc = smooth(b, l, b->prm.nu1, &in_r[l]);
       if (rc) return rc;
       const WList& wq = b->w_rr[l];
       if (wq.n == 0) continue;
-      kb_resid_restrict2<T, KIND><<<wq.nblocks, TPB, 0, s>>>(it(b, wq), wq.n, D, P, b->ctl, l);
+      kb_resid_restrict2<T, KIND><<<wq.nblocks, TPB, 0, s>>>(it(b, wq), wq.n, D, P, b->ctl, l, in_r[l]);
       FMB_LAUNCHED();
     }
     if (b->small_global)
@@ -658,10 +728,14 @@ struct Batch {
     for (int l = b->maxdepth - 1; l >= 0; --l) {
       const WList& wp = b->w_prolong[l];
       if (wp.n == 0) continue;
-      kb_prolong<T, LY::NU><<<wp.nblocks, TPB, 0, s>>>(it(b, wp), wp.n, D, b->ctl, l);
+      kb_prolong<T, LY::NU><<<wp.nblocks, TPB, 0, s>>>(it(b, wp), wp.n, D, b->ctl, l, in_r[l]);
       FMB_LAUNCHED();
-      int rc = smooth(b, l, b->prm.nu2);
+      int rc = smooth(b, l, b->prm.nu2, &in_r[l]);
       if (rc) return rc;
+      if (in_r[l]) {
+        rc = copy_back(b, l);
+        if (rc) return rc;
+      }
     }
     return FM_OK;
   }
@@ -839,9 +913,9 @@ struct Batch {
     cudaEvent_t e0, e1;
     FMB_CUDA(cudaEventCreate(&e0));
     FMB_CUDA(cudaEventCreate(&e1));
-    int rc = smooth(b, 0, 1);  // warm-up
+    int rc = launch_variant(b, b->rbv[0], 0);  // warm-up
     if (rc == FM_OK && cudaEventRecord(e0, b->stream) != cudaSuccess) rc = FM_ECUDA;
-    if (rc == FM_OK) rc = smooth(b, 0, iters);
+    for (int k = 0; k < iters && rc == FM_OK; ++k) rc = launch_variant(b, b->rbv[0], 0);
     if (rc == FM_OK && cudaEventRecord(e1, b->stream) != cudaSuccess) rc = FM_ECUDA;
     if (rc == FM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = FM_ECUDA;
     float t = 0.f;

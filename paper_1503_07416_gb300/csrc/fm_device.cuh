@@ -729,7 +729,7 @@ struct MarchAcc {
 
 // Start the copies of rows row0 and row0 + 1 (local rows lrow0, lrow0 + 1,
 // counted from y0 - 2) into their ring slots.
-template <typename T, int KIND, int TX>
+template <typename T, int KIND, int TX, int NR = MR>
 __device__ __forceinline__ void march_issue2(const Lvl<T>& G, T* buf, int x0, int row0, int lrow0, int dir) {
   constexpr int NU = Layout<KIND, 2>::NU;
   constexpr int NA = march_arrays<KIND>();
@@ -748,7 +748,7 @@ __device__ __forceinline__ void march_issue2(const Lvl<T>& G, T* buf, int x0, in
     for (int t = threadIdx.x; t < 2 * CPR; t += blockDim.x) {
       const int k = t >= CPR, c = t - k * CPR;
       const int gi = wrapi(row0 + k, ny) * nx + wrapi(x0 - RB_XO + c * V, nx);
-      T* d = buf + ((lrow0 + k) % MR) * NA * SW + c * V;
+      T* d = buf + ((lrow0 + k) % NR) * NA * SW + c * V;
 #pragma unroll
       for (int a = 0; a < NA; ++a) cp_async_16(d + a * SW, src[a] + gi);
     }
@@ -756,7 +756,7 @@ __device__ __forceinline__ void march_issue2(const Lvl<T>& G, T* buf, int x0, in
     for (int t = threadIdx.x; t < 2 * SW; t += blockDim.x) {
       const int k = t >= SW, c = t - k * SW;
       const int gi = wrapi(row0 + k, ny) * nx + wrapi(x0 - RB_XO + c, nx);
-      T* d = buf + ((lrow0 + k) % MR) * NA * SW + c;
+      T* d = buf + ((lrow0 + k) % NR) * NA * SW + c;
 #pragma unroll
       for (int a = 0; a < NA; ++a) cp_async_elem(d + a * SW, src[a] + gi);
     }
@@ -849,14 +849,158 @@ __global__ void __launch_bounds__(march_threads(TX), march_minb<T>(TX)) k_smooth
   march_sweep<T, KIND, TX>(G, P, reinterpret_cast<T*>(smraw), strip * TX, y0, min(y0 + ly, G.g.ny), dir);
 }
 
+// --------------------------------------------------------------------------
+// 2-D fused red-black sweep, two sweeps per pass (row-marching form)
+// --------------------------------------------------------------------------
+// The marching form above with a second sweep following the first, four
+// rows behind it, in the same pass.  Step s (ya = y0 - 4 + 2 s):
+//   phase 1: red of sweep 1 on rows ya + 1, ya + 2 (one point per column)
+//            and red of sweep 2 on rows ya - 3, ya - 2;
+//   phase 2: black of sweep 1 on rows ya, ya + 1 and black of sweep 2 on
+//            rows ya - 4, ya - 3, which are then final and written out.
+// Sweep-2 red on row r reads sweep-1 values of rows r - 1 .. r + 1, all
+// final after phase 2 of step s - 1; sweep-2 black reads sweep-2 red values
+// of phase 1.  A point keeps one value in the ring (before the sweeps, after
+// sweep 1, after sweep 2), and every read of an older value comes before the
+// phase that overwrites it, so one barrier after each phase suffices.
+//
+// Because sweep 2 at the block's edge rows and columns needs sweep-1 values
+// one point further out, the block computes sweep-1 red on rows y0 - 3 ..
+// y1 + 2 and columns x0 - 3 .. x0 + TX + 2, sweep-1 black one row and column
+// less, sweep-2 red one less again and sweep-2 black on its own points only
+// (the lanes 0..5 of the extra warp take the six outer columns); the staged
+// rows are y0 - 4 .. y1 + 3.  As in the one-sweep forms the correction is
+// read from one buffer and written to the other, so the result is exactly two
+// red-black sweeps.  The data are read once and written once for both sweeps.
+constexpr int MR2 = 14;  // row slots: rows ya - 5 .. ya + 7 are live in step s (one slot spare)
+
+template <typename T, int KIND, int TX>
+__host__ __device__ constexpr size_t march2_smem_bytes() {
+  return (size_t)MR2 * march_arrays<KIND>() * (TX + 2 * RB_XO) * sizeof(T);
+}
+template <typename T>
+__host__ __device__ constexpr int march2_minb(int tx) { return (sizeof(T) == 4 && tx == 128) ? 4 : 1; }
+
+template <typename T, int KIND, int TX>
+__device__ __forceinline__ void march2_sweep(const Lvl<T>& G, const Phys<T>& P, T* buf, int x0, int y0, int y1,
+                                             int dir) {
+  static_assert(RB_XO >= 4, "the two-sweep pass stages four halo columns");
+  constexpr int NU = Layout<KIND, 2>::NU;
+  constexpr int NA = march_arrays<KIND>();
+  constexpr int SW = TX + 2 * RB_XO;
+  constexpr int RS = NA * SW;
+  const int nx = G.g.nx, ny = G.g.ny;
+  const int txe = min(TX, nx - x0);
+  const PtK<T> K = make_ptk<T, 2>(P, G.h);
+  // this thread's staged column and its distance from the block's columns
+  // (0 inside; lanes 0..5 of the extra warp: x0 - 3 .. x0 - 1 at distance
+  // 3, 2, 1 and x0 + txe .. x0 + txe + 2 at distance 1, 2, 3)
+  const int tid = threadIdx.x;
+  int lx = -1, dist = 4;
+  if (tid < txe) {
+    lx = RB_XO + tid;
+    dist = 0;
+  } else if (tid >= TX && tid < TX + 3) {
+    lx = RB_XO - 3 + (tid - TX);
+    dist = 3 - (tid - TX);
+  } else if (tid >= TX + 3 && tid < TX + 6) {
+    lx = RB_XO + txe + (tid - TX - 3);
+    dist = 1 + (tid - TX - 3);
+  }
+  const int gx = x0 - RB_XO + lx;  // unwrapped column: its parity is the colour's
+  const int gxw = wrapi(gx, nx);
+  T* const* dst = dir ? G.e : G.r;
+  const int ylo = y0 - 4;  // first staged row
+  const int nsteps = (y1 - y0 + 7) / 2 + 1;
+  auto slot = [&](int row) { return ((row - ylo) % MR2) * RS; };
+  auto red_row = [&](int ya) { return ((gx + ya + 1) & 1) == 0 ? ya + 1 : ya + 2; };
+  auto black_row = [&](int ya) { return ((gx + ya) & 1) ? ya : ya + 1; };
+  // rows and columns each half-sweep covers
+  auto red1 = [&](int row) { return dist <= 3 && row >= y0 - 3 && row <= y1 + 2; };
+  auto black1 = [&](int row) { return dist <= 2 && row >= y0 - 2 && row <= y1 + 1; };
+  auto red2 = [&](int row) { return dist <= 1 && row >= y0 - 1 && row <= y1; };
+  auto black2 = [&](int row) { return dist == 0 && row >= y0 && row < y1; };
+  auto update = [&](int row, const MarchPt<T, KIND>& pt) {
+    const MarchAcc<T, KIND, SW> acc{buf, pt};
+    Nb n;
+    n.c = slot(row) + lx;
+    n.m[0] = n.c - 1;
+    n.p[0] = n.c + 1;
+    n.m[1] = slot(row - 1) + lx;
+    n.p[1] = slot(row + 1) + lx;
+    n.m[2] = n.p[2] = n.c;
+    smooth_point_a<T, KIND, 2>(acc, P, K, n, 0);
+  };
+
+  // rows y0 - 4 .. y0 + 1 (steps 0 and 1)
+  for (int k = 0; k < 3; ++k) march_issue2<T, KIND, TX, MR2>(G, buf, x0, ylo + 2 * k, 2 * k, dir);
+  cp_async_commit();
+  // point values of the red and black point of this column in steps s, s - 1,
+  // s - 2 (sweep 2 at step s updates the points sweep 1 updated at s - 2)
+  MarchPt<T, KIND> r0{}, r1{}, r2{}, b0{}, b1{}, b2{}, rn{}, bn{};
+  if (red1(red_row(ylo))) march_load_pt<T, KIND>(G, wrapi(red_row(ylo), ny) * nx + gxw, r0);
+  if (black1(black_row(ylo))) march_load_pt<T, KIND>(G, wrapi(black_row(ylo), ny) * nx + gxw, b0);
+  cp_async_wait_all();
+  __syncthreads();
+#pragma unroll 1
+  for (int s = 0; s < nsteps; ++s) {
+    const int ya = ylo + 2 * s;
+    const int rr = red_row(ya), br = black_row(ya);
+    if (red1(rr)) update(rr, r0);
+    if (red2(rr - 4)) update(rr - 4, r2);
+    cp_async_wait_all();
+    __syncthreads();
+    if (ya + 6 <= y1 + 3) march_issue2<T, KIND, TX, MR2>(G, buf, x0, ya + 6, 2 * s + 6, dir);  // step s + 2
+    cp_async_commit();
+    if (s + 1 < nsteps) {
+      const int rrn = red_row(ya + 2), brn = black_row(ya + 2);
+      if (red1(rrn)) march_load_pt<T, KIND>(G, wrapi(rrn, ny) * nx + gxw, rn);
+      if (black1(brn)) march_load_pt<T, KIND>(G, wrapi(brn, ny) * nx + gxw, bn);
+    }
+    if (black1(br)) update(br, b0);
+    if (black2(br - 4)) update(br - 4, b2);
+    if (dist == 0) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int row = ya - 4 + k;
+        if (row >= y0 && row < y1) {
+          const int si = slot(row) + lx;
+#pragma unroll
+          for (int q = 0; q < NU; ++q) dst[q][row * nx + gxw] = buf[si + q * SW];
+        }
+      }
+    }
+    __syncthreads();
+    r2 = r1;
+    r1 = r0;
+    r0 = rn;
+    b2 = b1;
+    b1 = b0;
+    b0 = bn;
+  }
+}
+
+template <typename T, int KIND, int TX>
+__global__ void __launch_bounds__(march_threads(TX), march2_minb<T>(TX)) k_smooth_march2(Lvl<T> G, Phys<T> P,
+                                                                     int nstrips, int ly, int dir) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int strip = blockIdx.x % nstrips, seg = blockIdx.x / nstrips;
+  const int y0 = seg * ly;
+  march2_sweep<T, KIND, TX>(G, P, reinterpret_cast<T*>(smraw), strip * TX, y0, min(y0 + ly, G.g.ny), dir);
+}
+
 // Variants of the 2-D fused sweep, chosen per level by the autotuner:
 // 0..11 tile form (bits 0-1: PIPE, SF; v >> 2: tile 32x16, 64x8, 32x32),
-// 12..17 marching form (strip width 64 or 128; rows per block 16, 32, 64).
+// 12..17 marching form (strip width 64 or 128; rows per block 16, 32, 64),
+// 18..23 the two-sweep marching form with the same strips and rows.
 constexpr int RB_NVAR = FM_SWEEP_VARIANTS;
 constexpr int TUNE_REPS = 10;  // timed launches per variant and level in the autotuners
 constexpr int RB_NTILE = 12;
-__host__ __device__ constexpr int march_tx(int v) { return v < 15 ? 64 : 128; }
+constexpr int RB_NMARCH = 6;
+constexpr int RB_TWO = RB_NTILE + RB_NMARCH;  // first two-sweep variant
+__host__ __device__ constexpr int march_tx(int v) { return (v - RB_NTILE) % RB_NMARCH < 3 ? 64 : 128; }
 __host__ __device__ constexpr int march_ly(int v) { return 16 << ((v - RB_NTILE) % 3); }
+__host__ __device__ constexpr int sweeps_per_launch(int v) { return v >= RB_TWO ? 2 : 1; }
 
 // The whole V-cycle of the small levels (each at most SMALL_N points) in one
 // thread block: phases separated by __syncthreads, data in L1/L2.

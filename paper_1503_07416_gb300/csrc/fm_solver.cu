@@ -172,6 +172,27 @@ static int launch_march(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStr
   return FM_OK;
 }
 
+// Launch the two-sweep marching form (strip width TX, ly rows per block).
+template <typename T, int KIND, int TX>
+static int launch_march2(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int dir, int ly) {
+  constexpr size_t smem = march2_smem_bytes<T, KIND, TX>();
+  if (smem + 4096 > (size_t)st->smem_optin) return FM_EINVAL;
+  if (!L.r[0]) return FM_EINVAL;
+  static bool attr = false;
+  if (!attr) {
+    FM_CUDA(cudaFuncSetAttribute(k_smooth_march2<T, KIND, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    attr = true;
+  }
+  const int nstrips = (L.g.nx + TX - 1) / TX;
+  const int nseg = (L.g.ny + ly - 1) / ly;
+  k_smooth_march2<T, KIND, TX><<<nstrips * nseg, march_threads(TX), smem, s>>>(L, P, nstrips, ly, dir);
+  return FM_OK;
+}
+
+// One launch of fused-sweep variant v on level L: sweeps_per_launch(v)
+// sweeps, the correction read from L.e and written to L.r (dir = 0) or the
+// reverse (dir = 1).
 template <typename T, int KIND>
 static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int dir = 0) {
   switch (v) {
@@ -192,8 +213,38 @@ static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cud
     case 14: return launch_march<T, KIND, 64>(st, L, P, s, dir, 64);
     case 15: return launch_march<T, KIND, 128>(st, L, P, s, dir, 16);
     case 16: return launch_march<T, KIND, 128>(st, L, P, s, dir, 32);
-    default: return launch_march<T, KIND, 128>(st, L, P, s, dir, 64);
+    case 17: return launch_march<T, KIND, 128>(st, L, P, s, dir, 64);
+    case 18: return launch_march2<T, KIND, 64>(st, L, P, s, dir, 16);
+    case 19: return launch_march2<T, KIND, 64>(st, L, P, s, dir, 32);
+    case 20: return launch_march2<T, KIND, 64>(st, L, P, s, dir, 64);
+    case 21: return launch_march2<T, KIND, 128>(st, L, P, s, dir, 16);
+    case 22: return launch_march2<T, KIND, 128>(st, L, P, s, dir, 32);
+    default: return launch_march2<T, KIND, 128>(st, L, P, s, dir, 64);
   }
+}
+
+// e = r on every point of a level (the correction back in e).
+template <typename T, int NU>
+__global__ void __launch_bounds__(TPB) k_copy_back(Lvl<T> L) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L.g.N) return;
+  T v[NU];
+#pragma unroll
+  for (int q = 0; q < NU; ++q) v[q] = L.r[q][idx];
+#pragma unroll
+  for (int q = 0; q < NU; ++q) L.e[q][idx] = v[q];
+}
+
+// View of a level with the roles of the correction and residual buffers
+// exchanged (the correction in r).
+template <typename T>
+static Lvl<T> swap_er(Lvl<T> L) {
+  for (int q = 0; q < MAXU; ++q) {
+    T* t = L.e[q];
+    L.e[q] = L.r[q];
+    L.r[q] = t;
+  }
+  return L;
 }
 
 // Sum the durations of the recorded (start, end) event pairs; call only after
@@ -261,8 +312,9 @@ struct Solver {
 
   // Choose, per multi-kernel level, the fastest variant of the fused 2-D
   // sweep: each variant is timed with CUDA events (one warm-up and TUNE_REPS
-  // timed launches) on the level itself; a later variant replaces the choice
-  // only if it is 2% faster.  The sweeps only touch solver scratch.
+  // timed launches) on the level itself and compared per sweep; a later
+  // variant replaces the choice only if it is 2% faster.  The sweeps only
+  // touch solver scratch.
   static int autotune(fm_state* st) {
     if constexpr (DIM != 2) {
       return FM_OK;
@@ -299,6 +351,7 @@ struct Solver {
           }
           float ms = 0.f;
           if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = FM_ECUDA; break; }
+          ms /= sweeps_per_launch(v);  // compared per sweep
           st->rbt[l][v] = ms / TUNE_REPS;
           if (ms < best * 0.98f) {  // a later variant must be clearly faster
             best = ms;
@@ -436,25 +489,15 @@ struct Solver {
       FM_LAUNCHED();
     }
     const Phys<T> P = make_phys<T>(st);
-    const int v = variant >= 0 ? variant : st->rbv[0];
-    const int nfused = (DIM == 2 && variant != FM_SWEEP_TWO_COLOUR && (st->fused_rb || variant >= 0))
-                           ? (sweeps & ~1) : 0;
-    for (int it = 0; it < sweeps; ++it) {
-      if (it < nfused) {
-        if constexpr (DIM == 2) {
-          rc = launch_rb<T, KIND>(st, v, L, P, s, it & 1);
-          if (rc) return rc;
-        }
-        FM_LAUNCHED();
-      } else {
-        for (int color = 0; color < 2; ++color) {
-          k_smooth<T, KIND, DIM><<<nblocks(G.N / 2), TPB, 0, s>>>(L, P, color);
-          FM_LAUNCHED();
-        }
-      }
-    }
+    const int v = (DIM == 2 && variant != FM_SWEEP_TWO_COLOUR && (st->fused_rb || variant >= 0))
+                      ? (variant >= 0 ? variant : st->rbv[0])
+                      : -1;
+    int in_r = 0;
+    rc = run_sweeps(st, L, v, P, sweeps, &in_r, false);
+    if (rc) return rc;
+    const Lvl<T> E = in_r ? swap_er(L) : L;
     for (int q = 0; q < LY::NU; ++q) {
-      k_convert<T, double><<<nblocks(G.N), TPB, 0, s>>>(L.e[q], st->r64[q], G.N);
+      k_convert<T, double><<<nblocks(G.N), TPB, 0, s>>>(E.e[q], st->r64[q], G.N);
       FM_LAUNCHED();
       FM_CUDA(cudaMemcpyAsync(e[q], st->r64[q], bytes, kind_out(where), s));
     }
@@ -462,27 +505,29 @@ struct Solver {
     return FM_OK;
   }
 
-  static int smooth(fm_state* st, int l, const Phys<T>& P, int iters) {
+  // `iters` sweeps on level L (its physical buffers; the correction is in
+  // L.r if *in_r, else in L.e; *in_r is updated).  v >= 0: fused variant v,
+  // each launch reading the correction from one buffer and writing it to the
+  // other, over the largest even number of sweeps; the rest (and all sweeps
+  // for v < 0) in place as a red and a black launch.  prof: CUDA events
+  // around each launch.
+  static int run_sweeps(fm_state* st, const Lvl<T>& L, int v, const Phys<T>& P, int iters, int* in_r, bool prof) {
     cudaStream_t s = st->stream;
-    Lvl<T> L = make_lvl<T>(st, l);
     const int half = L.g.N / 2;
-    const bool prof = st->prof && !st->capturing && l == 0;
-    // Fused sweeps run in pairs (e -> r, then r -> e), so the correction is
-    // back in e after each pair; an odd last sweep runs in place as two
-    // colour launches.
-    const int nfused = (DIM == 2 && st->fused_rb) ? (iters & ~1) : 0;
-    for (int it = 0; it < iters; ++it) {
+    const int nfused = (DIM == 2 && v >= 0) ? (iters & ~1) : 0;
+    const int per = v >= 0 ? sweeps_per_launch(v) : 1;
+    for (int it = 0; it < iters;) {
       const bool fused = it < nfused;
       const int nlaunch = fused ? 1 : 2;
       for (int color = 0; color < nlaunch; ++color) {
         if (prof && st->npev + 2 <= MAXEV) FM_CUDA(cudaEventRecord(st->pev[st->npev], s));
         if (fused) {
           if constexpr (DIM == 2) {
-            const int rc = launch_rb<T, KIND>(st, st->rbv[l], L, P, s, it & 1);
+            const int rc = launch_rb<T, KIND>(st, v, L, P, s, *in_r);
             if (rc) return rc;
           }
         } else {
-          k_smooth<T, KIND, DIM><<<nblocks(half), TPB, 0, s>>>(L, P, color);
+          k_smooth<T, KIND, DIM><<<nblocks(half), TPB, 0, s>>>(*in_r ? swap_er(L) : L, P, color);
         }
         FM_LAUNCHED();
         if (prof && st->npev + 2 <= MAXEV) {
@@ -490,8 +535,20 @@ struct Solver {
           st->npev += 2;
         }
       }
+      if (fused) {
+        *in_r ^= 1;
+        it += per;
+      } else {
+        it += 1;
+      }
     }
     return FM_OK;
+  }
+
+  static int smooth(fm_state* st, int l, const Phys<T>& P, int iters, int* in_r) {
+    const bool prof = st->prof && !st->capturing && l == 0;
+    const int v = (DIM == 2 && st->fused_rb) ? st->rbv[l] : -1;
+    return run_sweeps(st, make_lvl<T>(st, l), v, P, iters, in_r, prof);
   }
 
   static int vcycle(fm_state* st, int l, const Phys<T>& P) {
@@ -517,9 +574,14 @@ struct Solver {
       FM_LAUNCHED();
       return FM_OK;
     }
-    int rc = smooth(st, l, P, st->prm.nu1);
+    // The correction of level l may sit in its r buffer between the pre- and
+    // the post-smoothing (after an odd number of fused launches); the
+    // residual, restriction and prolongation then use the exchanged view.
+    int in_r = 0;
+    int rc = smooth(st, l, P, st->prm.nu1, &in_r);
     if (rc) return rc;
     Lvl<T> F = make_lvl<T>(st, l);
+    if (in_r) F = swap_er(F);
     Lvl<T> C = make_lvl<T>(st, l + 1);
     if constexpr (DIM == 2) {
       const int ntx = (C.g.nx + RR_TX - 1) / RR_TX, nty = (C.g.ny + RR_TY - 1) / RR_TY;
@@ -535,7 +597,13 @@ struct Solver {
     if (rc) return rc;
     k_prolong<T, LY::NU, DIM><<<nblocks(F.g.N), TPB, 0, s>>>(F, C);
     FM_LAUNCHED();
-    return smooth(st, l, P, st->prm.nu2);
+    rc = smooth(st, l, P, st->prm.nu2, &in_r);
+    if (rc) return rc;
+    if (in_r) {
+      k_copy_back<T, LY::NU><<<nblocks(F.g.N), TPB, 0, s>>>(make_lvl<T>(st, l));
+      FM_LAUNCHED();
+    }
+    return FM_OK;
   }
 
   static int enqueue_body(fm_state* st, cudaGraphConditionalHandle hdl, int use_handle) {

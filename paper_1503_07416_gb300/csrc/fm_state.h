@@ -65,7 +65,7 @@ struct fm_state {
   bool use_graph;                 // run fm_step as one CUDA graph launch
   bool fused_rb;                  // 2-D: one tiled launch per red-black sweep
   int rbv[fm::MAXLEV];            // chosen variant of the fused sweep per level
-  float rbt[fm::MAXLEV][FM_SWEEP_VARIANTS];  // autotuner timings (ms per launch)
+  float rbt[fm::MAXLEV][FM_SWEEP_VARIANTS];  // autotuner timings (ms per sweep)
   int small_from;                 // first level handled by the single-block V-cycle
   void* ctl;                      // device control block of the step
   cudaGraph_t graph;

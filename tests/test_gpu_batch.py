@@ -116,6 +116,43 @@ def test_batch_failure_is_isolated():
     b.close()
 
 
+@pytest.mark.parametrize("nu", [(2, 2), (1, 3), (3, 2)])
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_batch_two_sweep_smoother(precision, nu, monkeypatch):
+    """The batch with the two-sweep marching variant 21 on every level: the
+    correction of a level may sit in its second buffer between the pre- and
+    the post-smoothing (the fused residual + restriction and the prolongation
+    take it from there) and an odd sweep count runs the one-sweep variant of
+    the same strips.  Against the oracle with the same cycle and the
+    single-instance solver with the same variant."""
+    monkeypatch.setenv("FM_RB_VARIANT", "21")
+    sizes = [32, (256, 192), 128]
+    ens = _ensemble("pfc", sizes, 12)
+    h, tol = 0.9, 1e-12
+    prm = dict(kind="pfc", dim=2, h=h, alpha=0.6, tol=tol)
+    b = fm.Batch("pfc", sizes, h, alpha=0.6, precision=precision, tol=tol, w_damp=0.0, max_cycles=80,
+                 nu1=nu[0], nu2=nu[1])
+    for i, (rho, vel, dt) in enumerate(ens):
+        b.set_fields(i, rho, vel)
+    info = b.step([dt for _, _, dt in ens])
+    bound = 1e-10 if precision == fm.FM_FP64 else 1e-8
+    for i, (rho, vel, dt) in enumerate(ens):
+        assert info[i].res <= tol
+        rg, vg = b.get_fields(i)
+        P, opts, J = oracle_setup(rho, dict(prm, dt=dt), w_damp=0.0, tol=tol)
+        opts.nu1, opts.nu2 = nu
+        ro, vo, _ = S.step(rho, vel, P, opts, J=J)
+        errs = [rel(rg, ro)] + [rel(a, c) for a, c in zip(vg, vo)]
+        assert max(errs) <= bound, (i, errs)
+        sol = gpu_solver(rho, dict(prm, dt=dt), precision=precision, w_damp=0.0, tol=tol, nu1=nu[0], nu2=nu[1])
+        sol.set_fields(rho, vel)
+        sol.step(dt)
+        rs, vs = sol.get_fields()
+        sol.close()
+        assert rel(rg, rs) <= 1e-12 and all(rel(a, c) <= 1e-12 for a, c in zip(vg, vs))
+    b.close()
+
+
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
 def test_batch_odd_sweep_counts(precision):
     """V(1,3): every smoothing stage has an odd number of fused sweeps, so the

@@ -7,6 +7,7 @@ outer residual loop) 1e-8, with both solvers converged to the same float64
 residual tolerance (1e-12 unless stated).  Both solve the same discrete
 system; the two solvers' iterates differ, the fixed point does not.
 """
+import functools
 import math
 
 import numpy as np
@@ -329,6 +330,47 @@ def test_fused_tile_smoother_matches_two_colour_launches(kind, precision, monkey
     (rb, vb), cb = res[1]
     assert ca == cb
     assert rel(ra, rb) <= 1e-12 and all(rel(a, b) <= 1e-12 for a, b in zip(va, vb))
+
+
+@pytest.mark.parametrize("nu", [(2, 2), (1, 2), (3, 3)])
+@pytest.mark.parametrize("variant", [18, 21])
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_two_sweep_smoother_in_the_cycle(precision, variant, nu, monkeypatch):
+    """V-cycles whose fused launches run two sweeps each: after an odd number
+    of launches the correction of a level sits in its second buffer, where
+    the residual, restriction and prolongation read it (V(2,2), V(3,3)) or
+    from which it is copied back (V(1,2)); 192 x 256 PFC (ragged against the
+    128-wide strips), two steps against the oracle."""
+    monkeypatch.setenv("FM_RB_VARIANT", str(variant))
+    rho, vel, prm, ref = _two_sweep_case()
+    tol = prm["tol"]
+    sol = gpu_solver(rho, prm, precision=precision, w_damp=0.0, tol=tol, nu1=nu[0], nu2=nu[1])
+    bound = TOL64 if precision == fm.FM_FP64 else TOLMIX
+    for ro, vo in ref:
+        sol.set_fields(rho, vel)
+        assert sol.step(prm["dt"]).res <= tol
+        rg, vg = sol.get_fields()
+        errs = [rel(rg, ro)] + [rel(a, b) for a, b in zip(vg, vo)]
+        assert max(errs) <= bound, errs
+        rho, vel = ro, vo
+    sol.close()
+
+
+@functools.lru_cache(maxsize=1)
+def _two_sweep_case():
+    """192 x 256 PFC state and its two oracle steps (the converged step does
+    not depend on the cycle that reached it)."""
+    rng = np.random.default_rng(71)
+    shape = (192, 256)
+    rho = 0.8 + 0.05 * rng.uniform(-1, 1, shape)
+    vel = [0.03 * rng.standard_normal(shape) for _ in range(2)]
+    prm = dict(kind="pfc", dim=2, h=0.9, dt=0.02, alpha=0.6, tol=1e-12)
+    P, opts, J = oracle_setup(rho, prm, w_damp=0.0, tol=prm["tol"])
+    ref, r, v = [], rho, vel
+    for _ in range(2):
+        r, v, _ = S.step(r, v, P, opts, J=J)
+        ref.append((r, v))
+    return rho, vel, prm, ref
 
 
 @pytest.mark.parametrize("kind,n", [("pfc", 32), ("pfc", 16), ("cdft", 32)])
