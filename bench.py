@@ -138,6 +138,9 @@ def sweeps_per_launch(variant):
 def sweep_kernel(variant, batched):
     """Name of the fused-sweep kernel that variant `variant` launches."""
     pre = "kb_" if batched else "k_"
+    if variant >= 24:
+        tile = ["32x16", "64x8", "32x32"][variant - 24]
+        return f"{pre}smooth_rb2d<float,PFC,{tile}> (two sweeps per launch, halo 4)"
     if variant >= 12:
         m = (variant - 12) % 6
         tx = 64 if m < 3 else 128

@@ -257,7 +257,7 @@ int fm_batch_time_smoother(fm_batch* b, int iters, double* ms_per_launch, long l
 /* ---- Measurement (no counterpart in the paper). ---- */
 
 /* Number of variants of the 2-D fused red-black sweep. */
-#define FM_SWEEP_VARIANTS 24
+#define FM_SWEEP_VARIANTS 27
 
 /* Variant of the 2-D fused red-black sweep the autotuner chose for `level`
  * at fm_create, and its timings of all FM_SWEEP_VARIANTS variants in ms per
@@ -267,8 +267,10 @@ int fm_batch_time_smoother(fm_batch* b, int iters, double* ms_per_launch, long l
  * shared memory; bit 0: persistent double-buffered blocks); 12..17 the
  * row-marching form (strip width 64 for 12..14, 128 for 15..17; 16, 32 or 64
  * rows per block); 18..23 the row-marching form that runs two sweeps in one
- * pass (strips and rows as 12..17; its time per launch is halved to give the
- * time per sweep).  Setting the environment variable FM_RB_VARIANT=v before
+ * pass (strips and rows as 12..17); 24..26 the tile form that runs two sweeps
+ * per tile (tiles 32x16, 64x8, 32x32, halo of four, f and omega from global
+ * memory).  The time per launch of a two-sweep variant is halved to give its
+ * time per sweep.  Setting the environment variable FM_RB_VARIANT=v before
  * fm_create fixes the variant (no timing). */
 int fm_tuning(const fm_state* st, int level, int* variant, float* ms_per_variant);
 

@@ -88,13 +88,13 @@ __device__ __forceinline__ void smem_copy(S* dst, const S* src) {
 // PIPE: persistent blocks over tiles t = blockIdx.x, blockIdx.x + gridDim.x,
 // ..., two shared-memory buffers, the next tile's copies in flight while the
 // current one is computed; otherwise one tile per block.
-template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
+template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE, int NS = 1>
 __global__ void __launch_bounds__(rb_threads(TX, TY), rb_minb<T>(TX, TY)) kb_smooth_rb2d(const WorkItem* items, int nitems, const InstDev<T>* D,
                                                              const Phys<T>* P, const Ctl* ctl, int level,
                                                              int ntiles, int dir) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* buf0 = reinterpret_cast<T*>(smraw);
-  constexpr int BUFSTRIDE = rb_arrays<KIND, SF>() * RBGeom<TX, TY>::SN;
+  constexpr int BUFSTRIDE = rb_arrays<KIND, SF>() * RBGeom<TX, TY, NS>::SN;
   __shared__ Lvl<T> Gs[2];
   __shared__ int s_inst[2], s_x0[2], s_y0[2];
   int t = blockIdx.x;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(rb_threads(TX, TY), rb_minb<T>(TX, TY)) kb_smo
     if (s_inst[slot] >= 0) {
       smem_copy(&Gs[slot], &D[s_inst[slot]].lv[level]);
       __syncthreads();
-      rb2d_issue<T, KIND, TX, TY, SF>(Gs[slot], buf0 + slot * BUFSTRIDE, s_x0[slot], s_y0[slot], dir);
+      rb2d_issue<T, KIND, TX, TY, SF, NS>(Gs[slot], buf0 + slot * BUFSTRIDE, s_x0[slot], s_y0[slot], dir);
     }
     cp_async_commit();
   };
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(rb_threads(TX, TY), rb_minb<T>(TX, TY)) kb_smo
     fetch(t, 0);
     cp_async_wait_all();
     __syncthreads();
-    if (s_inst[0] >= 0) rb2d_compute<T, KIND, TX, TY, SF>(Gs[0], P[s_inst[0]], 0, s_x0[0], s_y0[0], dir);
+    if (s_inst[0] >= 0) rb2d_compute<T, KIND, TX, TY, SF, NS>(Gs[0], P[s_inst[0]], 0, s_x0[0], s_y0[0], dir);
   } else {
     fetch(t, 0);
     for (int k = 0;; ++k) {
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(rb_threads(TX, TY), rb_minb<T>(TX, TY)) kb_smo
       __syncthreads();
       const int slot = k & 1;
       if (s_inst[slot] >= 0)
-        rb2d_compute<T, KIND, TX, TY, SF>(Gs[slot], P[s_inst[slot]], slot * BUFSTRIDE, s_x0[slot], s_y0[slot],
+        rb2d_compute<T, KIND, TX, TY, SF, NS>(Gs[slot], P[s_inst[slot]], slot * BUFSTRIDE, s_x0[slot], s_y0[slot],
                                           dir);
       __syncthreads();
       if (!next) break;
@@ -545,22 +545,22 @@ struct Batch {
 
   static const WorkItem* it(fm_batch* b, const WList& w) { return b->items + w.off; }
 
-  template <int TX, int TY, bool SF, bool PIPE>
+  template <int TX, int TY, bool SF, bool PIPE, int NS = 1>
   static int launch_v(fm_batch* b, int l, int dir) {
-    constexpr size_t smem = rb_smem_bytes<T, KIND, TX, TY, SF, PIPE>();
+    constexpr size_t smem = rb_smem_bytes<T, KIND, TX, TY, SF, PIPE, NS>();
     if (smem + 4096 > (size_t)b->inst[0]->smem_optin) return FM_EINVAL;  // does not fit: skip
     static int per_sm = 0;
     if (!per_sm) {
-      FMB_CUDA(cudaFuncSetAttribute(kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>,
+      FMB_CUDA(cudaFuncSetAttribute(kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE, NS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      FMB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>,
+      FMB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE, NS>,
                                                              rb_threads(TX, TY), smem));
       if (per_sm < 1) per_sm = 1;
     }
     const WList& w = b->w_smooth[TX == 64 ? 1 : (TY == 32 ? 2 : 0)][l];
     int grid = w.nblocks;
     if (PIPE && grid > per_sm * b->inst[0]->sms) grid = per_sm * b->inst[0]->sms;
-    kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE><<<grid, rb_threads(TX, TY), smem, b->stream>>>(
+    kb_smooth_rb2d<T, KIND, TX, TY, SF, PIPE, NS><<<grid, rb_threads(TX, TY), smem, b->stream>>>(
         it(b, w), w.n, (const InstDev<T>*)b->D, (const Phys<T>*)b->P, b->ctl, l, w.nblocks, dir);
     FMB_LAUNCHED();
     return FM_OK;
@@ -627,20 +627,23 @@ struct Batch {
       case 20: return launch_m2<64>(b, l, dir, 20);
       case 21: return launch_m2<128>(b, l, dir, 21);
       case 22: return launch_m2<128>(b, l, dir, 22);
-      default: return launch_m2<128>(b, l, dir, 23);
+      case 23: return launch_m2<128>(b, l, dir, 23);
+      case 24: return launch_v<32, 16, false, false, 2>(b, l, dir);
+      case 25: return launch_v<64, 8, false, false, 2>(b, l, dir);
+      default: return launch_v<32, 32, false, false, 2>(b, l, dir);
     }
   }
 
   // `iters` sweeps of level l.  Each launch reads the correction from one
   // buffer and writes it to the other; *in_r says (and is updated to) whether
   // it is in r.  A two-sweep variant runs the sweeps in pairs and an odd last
-  // sweep with the one-sweep variant of the same strips.
+  // sweep with the one-sweep variant of the same blocks.
   static int smooth(fm_batch* b, int l, int iters, int* in_r) {
     if (b->w_smooth[0][l].n == 0) return FM_OK;
     const int v = b->rbv[l];
     for (int k = 0; k < iters;) {
       const int two = sweeps_per_launch(v) == 2 && k + 2 <= iters;
-      const int rc = launch_variant(b, (sweeps_per_launch(v) == 2 && !two) ? v - RB_NMARCH : v, l, *in_r);
+      const int rc = launch_variant(b, (sweeps_per_launch(v) == 2 && !two) ? one_sweep_twin(v) : v, l, *in_r);
       if (rc) return rc;
       *in_r ^= 1;
       k += two ? 2 : 1;

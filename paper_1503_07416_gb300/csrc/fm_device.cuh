@@ -440,7 +440,8 @@ __global__ void __launch_bounds__(TPB) k_prolong(Lvl<T> F, Lvl<T> C) {
 // launch followed by a black launch.  Blocks are persistent: each walks a
 // strided sequence of tiles with two shared-memory buffers, copying the next
 // tile in with cp.async (global -> shared, no register staging) while it
-// computes the current one.
+// computes the current one.  The two-sweep form (NS = 2) stages a halo of
+// four and runs both sweeps on the tile in one launch.
 constexpr int RB_H = 2;
 // Threads of a tile block: enough whole warps for the red pass over the tile
 // and its first halo ring ((tx + 2)/2 x (ty + 2) points) in one round.
@@ -488,10 +489,11 @@ struct TileAcc {
 // shared memory), TY + 2*RB_H rows.
 constexpr int RB_XO = 4;
 
-template <int TX, int TY>
+template <int TX, int TY, int NS = 1>
 struct RBGeom {
+  static constexpr int H = RB_H * NS;  // halo rows: two per sweep of the pass
   static constexpr int SW = TX + 2 * RB_XO;
-  static constexpr int SN = SW * (TY + 2 * RB_H);
+  static constexpr int SN = SW * (TY + 2 * H);
 };
 
 // Arrays staged per tile: e (NU), rk, cr, cv0, cv1, and with SF also f (NU)
@@ -501,9 +503,9 @@ __host__ __device__ constexpr int rb_arrays() {
   return Layout<KIND, 2>::NU + 4 + (SF ? Layout<KIND, 2>::NU + 1 : 0);
 }
 
-template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
+template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE, int NS = 1>
 __host__ __device__ constexpr size_t rb_smem_bytes() {
-  return (PIPE ? 2 : 1) * (size_t)rb_arrays<KIND, SF>() * RBGeom<TX, TY>::SN * sizeof(T);
+  return (PIPE ? 2 : 1) * (size_t)rb_arrays<KIND, SF>() * RBGeom<TX, TY, NS>::SN * sizeof(T);
 }
 
 
@@ -528,9 +530,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // the row length is a multiple of the chunk (chunks then never straddle the
 // periodic wrap), single elements otherwise.  The correction is read from G.e
 // (dir = 0) or from G.r (dir = 1).
-template <typename T, int KIND, int TX, int TY, bool SF>
+template <typename T, int KIND, int TX, int TY, bool SF, int NS = 1>
 __device__ __forceinline__ void rb2d_issue(const Lvl<T>& G, T* buf, int x0, int y0, int dir) {
-  using Gm = RBGeom<TX, TY>;
+  using Gm = RBGeom<TX, TY, NS>;
   constexpr int NU = Layout<KIND, 2>::NU;
   constexpr int NA = rb_arrays<KIND, SF>();
   constexpr int V = 16 / sizeof(T);
@@ -549,10 +551,10 @@ __device__ __forceinline__ void rb2d_issue(const Lvl<T>& G, T* buf, int x0, int 
   }
   if (nx % V == 0) {
     constexpr int CPR = Gm::SW / V;  // chunks per row
-    constexpr int NCH = CPR * (TY + 2 * RB_H);
+    constexpr int NCH = CPR * (TY + 2 * Gm::H);
     for (int t = threadIdx.x; t < NCH; t += blockDim.x) {
       const int ly = t / CPR, c = t - ly * CPR;
-      const int gidx = wrapi(y0 + ly - RB_H, ny) * nx + wrapi(x0 - RB_XO + c * V, nx);
+      const int gidx = wrapi(y0 + ly - Gm::H, ny) * nx + wrapi(x0 - RB_XO + c * V, nx);
       const int sidx = ly * Gm::SW + c * V;
 #pragma unroll
       for (int a = 0; a < NA; ++a) cp_async_16(buf + a * Gm::SN + sidx, src[a] + gidx);
@@ -560,37 +562,40 @@ __device__ __forceinline__ void rb2d_issue(const Lvl<T>& G, T* buf, int x0, int 
   } else {
     for (int t = threadIdx.x; t < Gm::SN; t += blockDim.x) {
       const int ly = t / Gm::SW, lx = t - ly * Gm::SW;
-      const int gidx = wrapi(y0 + ly - RB_H, ny) * nx + wrapi(x0 + lx - RB_XO, nx);
+      const int gidx = wrapi(y0 + ly - Gm::H, ny) * nx + wrapi(x0 + lx - RB_XO, nx);
 #pragma unroll
       for (int a = 0; a < NA; ++a) cp_async_elem(buf + a * Gm::SN + t, src[a] + gidx);
     }
   }
 }
 
-// Red pass on tile + ring 1, black pass on the tile, write-back of the tile
-// to G.r (dir = 0) or G.e (dir = 1); the staged tile starts at element `base`
-// of the dynamic shared memory.
-template <typename T, int KIND, int TX, int TY, bool SF>
+// NS = 1: red pass on tile + ring 1, black pass on the tile.  NS = 2 (two
+// sweeps, halo of four): red on tile + ring 3, black on ring 2, red on ring
+// 1, black on the tile -- each pass reads only values the previous pass has
+// finished on its wider ring.  Then the tile is written back to G.r (dir = 0)
+// or G.e (dir = 1); the staged tile starts at element `base` of the dynamic
+// shared memory.
+template <typename T, int KIND, int TX, int TY, bool SF, int NS = 1>
 __device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, int base, int x0, int y0,
                                              int dir) {
-  using Gm = RBGeom<TX, TY>;
+  using Gm = RBGeom<TX, TY, NS>;
   constexpr int NU = Layout<KIND, 2>::NU;
   constexpr int SN = Gm::SN, SW = Gm::SW;
   const TileAcc<T, KIND, SN, SF> acc{base, G.h, &G};
   const PtK<T> K = make_ptk<T, 2>(P, G.h);
   const int nx = G.g.nx, ny = G.g.ny;
 #pragma unroll
-  for (int pass = 0; pass < 2; ++pass) {
-    const int color = pass;              // red (i + j even) first, then black
-    const int ring = pass == 0 ? 1 : 0;  // red also on the first halo ring
-    const int w = TX + 2 * ring;         // even
+  for (int pass = 0; pass < 2 * NS; ++pass) {
+    const int color = pass & 1;           // red (i + j even) first, then black
+    const int ring = 2 * NS - 1 - pass;   // halo rings the pass also covers
+    const int w = TX + 2 * ring;          // even
     const int hw = w >> 1;
     const int npts = hw * (TY + 2 * ring);
     for (int t = threadIdx.x; t < npts; t += blockDim.x) {
       const int ry = t / hw;
       const int gy = y0 - ring + ry;
       const int rx = 2 * (t - ry * hw) + ((color + x0 + ring + gy) & 1);
-      const int lx = RB_XO - ring + rx, ly = RB_H - ring + ry;
+      const int lx = RB_XO - ring + rx, ly = Gm::H - ring + ry;
       Nb n;
       n.c = ly * SW + lx;
       n.m[0] = n.c - 1;
@@ -607,7 +612,7 @@ __device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, 
     const int ty = t / TX, tx = t - ty * TX;
     const int gx = x0 + tx, gy = y0 + ty;
     if (gx < nx && gy < ny) {
-      const int sidx = (ty + RB_H) * SW + tx + RB_XO;
+      const int sidx = (ty + Gm::H) * SW + tx + RB_XO;
 #pragma unroll
       for (int q = 0; q < NU; ++q) (dir ? G.e[q] : G.r[q])[gy * nx + gx] = acc.e(q, sidx);
     }
@@ -624,32 +629,32 @@ __device__ __forceinline__ void rb2d_compute(const Lvl<T>& G, const Phys<T>& P, 
 // holds values from before the sweep, whichever tiles have already been
 // written, so the result is exactly one red-black sweep for any block
 // schedule.
-template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
+template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE, int NS = 1>
 __global__ void __launch_bounds__(rb_threads(TX, TY), rb_minb<T>(TX, TY)) k_smooth_rb2d(Lvl<T> G, Phys<T> P, int ntx, int ntiles,
                                                                     int dir) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* buf0 = reinterpret_cast<T*>(smraw);
-  constexpr int BUFSTRIDE = rb_arrays<KIND, SF>() * RBGeom<TX, TY>::SN;
+  constexpr int BUFSTRIDE = rb_arrays<KIND, SF>() * RBGeom<TX, TY, NS>::SN;
   int t = blockIdx.x;
   if (t >= ntiles) return;
   if constexpr (!PIPE) {
-    rb2d_issue<T, KIND, TX, TY, SF>(G, buf0, (t % ntx) * TX, (t / ntx) * TY, dir);
+    rb2d_issue<T, KIND, TX, TY, SF, NS>(G, buf0, (t % ntx) * TX, (t / ntx) * TY, dir);
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    rb2d_compute<T, KIND, TX, TY, SF>(G, P, 0, (t % ntx) * TX, (t / ntx) * TY, dir);
+    rb2d_compute<T, KIND, TX, TY, SF, NS>(G, P, 0, (t % ntx) * TX, (t / ntx) * TY, dir);
   } else {
-    rb2d_issue<T, KIND, TX, TY, SF>(G, buf0, (t % ntx) * TX, (t / ntx) * TY, dir);
+    rb2d_issue<T, KIND, TX, TY, SF, NS>(G, buf0, (t % ntx) * TX, (t / ntx) * TY, dir);
     cp_async_commit();
     for (int k = 0;; ++k) {
       const int tn = t + gridDim.x;
       const bool next = tn < ntiles;
       if (next)
-        rb2d_issue<T, KIND, TX, TY, SF>(G, buf0 + ((k + 1) & 1) * BUFSTRIDE, (tn % ntx) * TX, (tn / ntx) * TY, dir);
+        rb2d_issue<T, KIND, TX, TY, SF, NS>(G, buf0 + ((k + 1) & 1) * BUFSTRIDE, (tn % ntx) * TX, (tn / ntx) * TY, dir);
       cp_async_commit();
       cp_async_wait_one();
       __syncthreads();
-      rb2d_compute<T, KIND, TX, TY, SF>(G, P, (k & 1) * BUFSTRIDE, (t % ntx) * TX, (t / ntx) * TY, dir);
+      rb2d_compute<T, KIND, TX, TY, SF, NS>(G, P, (k & 1) * BUFSTRIDE, (t % ntx) * TX, (t / ntx) * TY, dir);
       __syncthreads();
       if (!next) break;
       t = tn;
@@ -992,15 +997,22 @@ __global__ void __launch_bounds__(march_threads(TX), march2_minb<T>(TX)) k_smoot
 // Variants of the 2-D fused sweep, chosen per level by the autotuner:
 // 0..11 tile form (bits 0-1: PIPE, SF; v >> 2: tile 32x16, 64x8, 32x32),
 // 12..17 marching form (strip width 64 or 128; rows per block 16, 32, 64),
-// 18..23 the two-sweep marching form with the same strips and rows.
+// 18..23 the two-sweep marching form with the same strips and rows, 24..26
+// the two-sweep tile form (tiles 32x16, 64x8, 32x32; f and omega from global
+// memory, one tile per block).
 constexpr int RB_NVAR = FM_SWEEP_VARIANTS;
 constexpr int TUNE_REPS = 10;  // timed launches per variant and level in the autotuners
 constexpr int RB_NTILE = 12;
 constexpr int RB_NMARCH = 6;
 constexpr int RB_TWO = RB_NTILE + RB_NMARCH;  // first two-sweep variant
+constexpr int RB_TWO_TILE = RB_TWO + RB_NMARCH;  // first two-sweep tile variant
 __host__ __device__ constexpr int march_tx(int v) { return (v - RB_NTILE) % RB_NMARCH < 3 ? 64 : 128; }
 __host__ __device__ constexpr int march_ly(int v) { return 16 << ((v - RB_NTILE) % 3); }
 __host__ __device__ constexpr int sweeps_per_launch(int v) { return v >= RB_TWO ? 2 : 1; }
+// The one-sweep variant with the same blocks as two-sweep variant v.
+__host__ __device__ constexpr int one_sweep_twin(int v) {
+  return v >= RB_TWO_TILE ? (v - RB_TWO_TILE) * 4 : (v >= RB_TWO ? v - RB_NMARCH : v);
+}
 
 // The whole V-cycle of the small levels (each at most SMALL_N points) in one
 // thread block: phases separated by __syncthreads, data in L1/L2.

@@ -130,16 +130,16 @@ static cudaMemcpyKind kind_out(int where) {
   } while (0)
 
 // Launch variant (TX, TY, SF, PIPE) of the 2-D fused sweep on level L.
-template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE>
+template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE, int NS = 1>
 static int launch_rb_v(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int dir) {
-  constexpr size_t smem = rb_smem_bytes<T, KIND, TX, TY, SF, PIPE>();
+  constexpr size_t smem = rb_smem_bytes<T, KIND, TX, TY, SF, PIPE, NS>();
   if (smem + 4096 > (size_t)st->smem_optin) return FM_EINVAL;  // variant does not fit on this device
   if (!L.r[0]) return FM_EINVAL;                               // no second correction buffer
   static int per_sm = 0;
   if (!per_sm) {
-    if (cudaFuncSetAttribute(k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE>, rb_threads(TX, TY),
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE, NS>, rb_threads(TX, TY),
                                                       smem) != cudaSuccess) {
       cudaGetLastError();
       return FM_ECUDA;
@@ -150,7 +150,7 @@ static int launch_rb_v(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStre
   const int ntiles = ntx * ((L.g.ny + TY - 1) / TY);
   int grid = ntiles;
   if (PIPE && grid > per_sm * st->sms) grid = per_sm * st->sms;
-  k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE><<<grid, rb_threads(TX, TY), smem, s>>>(L, P, ntx, ntiles, dir);
+  k_smooth_rb2d<T, KIND, TX, TY, SF, PIPE, NS><<<grid, rb_threads(TX, TY), smem, s>>>(L, P, ntx, ntiles, dir);
   return FM_OK;
 }
 
@@ -219,7 +219,10 @@ static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cud
     case 20: return launch_march2<T, KIND, 64>(st, L, P, s, dir, 64);
     case 21: return launch_march2<T, KIND, 128>(st, L, P, s, dir, 16);
     case 22: return launch_march2<T, KIND, 128>(st, L, P, s, dir, 32);
-    default: return launch_march2<T, KIND, 128>(st, L, P, s, dir, 64);
+    case 23: return launch_march2<T, KIND, 128>(st, L, P, s, dir, 64);
+    case 24: return launch_rb_v<T, KIND, 32, 16, false, false, 2>(st, L, P, s, dir);
+    case 25: return launch_rb_v<T, KIND, 64, 8, false, false, 2>(st, L, P, s, dir);
+    default: return launch_rb_v<T, KIND, 32, 32, false, false, 2>(st, L, P, s, dir);
   }
 }
 

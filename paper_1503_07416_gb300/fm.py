@@ -237,7 +237,7 @@ def fm_residual(st, g, r=None):
     return nrm.value
 
 
-FM_SWEEP_VARIANTS = 24
+FM_SWEEP_VARIANTS = 27
 FM_SWEEP_AUTO = -1
 FM_SWEEP_TWO_COLOUR = -2
 

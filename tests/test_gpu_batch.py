@@ -116,16 +116,17 @@ def test_batch_failure_is_isolated():
     b.close()
 
 
+@pytest.mark.parametrize("variant", [21, 24])
 @pytest.mark.parametrize("nu", [(2, 2), (1, 3), (3, 2)])
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
-def test_batch_two_sweep_smoother(precision, nu, monkeypatch):
-    """The batch with the two-sweep marching variant 21 on every level: the
+def test_batch_two_sweep_smoother(precision, nu, variant, monkeypatch):
+    """The batch with a two-sweep variant (marching 21, tile 24) on every level: the
     correction of a level may sit in its second buffer between the pre- and
     the post-smoothing (the fused residual + restriction and the prolongation
     take it from there) and an odd sweep count runs the one-sweep variant of
-    the same strips.  Against the oracle with the same cycle and the
+    the same blocks.  Against the oracle with the same cycle and the
     single-instance solver with the same variant."""
-    monkeypatch.setenv("FM_RB_VARIANT", "21")
+    monkeypatch.setenv("FM_RB_VARIANT", str(variant))
     sizes = [32, (256, 192), 128]
     ens = _ensemble("pfc", sizes, 12)
     h, tol = 0.9, 1e-12

@@ -333,7 +333,7 @@ def test_fused_tile_smoother_matches_two_colour_launches(kind, precision, monkey
 
 
 @pytest.mark.parametrize("nu", [(2, 2), (1, 2), (3, 3)])
-@pytest.mark.parametrize("variant", [18, 21])
+@pytest.mark.parametrize("variant", [18, 21, 24])
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
 def test_two_sweep_smoother_in_the_cycle(precision, variant, nu, monkeypatch):
     """V-cycles whose fused launches run two sweeps each: after an odd number

@@ -140,25 +140,26 @@ def test_pfc_every_fused_variant_matches_two_colour_launches(precision):
 @pytest.mark.parametrize("kind,shape", [("pfc", (1000, 1002)), ("pfc", (18, 10)), ("pfc", (6, 140)),
                                         ("cdft", (64, 128))])
 def test_two_sweep_pass_equals_one_sweep_passes(kind, shape, precision, monkeypatch):
-    """The two-sweep marching variants (18..23) run the same point update on
-    the same values as the one-sweep marching variants with the same strips
-    and rows (12..17), only in another order of independent points, so the
-    results agree bit for bit: 2 sweeps (one pass) and 5 (two passes and a
-    two-colour sweep), on grids with ragged strips, fewer rows than a block
-    and fewer columns than a strip."""
+    """The two-sweep variants run the same point update on the same values
+    as the one-sweep variants with the same blocks -- marching 18..23 against
+    12..17, tiles 24..26 against 0, 4, 8 -- only in another order of
+    independent points, so the results agree bit for bit: 2 sweeps (one pass)
+    and 5 (two passes and a two-colour sweep), on grids with ragged strips
+    and tiles, fewer rows than a block and fewer columns than a strip."""
     monkeypatch.setenv("FM_RB_VARIANT", "0")  # no autotuning at create
     rho, vel, prm = _case(kind, shape, 9)
     f, _ = _oracle(rho, vel, prm, 0.0, 0)
+    pairs = [(18 + m, 12 + m) for m in range(6)] + [(24 + k, 4 * k) for k in range(3)]
     for sweeps in (2, 5):
-        for m in range(6):
+        for v2, v1 in pairs:
             try:
-                one = _gpu(rho, vel, prm, f, precision, 0.0, sweeps, 12 + m)
+                one = _gpu(rho, vel, prm, f, precision, 0.0, sweeps, v1)
+                two = _gpu(rho, vel, prm, f, precision, 0.0, sweeps, v2)
             except fm.FMError as err:
                 assert err.code == fm.FM_EINVAL and precision == fm.FM_FP64
                 continue
-            two = _gpu(rho, vel, prm, f, precision, 0.0, sweeps, 18 + m)
             for q, (a, b) in enumerate(zip(two, one)):
-                assert np.array_equal(a, b), (sweeps, m, q, float(np.max(np.abs(a - b))))
+                assert np.array_equal(a, b), (sweeps, v2, q, float(np.max(np.abs(a - b))))
 
 
 def test_smooth_row_rejects_bad_arguments():
