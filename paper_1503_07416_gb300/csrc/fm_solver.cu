@@ -335,7 +335,8 @@ struct Solver {
       FM_CUDA(cudaEventCreate(&e0));
       FM_CUDA(cudaEventCreate(&e1));
       int rc = FM_OK;
-      for (int l = 0; l < st->small_from && rc == FM_OK; ++l) {
+      const int ntuned = st->small_from + (st->coarse_fused ? 1 : 0);
+      for (int l = 0; l < ntuned && rc == FM_OK; ++l) {
         Lvl<T> L = make_lvl<T>(st, l);
         float best = 1e30f;
         for (int v = 0; v < RB_NVAR && rc == FM_OK; ++v) {
@@ -554,8 +555,14 @@ struct Solver {
     return run_sweeps(st, make_lvl<T>(st, l), v, P, iters, in_r, prof);
   }
 
-  static int vcycle(fm_state* st, int l, const Phys<T>& P) {
+  // One V-cycle from level l down; *out_in_r: on return the correction of
+  // level l is in its r buffer (1) or in e (0).
+  static int vcycle(fm_state* st, int l, const Phys<T>& P, int* out_in_r) {
     cudaStream_t s = st->stream;
+    *out_in_r = 0;
+    if (l >= st->small_from && st->coarse_fused) {  // the coarsest level: ncoarse fused sweeps
+      return smooth(st, l, P, st->prm.ncoarse, out_in_r);
+    }
     if (l >= st->small_from) {
       SmallLv<T> S;
       S.count = st->nlev - l;
@@ -596,16 +603,14 @@ struct Solver {
       k_restrict_rhs<T, KIND, DIM><<<nblocks(C.g.N), TPB, 0, s>>>(F, C, P);
       FM_LAUNCHED();
     }
-    rc = vcycle(st, l + 1, P);
+    int c_in_r = 0;
+    rc = vcycle(st, l + 1, P, &c_in_r);
     if (rc) return rc;
-    k_prolong<T, LY::NU, DIM><<<nblocks(F.g.N), TPB, 0, s>>>(F, C);
+    k_prolong<T, LY::NU, DIM><<<nblocks(F.g.N), TPB, 0, s>>>(F, c_in_r ? swap_er(C) : C);
     FM_LAUNCHED();
     rc = smooth(st, l, P, st->prm.nu2, &in_r);
     if (rc) return rc;
-    if (in_r) {
-      k_copy_back<T, LY::NU><<<nblocks(F.g.N), TPB, 0, s>>>(make_lvl<T>(st, l));
-      FM_LAUNCHED();
-    }
+    *out_in_r = in_r;
     return FM_OK;
   }
 
@@ -613,8 +618,13 @@ struct Solver {
     int rc = inject_all(st, true);
     if (rc) return rc;
     Phys<T> P = make_phys<T>(st);
-    rc = vcycle(st, 0, P);
+    int in_r = 0;
+    rc = vcycle(st, 0, P, &in_r);
     if (rc) return rc;
+    if (in_r) {  // the float64 update reads the level-0 correction from e
+      k_copy_back<T, LY::NU><<<nblocks(st->lv[0].g.N), TPB, 0, st->stream>>>(make_lvl<T>(st, 0));
+      FM_LAUNCHED();
+    }
     const Geo G = st->lv[0].g;
     Fields64 F = make_fields(st);
     Resid64Out O = resid_out(st, true, nullptr);
@@ -1026,6 +1036,11 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
     const char* ef = getenv("FM_FUSED_RB");
     st->fused_rb = !(ef && ef[0] == '0');
   }
+  // A coarsest level that is the only level of the single-block part and
+  // larger than SMALL_N points is smoothed by the multi-block fused sweeps
+  // instead (one block would run its points serially).
+  st->coarse_fused = grid->dim == 2 && st->fused_rb && st->small_from == nlev - 1 &&
+                     st->lv[nlev - 1].g.N > SMALL_N;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {

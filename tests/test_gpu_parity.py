@@ -356,6 +356,28 @@ def test_two_sweep_smoother_in_the_cycle(precision, variant, nu, monkeypatch):
     sol.close()
 
 
+@pytest.mark.parametrize("ncoarse", [2, 3])
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_large_coarsest_level_uses_fused_sweeps(precision, ncoarse):
+    """A coarsest level above 1024 points (48 x 64 of the 192 x 256 grid with
+    coarsest = 48) is smoothed by the multi-block fused sweeps, its
+    correction handed to the prolongation from whichever buffer holds it;
+    two steps against the oracle, an even and an odd coarse sweep count."""
+    rho, vel, prm, ref = _two_sweep_case()
+    tol = prm["tol"]
+    sol = gpu_solver(rho, prm, precision=precision, w_damp=0.0, tol=tol, coarsest=48, ncoarse=ncoarse)
+    assert fm.fm_levels(sol.handle) == 3
+    bound = TOL64 if precision == fm.FM_FP64 else TOLMIX
+    for ro, vo in ref:
+        sol.set_fields(rho, vel)
+        assert sol.step(prm["dt"]).res <= tol
+        rg, vg = sol.get_fields()
+        errs = [rel(rg, ro)] + [rel(a, b) for a, b in zip(vg, vo)]
+        assert max(errs) <= bound, errs
+        rho, vel = ro, vo
+    sol.close()
+
+
 @functools.lru_cache(maxsize=1)
 def _two_sweep_case():
     """192 x 256 PFC state and its two oracle steps (the converged step does
