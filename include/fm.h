@@ -254,6 +254,12 @@ int fm_batch_tuning(const fm_batch* b, int level, int* variant, float* ms_per_va
  * the next fm_step_batch resets. */
 int fm_batch_time_smoother(fm_batch* b, int iters, double* ms_per_launch, long long* points);
 
+/* Measurement (no counterpart in the paper): as fm_batch_time_smoother for
+ * fused-sweep variant `variant` (0 .. FM_SWEEP_VARIANTS - 1, encoding as
+ * fm_tuning) instead of the autotuned one.  FM_EINVAL for an unknown variant
+ * or one that does not fit in shared memory. */
+int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_per_launch, long long* points);
+
 /* ---- Measurement (no counterpart in the paper). ---- */
 
 /* Number of variants of the 2-D fused red-black sweep. */

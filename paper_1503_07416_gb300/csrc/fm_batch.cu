@@ -907,18 +907,18 @@ struct Batch {
     return FM_OK;
   }
 
-  // Time `iters` finest-level fused sweeps over all instances (CUDA events on
-  // the batch stream); the corrections they write are scratch that the next
-  // step resets.
-  static int time_smoother(fm_batch* b, int iters, double* ms) {
+  // Time `iters` finest-level launches of fused-sweep variant v over all
+  // instances (CUDA events on the batch stream); the corrections they write
+  // are scratch that the next step resets.
+  static int time_smoother(fm_batch* b, int v, int iters, double* ms) {
     kb_set_active<<<(b->count + 255) / 256, 256, 0, b->stream>>>(b->ctl, b->count);
     FMB_LAUNCHED();
     cudaEvent_t e0, e1;
     FMB_CUDA(cudaEventCreate(&e0));
     FMB_CUDA(cudaEventCreate(&e1));
-    int rc = launch_variant(b, b->rbv[0], 0);  // warm-up
+    int rc = launch_variant(b, v, 0);  // warm-up
     if (rc == FM_OK && cudaEventRecord(e0, b->stream) != cudaSuccess) rc = FM_ECUDA;
-    for (int k = 0; k < iters && rc == FM_OK; ++k) rc = launch_variant(b, b->rbv[0], 0);
+    for (int k = 0; k < iters && rc == FM_OK; ++k) rc = launch_variant(b, v, 0);
     if (rc == FM_OK && cudaEventRecord(e1, b->stream) != cudaSuccess) rc = FM_ECUDA;
     if (rc == FM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = FM_ECUDA;
     float t = 0.f;
@@ -1067,18 +1067,29 @@ int fm_batch_tuning(const fm_batch* b, int level, int* variant, float* ms_per_va
   return FM_OK;
 }
 
-int fm_batch_time_smoother(fm_batch* b, int iters, double* ms_per_launch, long long* points) {
+static int batch_time_variant(fm_batch* b, int variant, int iters, double* ms_per_launch, long long* points) {
   if (!b || iters < 1 || !ms_per_launch) return FM_EINVAL;
   if (b->maxdepth < 1) return FM_EINVAL;  // no instance has a multi-kernel finest level
+  const int v = variant < 0 ? b->rbv[0] : variant;
+  if (v >= RB_NVAR) return FM_EINVAL;
   long long np = 0;
   for (int i = 0; i < b->count; ++i)
     if (b->inst[i]->small_from > 0) np += b->inst[i]->lv[0].g.N;
   if (points) *points = np;
   if (b->prm.precision == FM_MIXED)
-    return b->kind == FM_PFC ? Batch<float, KPFC>::time_smoother(b, iters, ms_per_launch)
-                             : Batch<float, KCDFT>::time_smoother(b, iters, ms_per_launch);
-  return b->kind == FM_PFC ? Batch<double, KPFC>::time_smoother(b, iters, ms_per_launch)
-                           : Batch<double, KCDFT>::time_smoother(b, iters, ms_per_launch);
+    return b->kind == FM_PFC ? Batch<float, KPFC>::time_smoother(b, v, iters, ms_per_launch)
+                             : Batch<float, KCDFT>::time_smoother(b, v, iters, ms_per_launch);
+  return b->kind == FM_PFC ? Batch<double, KPFC>::time_smoother(b, v, iters, ms_per_launch)
+                           : Batch<double, KCDFT>::time_smoother(b, v, iters, ms_per_launch);
+}
+
+int fm_batch_time_smoother(fm_batch* b, int iters, double* ms_per_launch, long long* points) {
+  return batch_time_variant(b, -1, iters, ms_per_launch, points);
+}
+
+int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_per_launch, long long* points) {
+  if (variant < 0) return FM_EINVAL;
+  return batch_time_variant(b, variant, iters, ms_per_launch, points);
 }
 
 }  // extern "C"

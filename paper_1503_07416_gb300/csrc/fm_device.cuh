@@ -1567,6 +1567,30 @@ __global__ void k_norm_final(const double* partials, int nblk, double w, double*
 }
 
 
+// Residual value r at point idx: store it in precision T for the cycle (f0,
+// when given) and add r^2 to the sum of squares of the stopping test.  In the
+// cycle of the mixed path the square is taken of the float32-rounded residual
+// the cycle receives and summed in float32 (fa), off the float64 pipe: the
+// sum only decides when to stop, and float32 carries it to ~1e-7 relative.
+// Otherwise it is summed in float64 (acc).
+template <typename T>
+__device__ __forceinline__ void norm_add(void* f0, double r, double& acc, float& fa, int idx) {
+  if (f0) {
+    const T rt = to_t<T>(r);
+    static_cast<T*>(f0)[idx] = rt;
+    if constexpr (sizeof(T) == 4) {
+      fa = fmaf(rt, rt, fa);
+      return;
+    }
+  }
+  acc += r * r;
+}
+template <int NQ>
+__device__ __forceinline__ void norm_finish(double (&acc)[NQ], const float (&fa)[NQ]) {
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] += widen(fa[q]);
+}
+
 struct Resid64Out {
   void* f0[MAXU];   // precision-T rhs of level 0 (or null)
   void* e0[MAXU];   // precision-T correction of level 0, zeroed (or null)
@@ -1585,6 +1609,9 @@ __device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out
   double acc[LY::NU];
 #pragma unroll
   for (int q = 0; q < LY::NU; ++q) acc[q] = 0.0;
+  float fa[LY::NU];
+#pragma unroll
+  for (int q = 0; q < LY::NU; ++q) fa[q] = 0.0f;
   const double ih2 = K.ih2, c_div = K.c_div, c_w = K.c_w, c_q = K.c_div, c_m = K.c_m, c_v = K.c_v;
   const double third = 1.0 / 3.0;
   for (int idx = lb * blockDim.x + threadIdx.x; idx < G.N; idx += nb * blockDim.x) {
@@ -1642,8 +1669,7 @@ __device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out
 #pragma unroll
     for (int q = 0; q < LY::NU; ++q) {
       const double r = rv[q];
-      acc[q] += r * r;
-      if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = to_t<T>(r);
+      norm_add<T>(O.f0[q], r, acc[q], fa[q], idx);
       if (O.e0[q]) static_cast<T*>(O.e0[q])[idx] = T(0);
       if (O.r64[q]) O.r64[q][idx] = r;
     }
@@ -1653,6 +1679,7 @@ __device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out
       for (int d = 0; d < DIM; ++d) O.cv32[d][idx] = narrow_rn(uc[d]);
     }
   }
+  norm_finish<LY::NU>(acc, fa);
   block_partials<LY::NU>(acc, partials, lb);
 }
 
@@ -1674,6 +1701,9 @@ __device__ __forceinline__ void resid64_tile_body(const Fields64& F, const Resid
   double acc[LY::NU];
 #pragma unroll
   for (int q = 0; q < LY::NU; ++q) acc[q] = 0.0;
+  float fa[LY::NU];
+#pragma unroll
+  for (int q = 0; q < LY::NU; ++q) fa[q] = 0.0f;
   const double ih2 = K.ih2, c_div = K.c_div, c_w = K.c_w, c_q = K.c_div, c_m = K.c_m, c_v = K.c_v;
   const double third = 1.0 / 3.0;
   const int nx = G.nx, ny = G.ny;
@@ -1735,8 +1765,7 @@ __device__ __forceinline__ void resid64_tile_body(const Fields64& F, const Resid
 #pragma unroll
         for (int q = 0; q < LY::NU; ++q) {
           const double r = rv[q];
-          acc[q] += r * r;
-          if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = to_t<T>(r);
+          norm_add<T>(O.f0[q], r, acc[q], fa[q], idx);
           if (O.e0[q]) static_cast<T*>(O.e0[q])[idx] = T(0);
           if (O.r64[q]) O.r64[q][idx] = r;
         }
@@ -1749,6 +1778,7 @@ __device__ __forceinline__ void resid64_tile_body(const Fields64& F, const Resid
     }
     __syncthreads();
   }
+  norm_finish<LY::NU>(acc, fa);
   block_partials<LY::NU>(acc, partials, lb);
 }
 
@@ -1792,6 +1822,9 @@ __global__ void __launch_bounds__(TPB) k_resid64_x(Fields64 F, Shared64 X, Resid
   double acc[LY::NU];
 #pragma unroll
   for (int q = 0; q < LY::NU; ++q) acc[q] = 0.0;
+  float fa[LY::NU];
+#pragma unroll
+  for (int q = 0; q < LY::NU; ++q) fa[q] = 0.0f;
   const double ih2 = K.ih2, c_div = K.c_div, c_w = K.c_w, c_q = K.c_div, c_m = K.c_m, c_v = K.c_v;
   const double third = 1.0 / 3.0;
   const double* const* g = F.g;
@@ -1833,8 +1866,7 @@ __global__ void __launch_bounds__(TPB) k_resid64_x(Fields64 F, Shared64 X, Resid
 #pragma unroll
     for (int q = 0; q < LY::NU; ++q) {
       const double r = rv[q];
-      acc[q] += r * r;
-      if (O.f0[q]) static_cast<T*>(O.f0[q])[idx] = to_t<T>(r);
+      norm_add<T>(O.f0[q], r, acc[q], fa[q], idx);
       if (O.e0[q]) static_cast<T*>(O.e0[q])[idx] = T(0);
       if (O.r64[q]) O.r64[q][idx] = r;
     }
@@ -1844,6 +1876,7 @@ __global__ void __launch_bounds__(TPB) k_resid64_x(Fields64 F, Shared64 X, Resid
       for (int d = 0; d < DIM; ++d) O.cv32[d][idx] = narrow_rn(uc[d]);
     }
   }
+  norm_finish<LY::NU>(acc, fa);
   block_partials<LY::NU>(acc, partials, blockIdx.x);
 }
 

@@ -96,6 +96,8 @@ _SIGS = {
     "fm_batch_launches": (C.c_longlong, [C.c_void_p]),
     "fm_batch_tuning": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "fm_batch_time_smoother": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "fm_batch_time_sweep_variant": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                              C.POINTER(C.c_longlong)]),
     "fm_mass_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_double, C.c_void_p,
                                   C.c_void_p]),
     "fm_profile": (C.c_int, [C.c_void_p, C.c_int]),
@@ -325,6 +327,14 @@ def fm_batch_time_smoother(b, iters):
     """(ms per launch, finest points per launch)."""
     ms, pts = C.c_double(), C.c_longlong()
     _check(lib().fm_batch_time_smoother(b, iters, C.byref(ms), C.byref(pts)), "fm_batch_time_smoother")
+    return ms.value, pts.value
+
+
+def fm_batch_time_sweep_variant(b, variant, iters):
+    """(ms per launch of fused-sweep variant `variant`, finest points per launch)."""
+    ms, pts = C.c_double(), C.c_longlong()
+    _check(lib().fm_batch_time_sweep_variant(b, variant, iters, C.byref(ms), C.byref(pts)),
+           "fm_batch_time_sweep_variant")
     return ms.value, pts.value
 
 

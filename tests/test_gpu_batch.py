@@ -210,3 +210,26 @@ def test_batch_with_the_benchmark_hierarchy(precision):
         errs = [rel(rg, ro)] + [rel(a, c) for a, c in zip(vg, vo)]
         assert max(errs) <= bound, (i, errs)
     b.close()
+
+
+def test_batch_smoother_timing_entry_points():
+    """fm_batch_time_smoother times the autotuned variant and
+    fm_batch_time_sweep_variant any fixed one (positive times, the finest
+    points of the multi-kernel instances); unknown variants are rejected, and
+    a later step still converges (the timed sweeps only touch scratch)."""
+    sizes = [128, 256]
+    ens = _ensemble("pfc", sizes, 13)
+    b = fm.Batch("pfc", sizes, 0.9, alpha=0.6, precision=fm.FM_MIXED, tol=1e-10, w_damp=0.0, max_cycles=80)
+    for i, (rho, vel, dt) in enumerate(ens):
+        b.set_fields(i, rho, vel)
+    ms, pts = fm.fm_batch_time_smoother(b.handle, 3)
+    assert ms > 0 and pts == 128 * 128 + 256 * 256
+    for v in (0, 16, 22, 24):
+        ms_v, pts_v = fm.fm_batch_time_sweep_variant(b.handle, v, 3)
+        assert ms_v > 0 and pts_v == pts
+    for v in (-1, fm.FM_SWEEP_VARIANTS):
+        with pytest.raises(fm.FMError):
+            fm.fm_batch_time_sweep_variant(b.handle, v, 3)
+    info = b.step([dt for _, _, dt in ens])
+    assert all(x.res <= 1e-10 for x in info)
+    b.close()
