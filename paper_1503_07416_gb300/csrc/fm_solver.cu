@@ -1037,10 +1037,10 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
     st->fused_rb = !(ef && ef[0] == '0');
   }
   // A coarsest level that is the only level of the single-block part and
-  // larger than SMALL_N points is smoothed by the multi-block fused sweeps
-  // instead (one block would run its points serially).
-  st->coarse_fused = grid->dim == 2 && st->fused_rb && st->small_from == nlev - 1 &&
-                     st->lv[nlev - 1].g.N > SMALL_N;
+  // larger than SMALL_N points is smoothed by multi-block sweeps instead (the
+  // fused sweeps in 2-D, a red and a black launch per sweep in 3-D or without
+  // fusion); one block would run its points serially.
+  st->coarse_fused = st->small_from == nlev - 1 && st->lv[nlev - 1].g.N > SMALL_N;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {

@@ -64,7 +64,7 @@ struct fm_state {
   bool capturing;
   bool use_graph;                 // run fm_step as one CUDA graph launch
   bool fused_rb;                  // 2-D: one tiled launch per red-black sweep
-  bool coarse_fused;              // 2-D: the coarsest level alone exceeds one block's share: fused sweeps
+  bool coarse_fused;              // the coarsest level alone exceeds one block's share: multi-block sweeps
   int rbv[fm::MAXLEV];            // chosen variant of the fused sweep per level
   float rbt[fm::MAXLEV][FM_SWEEP_VARIANTS];  // autotuner timings (ms per sweep)
   int small_from;                 // first level handled by the single-block V-cycle

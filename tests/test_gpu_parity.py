@@ -101,11 +101,13 @@ def test_smallest_grid():
     _compare_step(rho, vel, prm, fm.FM_FP64, w_damp=0.0, ncoarse=40)
 
 
+@pytest.mark.parametrize("n", [16, 32])
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
-def test_3d_pfc(precision):
-    """3-D PFC 16^3 with random velocity (three vorticity components)."""
+def test_3d_pfc(precision, n):
+    """3-D PFC with random velocity (three vorticity components): 16^3 (one
+    level, its sweeps as red and black launches over the whole grid) and 32^3
+    (two levels, the 16^3 coarsest grid smoothed by multi-block launches)."""
     rng = np.random.default_rng(6)
-    n = 16
     rho = 0.8 + 0.05 * rng.uniform(-1, 1, (n, n, n))
     vel = [0.03 * rng.standard_normal((n, n, n)) for _ in range(3)]
     prm = dict(kind="pfc", dim=3, h=0.9, dt=0.02, alpha=0.6, tol=1e-12)
