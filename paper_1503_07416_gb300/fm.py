@@ -203,6 +203,27 @@ def fm_step_host(st, dt, rho_in, vel_in, rho_out, vel_out):
     return code, info
 
 
+class HostStepper:
+    """Repeated fm_step_host calls on the same host buffers (see
+    Solver.host_stepper).  The buffers must stay alive and unmoved; the
+    returned fm_step_info is overwritten by the next call."""
+
+    def __init__(self, sol, rho_in, vel_in, rho_out, vel_out):
+        arrs = [rho_in, *vel_in, rho_out, *vel_out]
+        for a in arrs:
+            if _ptr(a)[1] != FM_HOST:
+                raise ValueError("fm_step_host takes host arrays")
+        self._keep = arrs
+        self._handle = sol.handle
+        self._args = (C.c_void_p(_ptr(rho_in)[0]), _vec(vel_in), C.c_void_p(_ptr(rho_out)[0]), _vec(vel_out))
+        self._info = fm_step_info()
+        self._fn = lib().fm_step_host
+
+    def __call__(self, dt):
+        _check(self._fn(self._handle, C.c_double(dt), *self._args, C.byref(self._info)), "fm_step_host")
+        return self._info
+
+
 def fm_step_raw(st, dt):
     """fm_step returning (code, info) without raising."""
     info = fm_step_info()
@@ -481,6 +502,11 @@ class Solver:
         code, info = fm_step_host(self.handle, dt, rho_in, vel_in, rho_out, vel_out)
         _check(code, "fm_step_host")
         return info
+
+    def host_stepper(self, rho_in, vel_in, rho_out, vel_out):
+        """fm_step_host on fixed host buffers, checked and marshalled once:
+        the returned callable takes dt and makes one C call per step."""
+        return HostStepper(self, rho_in, vel_in, rho_out, vel_out)
 
     def energy(self):
         return fm_energy(self.handle)

@@ -511,3 +511,34 @@ def test_step_host_equals_set_step_get(precision):
     assert np.isnan(ro[5, 7]) and np.array_equal(vo[0], vb[0])
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_host_stepper_equals_step_host(precision):
+    """Solver.host_stepper (buffers checked and marshalled once, one C call
+    per step, the outputs copied back into the inputs between steps) gives
+    the same bits as step_host on fresh arrays, three steps in a row, and
+    rejects device tensors."""
+    rho, vel, prm = inputs.pfc_supercooled(128, seed=29)
+    a = gpu_solver(rho, prm, precision=precision, w_damp=0.0)
+    b = gpu_solver(rho, prm, precision=precision, w_damp=0.0)
+    ri, vi = rho.copy(), [v.copy() for v in vel]
+    ro, vo = np.empty_like(ri), [np.empty_like(v) for v in vi]
+    stepper = b.host_stepper(ri, vi, ro, vo)
+    ra, va = rho.copy(), [v.copy() for v in vel]
+    for _ in range(3):
+        out_r, out_v = np.empty_like(ra), [np.empty_like(v) for v in va]
+        ia = a.step_host(prm["dt"], ra, va, out_r, out_v)
+        ra, va = out_r, out_v
+        ib = stepper(prm["dt"])
+        assert ia.cycles == ib.cycles
+        assert np.array_equal(ra, ro) and all(np.array_equal(x, y) for x, y in zip(va, vo))
+        ri[...] = ro
+        for x, y in zip(vi, vo):
+            x[...] = y
+    torch = pytest.importorskip("torch")
+    d = torch.zeros(rho.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        b.host_stepper(d, vi, ro, vo)
+    a.close()
+    b.close()
