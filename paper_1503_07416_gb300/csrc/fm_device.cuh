@@ -1585,10 +1585,44 @@ __device__ __forceinline__ void norm_add(void* f0, double r, double& acc, float&
   }
   acc += r * r;
 }
+// Block partial sums of the stopping test: from the float32 sums (fa) when
+// the float32-rounded residual was summed (mixed cycle: f0 given, T float;
+// the tree stays in float32 and each block's result is widened once),
+// otherwise from the float64 sums (acc).  `f0` is the same for the whole
+// launch, so the branch is uniform.
 template <int NQ>
-__device__ __forceinline__ void norm_finish(double (&acc)[NQ], const float (&fa)[NQ]) {
+__device__ __forceinline__ void block_partials_f(float (&v)[NQ], double* partials, int blk) {
+  __shared__ float sm[NQ][TPB];
+  const int tid = threadIdx.x, lane = tid & 31;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) acc[q] += widen(fa[q]);
+  for (int q = 0; q < NQ; ++q) sm[q][tid] = v[q];
+  __syncthreads();
+#pragma unroll
+  for (int s = TPB / 2; s >= 32; s >>= 1) {
+    if (tid < s)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) sm[q][tid] += sm[q][tid + s];
+    __syncthreads();
+  }
+  if (tid < 32) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      float x = sm[q][lane];
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      if (lane == 0) partials[blk * NQ + q] = widen(x);
+    }
+  }
+}
+template <typename T, int NQ>
+__device__ __forceinline__ void norm_partials(const void* f0, double (&acc)[NQ], float (&fa)[NQ], double* partials,
+                                              int blk) {
+  if constexpr (sizeof(T) == 4) {
+    if (f0) {
+      block_partials_f<NQ>(fa, partials, blk);
+      return;
+    }
+  }
+  block_partials<NQ>(acc, partials, blk);
 }
 
 struct Resid64Out {
@@ -1679,8 +1713,7 @@ __device__ __forceinline__ void resid64_body(const Fields64& F, const Resid64Out
       for (int d = 0; d < DIM; ++d) O.cv32[d][idx] = narrow_rn(uc[d]);
     }
   }
-  norm_finish<LY::NU>(acc, fa);
-  block_partials<LY::NU>(acc, partials, lb);
+  norm_partials<T, LY::NU>(O.f0[0], acc, fa, partials, lb);
 }
 
 // 2-D float64 residual in 32 x 8 tiles: the quantities every point shares
@@ -1778,8 +1811,7 @@ __device__ __forceinline__ void resid64_tile_body(const Fields64& F, const Resid
     }
     __syncthreads();
   }
-  norm_finish<LY::NU>(acc, fa);
-  block_partials<LY::NU>(acc, partials, lb);
+  norm_partials<T, LY::NU>(O.f0[0], acc, fa, partials, lb);
 }
 
 template <int KIND, typename T>
@@ -1876,8 +1908,7 @@ __global__ void __launch_bounds__(TPB) k_resid64_x(Fields64 F, Shared64 X, Resid
       for (int d = 0; d < DIM; ++d) O.cv32[d][idx] = narrow_rn(uc[d]);
     }
   }
-  norm_finish<LY::NU>(acc, fa);
-  block_partials<LY::NU>(acc, partials, blockIdx.x);
+  norm_partials<T, LY::NU>(O.f0[0], acc, fa, partials, blockIdx.x);
 }
 
 template <int KIND, int DIM, typename T>
