@@ -346,7 +346,8 @@ def run_ours(args):
             "l2": "flushed (256 MiB write) between timed steps, flush untimed",
             "cycles_per_step_mean": round(statistics.mean(mix["cycles"]), 3),
             "multigrid": {"cycle": "V(2,2)", "levels": "512^2 .. 64^2 (4)", "coarsest_sweeps": 2,
-                          "coarse_solve": "single-block kernel"},
+                          "coarse_solve": "2 fused red-black sweeps of the 64^2 grid (multi-block, two sweeps "
+                                          "per launch)"},
             "parallelism": f"{world} independent instance(s), one per GPU",
             "fp64_path": {
                 "value": round(world * steps / (f64["total_ms"] / 1e3), 3),
