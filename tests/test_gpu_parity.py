@@ -542,3 +542,19 @@ def test_host_stepper_equals_step_host(precision):
         b.host_stepper(d, vi, ro, vo)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("nu", [(2, 2), (1, 2)])
+@pytest.mark.parametrize("variant", [18, 24])
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_two_sweep_smoother_in_the_cycle_cdft(precision, variant, nu, monkeypatch):
+    """The non-local functional with two-sweep launches on every level (the
+    correction left in the second buffer between pre- and post-smoothing,
+    V(2,2), or copied back, V(1,2)): 64^2 CDFT with the 256^2 physics, two
+    steps against the oracle."""
+    monkeypatch.setenv("FM_RB_VARIANT", str(variant))
+    rho, vel, prm = inputs.cdft256(n=64)
+    prm = dict(prm, h=17.0 / 128)
+    rng = np.random.default_rng(9)
+    vel = [0.02 * rng.standard_normal(rho.shape) for _ in range(2)]
+    _compare_step(rho, vel, prm, precision, steps=2, nu1=nu[0], nu2=nu[1])
