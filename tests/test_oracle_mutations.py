@@ -22,6 +22,28 @@ def _flipped_cross(om, U):
     return [-x for x in _orig["omega_cross"](om, U)]
 
 
+def _flipped_cross_3d(om, U):
+    # the consistent 3-D analogue of sigma = -1: only the 3-D branch negated
+    out = _orig["omega_cross"](om, U)
+    return [-x for x in out] if len(U) == 3 else out
+
+
+def _swapped_cross_3d(om, U):
+    # one slot of the 3-D cross product with its operands exchanged
+    out = _orig["omega_cross"](om, U)
+    if len(U) == 3:
+        out[1] = om[0] * U[2] - om[2] * U[0]
+    return out
+
+
+def _curl_x_flipped(vel, h):
+    # the x-component of the 3-D centred curl with the wrong sign
+    out = _orig["vorticity"](vel, h)
+    if len(vel) == 3:
+        out[0] = -out[0]
+    return out
+
+
 def _forward_div(F, h):
     return sum((S.sh(F[d], d, 1) - F[d]) / h for d in range(len(F)))
 
@@ -45,7 +67,13 @@ def _ce_unweighted(shape, h, nu):
 
 
 _orig = {k: getattr(S, k) for k in ("lap", "omega_cross", "div0", "restrict_fw",
-                                    "pfc_energy_terms", "closure", "cdft_setup")}
+                                    "pfc_energy_terms", "closure", "cdft_setup", "vorticity")}
+
+
+def _all_3d_shears():
+    for a, b in pins.SHEAR_3D:
+        pins.test_3d_shear_flow_generates_no_cross_flow(a, b)
+
 
 MUTATIONS = [
     ("lap", _garbled_lap, [lambda: pins.test_stencil_symbols()]),
@@ -55,10 +83,16 @@ MUTATIONS = [
     ("pfc_energy_terms", _quartic_wrong, [pins.test_pfc_energy_of_a_mode]),
     ("closure", _closure_no_half, [lambda: pins.test_mass_energy_and_kinetic_identity("pfc")]),
     ("cdft_setup", _ce_unweighted, [pins.test_ce_closed_form]),
+    ("omega_cross", _flipped_cross_3d, [_all_3d_shears]),
+    ("omega_cross", _swapped_cross_3d, [_all_3d_shears]),
+    ("vorticity", _curl_x_flipped, [_all_3d_shears]),
 ]
 
+IDS = ["lap", "omega_cross", "div0", "restrict_fw", "pfc_energy_terms", "closure", "cdft_setup",
+       "omega_cross_3d_negated", "omega_cross_3d_slot_swapped", "curl_3d_x_negated"]
 
-@pytest.mark.parametrize("name,fn,checks", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+
+@pytest.mark.parametrize("name,fn,checks", MUTATIONS, ids=IDS)
 def test_pins_catch_planted_mistake(monkeypatch, name, fn, checks):
     monkeypatch.setattr(S, name, fn)
     caught = 0
@@ -68,3 +102,52 @@ def test_pins_catch_planted_mistake(monkeypatch, name, fn, checks):
         except (AssertionError, S.NoConvergence, np.linalg.LinAlgError, FloatingPointError):
             caught += 1
     assert caught == len(checks), f"planted mistake in {name} not caught"
+
+
+# ---------------------------------------------------------------- gradient flow
+from oracle import gradflow as G  # noqa: E402
+import tests.test_oracle_gradflow as gpins  # noqa: E402
+
+_gorig = {k: getattr(G, k) for k in ("explicit_mu", "closure", "apply_N")}
+
+
+def _explicit_sign(rk, P, C=None):
+    return -_gorig["explicit_mu"](rk, P, C)
+
+
+def _closure_minus(g, rk, P, Emu=None):
+    rho = rk - P.s * S.lap(G.mu_of(g, P, Emu), P.h)
+    return np.sqrt(rho * rho + P.delta * P.delta)
+
+
+def _cubic_unscaled(g, P):
+    out = _gorig["apply_N"](g, P)
+    if P.kind == S.PFC:
+        psi = g[0] - 1.5
+        out[1] = out[1] - (2.0 / 3.0) * psi ** 3
+    return out
+
+
+def _gf_modes():
+    for kind in ("pfc", "cdft"):
+        gpins.test_linearised_single_mode_step(kind, 0)
+
+
+G_MUTATIONS = [
+    ("explicit_mu", _explicit_sign, [_gf_modes]),
+    ("closure", _closure_minus, [_gf_modes, lambda: gpins.test_mass_and_thm33_energy_bound("pfc")]),
+    ("apply_N", _cubic_unscaled, [lambda: gpins.test_linearised_single_mode_step("pfc", 1)]),
+]
+
+
+@pytest.mark.parametrize("name,fn,checks", G_MUTATIONS, ids=["gf_explicit_sign", "gf_closure_sign",
+                                                             "gf_cubic_weight"])
+def test_gradflow_pins_catch_planted_mistake(monkeypatch, name, fn, checks):
+    monkeypatch.setattr(G, name, fn)
+    caught = 0
+    for chk in checks:
+        try:
+            chk()
+        except (AssertionError, S.NoConvergence, np.linalg.LinAlgError, FloatingPointError):
+            caught += 1
+    assert caught == len(checks), f"planted mistake in gradflow.{name} not caught"

@@ -273,6 +273,60 @@ def test_shear_flow_generates_no_cross_flow():
     assert out[1.0] < 0.05 * scale
 
 
+SHEAR_3D = [(0, 1), (1, 0), (0, 2), (2, 0), (1, 2), (2, 1)]
+
+
+@pytest.mark.parametrize("a,b", SHEAR_3D)
+def test_3d_shear_flow_generates_no_cross_flow(a, b):
+    """3-D analogue of the shear pin (Sec. 4 identity u.grad u = omega x u +
+    grad|u|^2/2, Eq. discrete_b): u_a = V cos(k x_b), the other components
+    zero, has u.grad u = 0.  Its centred curl has one component, along the
+    third axis, and omega x u points along x_b, where grad|u|^2/2 cancels it
+    only with the vector-form sign.  The six (a, b) pairs exercise every
+    component of the 3-D curl and every slot of the cross product; a sign
+    error in any of them drives a cross flow of the s V^2 k scale."""
+    n, h, s, V = 16, 0.5, 0.01, 1e-3
+    rb = 1.5 - 0.07 * math.sqrt(3)
+    k = 2 * math.pi / (n * h)
+    shape = (n, n, n)
+    bshape = [1, 1, 1]
+    bshape[2 - b] = n
+    prof = V * np.cos(k * np.arange(n) * h).reshape(bshape) * np.ones(shape)
+    out = {}
+    for sig in (1.0, -1.0):
+        P = S.Params(kind=S.PFC, dim=3, h=h, s=s, alpha=0.975, sigma=sig)
+        vel = [np.zeros(shape) for _ in range(3)]
+        vel[a] = prof.copy()
+        _, v1, _ = S.step(np.full(shape, rb), vel, P, S.SolverOpts(tol=1e-12, coarsest=2))
+        out[sig] = max(float(np.max(np.abs(v1[c]))) for c in range(3) if c != a)
+    scale = s * V * V * k
+    assert out[-1.0] > 0.5 * scale, out
+    assert out[1.0] < 0.1 * scale, out
+
+
+def test_3d_kinetic_energy_identity():
+    """The exact discrete identity of App. F in 3-D:
+    KE^{k+1} - KE^k + (rho^{k+1} - rho^k || mu^{k+1}) + s gamma D = 0, with D
+    the edge norms of all nine differences D_d u_c of u^{k+1/2}; the energy
+    drop is at least s gamma D."""
+    n = 8
+    rng = np.random.default_rng(19)
+    rho = 0.8 + 0.05 * rng.uniform(-1, 1, (n, n, n))
+    vel = [0.05 * rng.standard_normal((n, n, n)) for _ in range(3)]
+    P = S.Params(kind=S.PFC, dim=3, h=0.9, s=0.02, alpha=0.6)
+    for _ in range(2):
+        E0, _, K0 = S.energy(rho, vel, P)
+        r1, v1, info = S.step(rho, vel, P, S.SolverOpts(tol=1e-13, coarsest=2))
+        E1, _, K1 = S.energy(r1, v1, P)
+        mu = info["g"][4]
+        uh = [0.5 * (x + y) for x, y in zip(v1, vel)]
+        D = S.edge_dissipation(uh, P.h)
+        ident = K1 - K0 + S.inner(r1 - rho, mu, P.h) + P.s * P.gamma * D
+        assert abs(ident) < 1e-10 * max(1.0, abs(E0)), ident
+        assert E1 - E0 <= -P.s * P.gamma * D + 1e-10
+        rho, vel = r1, v1
+
+
 @pytest.mark.parametrize("kind", ["pfc", "cdft"])
 def test_uniform_state_is_a_fixed_point(kind):
     """rho = rho_bar, u = 0 makes every difference vanish: zero V-cycles and
