@@ -47,7 +47,9 @@ extern "C" {
 #define FM_ENOMEM   (-2)  /* device allocation failed */
 #define FM_ECUDA    (-3)  /* a CUDA runtime call failed */
 #define FM_ENOCONV  (-4)  /* residual above tol after max_cycles V-cycles */
-#define FM_ENONPOS  (-5)  /* non-positive density reached ln (CDFT, delta = 0) */
+#define FM_ENONPOS  (-5)  /* CDFT: a density <= 0 where ln rho is needed -- an input
+                             rho^k <= 0, or (delta = 0, no projection floor) an
+                             update that left rho <= 0; the state is unchanged */
 #define FM_ENAN     (-6)  /* non-finite residual */
 
 #define FM_PFC   1        /* local phase-field-crystal functional, Sec. 2.2 / 5.3 */
@@ -126,8 +128,8 @@ int fm_get_fields(fm_state* st, double* rho, double* const* vel, int where);
 /* Advance one time step of size dt (the paper's s) with FAS V(nu1, nu2)
  * cycles until the float64 residual norm is <= tol, then re-evaluate
  * rho^{k+1} from the continuity equation with the final velocity (mass exact
- * to round-off) and project.  info may be null.  FM_ENOCONV / FM_ENAN leave
- * the state unchanged. */
+ * to round-off) and project.  info may be null.  FM_ENOCONV / FM_ENAN /
+ * FM_ENONPOS leave the state unchanged. */
 int fm_step(fm_state* st, double dt, fm_step_info* info);
 
 /* One step for a caller that keeps the fields in host memory: copies rho_in
@@ -136,7 +138,8 @@ int fm_step(fm_state* st, double dt, fm_step_info* info);
  * the state's stream and copies the new rho and velocity to rho_out and
  * vel_out (host), with a single host synchronisation at the end.  The same
  * arithmetic as fm_set_fields + fm_step + fm_get_fields.  On FM_ENOCONV /
- * FM_ENAN the state and the outputs hold the inputs (time level k). */
+ * FM_ENAN / FM_ENONPOS the state and the outputs hold the inputs (time level
+ * k). */
 int fm_step_host(fm_state* st, double dt, const double* rho_in, const double* const* vel_in,
                  double* rho_out, double* const* vel_out, fm_step_info* info);
 
@@ -145,6 +148,18 @@ int fm_step_host(fm_state* st, double dt, const double* rho_in, const double* co
  * (Eq. CS_DFT_discrete); F and KE separately.  Float64 deterministic
  * reductions.  Any output pointer may be null. */
 int fm_energy(fm_state* st, double* E, double* F, double* KE);
+
+/* Components of the energy of the current state (the quantities the paper
+ * plots in its freezing and convergence figures, Sec. 6.1-6.2), float64
+ * deterministic reductions, into terms[0..4]:
+ *   terms[0] = KE = 1/2 (rho u || u);
+ *   PFC (Eq. CS_PFC_discrete): terms[1..4] = h^d sum psi^4/12,
+ *        h^d sum alpha psi^2/2, h^d sum (Lap_h rho)^2/2, h^d sum rho Lap_h rho
+ *        (psi = rho - 3/2; F is their sum);
+ *   CDFT (Eq. CS_DFT_discrete): terms[1] = F_id = (rho || ln rho - 1),
+ *        terms[2] = F_ex = -1/2 (rho || J * rho), terms[3] = terms[4] = 0.
+ * terms must hold 5 doubles (host memory).  Synchronises the state's stream. */
+int fm_energy_terms(fm_state* st, double* terms);
 
 /* Mass (rho || 1) = h^d sum rho (Thm 5.1). */
 int fm_mass(fm_state* st, double* M);

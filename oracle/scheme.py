@@ -43,7 +43,9 @@ R6  restriction = nodal full weighting, injection of the iterate, bilinear
     grid (the paper defers these to another reference).
 R7  damping applies to every unknown of the point block.
 R8  projection rho <- sqrt(rho^2 + delta^2) after each point update of rho and
-    after the step closure.
+    after the step closure; for delta > 0 (CDFT) also after the coarse-grid
+    correction, the other update of rho inside a cycle (Sec. 6 item 1 gives
+    the purpose: ln rho must never see a non-positive argument).
 R9  residual norm = max over components of sqrt(h^d * sum r^2).
 R10 step closure: after the solve, rho^{k+1} is re-evaluated from the
     continuity equation with the final velocity, so mass is exact to round-off.
@@ -507,6 +509,10 @@ def vcycle(g, f, c, P, opts):
     vcycle(gH, fH, cH, PH, opts)
     for i in range(len(g)):
         g[i] = g[i] + prolong(gH[i] - gH0[i])
+    if P.delta > 0.0:
+        # reading R8: the corrected density is projected before ln rho is
+        # evaluated on it again (Sec. 6 item 1)
+        g[0] = np.sqrt(g[0] * g[0] + P.delta * P.delta)
     for _ in range(opts.nu2):
         smooth(g, f, c, P, opts.ordering)
 

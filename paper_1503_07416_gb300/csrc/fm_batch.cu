@@ -67,7 +67,7 @@ __device__ __forceinline__ int find_item(const WorkItem* it, int n, int b) {
   return lo;
 }
 
-__device__ __forceinline__ bool inst_active(const Ctl* ctl, int inst) { return ctl[inst].pad[0] != 0; }
+__device__ __forceinline__ bool inst_active(const Ctl* ctl, int inst) { return ctl[inst].active != 0; }
 
 // Cooperative copy of a POD struct into shared memory.
 template <typename S>
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(TPB) kb_resid_restrict2(const WorkItem* items,
 
 template <typename T, int NU>
 __global__ void __launch_bounds__(TPB) kb_prolong(const WorkItem* items, int nitems, const InstDev<T>* D,
-                                                  const Ctl* ctl, int level, int fswap) {
+                                                  const Phys<T>* P, const Ctl* ctl, int level, int fswap) {
   FM_BATCH_HEAD();
   if (!inst_active(ctl, inst)) return;
   __shared__ Lvl<T> F, Cc;
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(TPB) kb_prolong(const WorkItem* items, int nit
   __syncthreads();
   lvl_swap_er(F, fswap);
   const int idx = lb * TPB + threadIdx.x;
-  if (idx < F.g.N) prolong_point<T, NU, 2>(F, Cc, idx);
+  if (idx < F.g.N) prolong_point<T, NU, 2>(F, Cc, P[inst], idx);
 }
 
 // one block per instance
@@ -295,12 +295,15 @@ __global__ void kb_norm(const InstDev<T>* D, Ctl* ctl, double tol, int max_cycle
   const InstDev<T>& I = D[inst];
   const double w = I.h0 * I.h0;
   const bool cont = norm_ctl_body<NQ>(I.partials, I.nblk64, w, &ctl[inst], tol, max_cycles, in_body);
-  if (threadIdx.x == 0) ctl[inst].pad[0] = cont ? 1 : 0;
+  if (threadIdx.x == 0) ctl[inst].active = cont ? 1 : 0;
 }
 
 __global__ void kb_set_active(Ctl* ctl, int count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) ctl[i].pad[0] = 1;
+  if (i < count) {
+    ctl[i].active = 1;
+    ctl[i].nonpos = 0;
+  }
 }
 
 __global__ void kb_condition(const Ctl* ctl, int count, cudaGraphConditionalHandle handle) {
@@ -308,7 +311,7 @@ __global__ void kb_condition(const Ctl* ctl, int count, cudaGraphConditionalHand
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < count; i += blockDim.x)
-    if (ctl[i].pad[0]) atomicOr(&any, 1);
+    if (ctl[i].active) atomicOr(&any, 1);
   __syncthreads();
   if (threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
 }
@@ -731,7 +734,7 @@ struct Batch {
     for (int l = b->maxdepth - 1; l >= 0; --l) {
       const WList& wp = b->w_prolong[l];
       if (wp.n == 0) continue;
-      kb_prolong<T, LY::NU><<<wp.nblocks, TPB, 0, s>>>(it(b, wp), wp.n, D, b->ctl, l, in_r[l]);
+      kb_prolong<T, LY::NU><<<wp.nblocks, TPB, 0, s>>>(it(b, wp), wp.n, D, P, b->ctl, l, in_r[l]);
       FMB_LAUNCHED();
       int rc = smooth(b, l, b->prm.nu2, &in_r[l]);
       if (rc) return rc;
@@ -769,6 +772,8 @@ struct Batch {
         if (rc) return rc;
       }
     }
+    kb_set_active<<<(b->count + 255) / 256, 256, 0, s>>>(b->ctl, b->count);  // clears the flags
+    FMB_LAUNCHED();
     const WList& w = b->w_fine;
     kb_prepare<T, KIND><<<w.nblocks, TPB, 0, s>>>(it(b, w), w.n, D, b->P64, b->K64);
     FMB_LAUNCHED();
@@ -891,6 +896,9 @@ struct Batch {
     b->K64 = (Step64*)p; p += al(szK64);
     b->ctl = (Ctl*)p; p += al(szC);
     b->items = (WorkItem*)p;
+    // the non-positive-density flag of an instance lives in the batch's
+    // control block, not in the instance's own
+    for (int i = 0; i < b->count; ++i) H[i].F.nonpos = KIND == KCDFT ? &b->ctl[i].nonpos : nullptr;
     FMB_CUDA(cudaMemcpy(b->D, H.data(), szD, cudaMemcpyHostToDevice));
     if (!b->hitems.empty())
       FMB_CUDA(cudaMemcpy(b->items, b->hitems.data(), sizeof(WorkItem) * b->hitems.size(), cudaMemcpyHostToDevice));

@@ -30,7 +30,19 @@ struct PtK {
   T c_v;    // s gamma/(2h^2): viscous neighbour sum
   T c_ad;   // s gamma d/h^2: viscous diagonal (reading R2)
   T c_b;    // sigma s/2: vorticity coupling (times rho^k omega^k)
+  T proj;   // positive projection applied where rho <= proj (see proj_threshold)
 };
+
+// The positive projection rho <- sqrt(rho^2 + delta^2) of Sec. 6 changes a
+// density x >= delta * sqrt(2 / eps_T) by less than a quarter of its last
+// bit, so above that threshold it is the identity in precision T; below it
+// (and wherever x <= 0) it is applied.  This gives the projection applied at
+// every density update, up to rounding, while the correction e keeps its
+// full relative precision where the projection cannot show.
+template <typename T>
+__host__ __device__ __forceinline__ T proj_threshold(T delta) {
+  return delta * (sizeof(T) == 4 ? T(8192) : T(134217728));  // 2^13 ~ sqrt(2/2^-24), 2^27 ~ sqrt(2/2^-53)
+}
 
 template <typename T, int DIM>
 __device__ __forceinline__ PtK<T> make_ptk(const Phys<T>& P, T h) {
@@ -42,6 +54,7 @@ __device__ __forceinline__ PtK<T> make_ptk(const Phys<T>& P, T h) {
   K.c_v = T(0.5) * P.s * P.gamma * K.ih2;
   K.c_ad = P.s * P.gamma * T(DIM) * K.ih2;
   K.c_b = T(0.5) * P.sigma * P.s;
+  K.proj = proj_threshold<T>(P.delta);
   return K;
 }
 
@@ -76,7 +89,7 @@ __device__ __forceinline__ void smooth_point_a(const A& a, const Phys<T>& P, con
   T er = a.f(0, fc) - K.c_div * div;
   {
     const T x = crc + er;
-    if (x <= T(0)) er = sqrt_t(x * x + P.delta * P.delta) - crc;  // Sec. 6 projection
+    if (x <= K.proj) er = sqrt_t(x * x + P.delta * P.delta) - crc;  // Sec. 6 projection
   }
   T eg[LY::NU];
   eg[0] = er;
@@ -251,8 +264,11 @@ __device__ __forceinline__ void coarse_rhs_point(const Lvl<T>& L, const Phys<T>&
 }
 
 // fine point idx: e_F += P(e_C - eh_C)  (bilinear / trilinear)
+// e_F += P(e_C - eh_C) at fine point idx; for delta > 0 (the CDFT case,
+// where ln rho needs a positive argument) the corrected density c + e is then
+// projected as in the smoother (Sec. 6, item 1).
 template <typename T, int NU, int DIM>
-__device__ __forceinline__ void prolong_point(const Lvl<T>& F, const Lvl<T>& C, int idx) {
+__device__ __forceinline__ void prolong_point(const Lvl<T>& F, const Lvl<T>& C, const Phys<T>& P, int idx) {
   int i, j, k;
   coords(idx, F.g, i, j, k);
   int xi[2], yi[2], zi[2];
@@ -283,6 +299,11 @@ __device__ __forceinline__ void prolong_point(const Lvl<T>& F, const Lvl<T>& C, 
           acc += C.e[q][ci] - C.eh[q][ci];
         }
     ev[q] = F.e[q][idx] + w * acc;
+  }
+  if (P.delta > T(0)) {
+    const T c = F.cr[idx];
+    const T x = c + ev[0];
+    if (x <= proj_threshold<T>(P.delta)) ev[0] = sqrt_t(x * x + P.delta * P.delta) - c;
   }
 #pragma unroll
   for (int q = 0; q < NU; ++q) F.e[q][idx] = ev[q];
@@ -426,9 +447,9 @@ __global__ void __launch_bounds__(TPB) k_coarse_rhs(Lvl<T> L, Phys<T> P) {
 }
 
 template <typename T, int NU, int DIM>
-__global__ void __launch_bounds__(TPB) k_prolong(Lvl<T> F, Lvl<T> C) {
+__global__ void __launch_bounds__(TPB) k_prolong(Lvl<T> F, Lvl<T> C, Phys<T> P) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < F.g.N) prolong_point<T, NU, DIM>(F, C, idx);
+  if (idx < F.g.N) prolong_point<T, NU, DIM>(F, C, P, idx);
 }
 
 // Fused red-black sweep of a 2-D level in TX x TY tiles.  The tile and a
@@ -1064,7 +1085,7 @@ __device__ __forceinline__ void vcycle_small_body(const SmallLv<T>& S, const Phy
   for (int l = nl - 2; l >= 0; --l) {
     const Lvl<T>& F = S.lv[l];
     const Lvl<T>& C = S.lv[l + 1];
-    for (int idx = threadIdx.x; idx < F.g.N; idx += blockDim.x) prolong_point<T, LY::NU, DIM>(F, C, idx);
+    for (int idx = threadIdx.x; idx < F.g.N; idx += blockDim.x) prolong_point<T, LY::NU, DIM>(F, C, P, idx);
     __syncthreads();
     block_smooth<T, KIND, DIM>(F, P, nu2);
   }
@@ -1143,7 +1164,7 @@ __device__ __forceinline__ void group_up(const Lvl<T>& F, const Lvl<T>& C, const
   using LY = Layout<KIND, DIM>;
   const int tid = WARP ? (threadIdx.x & 31) : threadIdx.x;
   const int nth = WARP ? 32 : blockDim.x;
-  for (int idx = tid; idx < F.g.N; idx += nth) prolong_point<T, LY::NU, DIM>(F, C, idx);
+  for (int idx = tid; idx < F.g.N; idx += nth) prolong_point<T, LY::NU, DIM>(F, C, P, idx);
   group_sync<T, KIND, DIM, WARP>();
   group_smooth<T, KIND, DIM, WARP>(F, P, nu2);
 }
@@ -1386,6 +1407,7 @@ struct Fields64 {
   double* g[MAXU];            // iterate
   float* rk32;                // float copies for the mixed path (or null)
   float* om32[3];
+  int* nonpos;                // CDFT: set to 1 where a density <= 0 would reach ln (or null)
 };
 
 // omega^k, S and the initial iterate g^0 (kappa^0 = Lap_h rho^k for PFC).
@@ -1410,6 +1432,9 @@ __device__ __forceinline__ void prepare_point(const Fields64& F, const Geo& G, c
     w[2] = K.hih * ((v[n.p[0]] - v[n.m[0]]) - (u[n.p[1]] - u[n.m[1]]));
   }
   const double rkc = F.rho[n.c];
+  if constexpr (KIND == KCDFT) {
+    if (F.nonpos && rkc <= 0.0) atomicOr(F.nonpos, 1);  // ln rho^k undefined: FM_ENONPOS
+  }
   double div = 0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d)
@@ -1938,6 +1963,7 @@ __device__ __forceinline__ void update64_point(const Fields64& F, const Resid64O
 #pragma unroll
   for (int q = 0; q < NU; ++q) gv[q] += from_t<T>(ev[q]);
   gv[0] = (delta > 0.0) ? sqrt(gv[0] * gv[0] + delta * delta) : fabs(gv[0]);
+  if (F.nonpos && gv[0] <= 0.0) atomicOr(F.nonpos, 1);  // CDFT, delta = 0: ln 0 next
 #pragma unroll
   for (int q = 0; q < NU; ++q) F.g[q][idx] = gv[q];
 }
@@ -1954,7 +1980,8 @@ struct Ctl {
   double norm0;
   int cycles;
   int status;
-  int pad[2];
+  int active;   // batch: the instance still iterates
+  int nonpos;   // CDFT: a density <= 0 reached ln this step (FM_ENONPOS)
 };
 
 // Finishes the residual norm max_q sqrt(w * sum_q), updates the control
@@ -1995,7 +2022,8 @@ __device__ __forceinline__ bool norm_ctl_body(const double* partials, int nblk, 
     ctl->norm = nrm;
     if (!in_body) ctl->norm0 = nrm;
     int status = FM_OK;
-    if (!finite) status = FM_ENAN;
+    if (ctl->nonpos) status = FM_ENONPOS;
+    else if (!finite) status = FM_ENAN;
     else if (nrm > tol && cycles >= max_cycles) status = FM_ENOCONV;
     ctl->status = status;
     return status == FM_OK && nrm > tol;
@@ -2167,6 +2195,7 @@ static Fields64 make_fields(fm_state* st) {
     F.g[q] = st->g[q];
   }
   F.rk32 = nullptr;
+  F.nonpos = st->kind == FM_CDFT ? &static_cast<Ctl*>(st->ctl)->nonpos : nullptr;
   if (st->prm.precision == FM_MIXED) {
     F.rk32 = (float*)st->lv[0].rk;
     for (int d = 0; d < st->nom; ++d) F.om32[d] = (float*)st->lv[0].om[d];

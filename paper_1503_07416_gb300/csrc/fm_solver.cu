@@ -376,6 +376,7 @@ struct Solver {
     Phys<double> P = make_phys<double>(st);
     cudaStream_t s = st->stream;
     if (KIND == KCDFT) {
+      FM_CUDA(cudaMemsetAsync(&static_cast<Ctl*>(st->ctl)->nonpos, 0, sizeof(int), s));
       int rc = fft_convolve(st, st->rho, st->conv);
       if (rc) return rc;
     }
@@ -606,7 +607,7 @@ struct Solver {
     int c_in_r = 0;
     rc = vcycle(st, l + 1, P, &c_in_r);
     if (rc) return rc;
-    k_prolong<T, LY::NU, DIM><<<nblocks(F.g.N), TPB, 0, s>>>(F, c_in_r ? swap_er(C) : C);
+    k_prolong<T, LY::NU, DIM><<<nblocks(F.g.N), TPB, 0, s>>>(F, c_in_r ? swap_er(C) : C, P);
     FM_LAUNCHED();
     rc = smooth(st, l, P, st->prm.nu2, &in_r);
     if (rc) return rc;
@@ -780,7 +781,7 @@ struct Solver {
       rc = FM_OK;
     } else {
       rc = step_hostloop(st, nullptr);  // synchronises; status read below
-      if (rc != FM_OK && rc != FM_ENOCONV && rc != FM_ENAN) return rc;
+      if (rc != FM_OK && rc != FM_ENOCONV && rc != FM_ENAN && rc != FM_ENONPOS) return rc;
     }
     FM_CUDA(cudaMemcpyAsync(rho_out, st->rho, bytes, cudaMemcpyDeviceToHost, st->stream));
     for (int d = 0; d < DIM; ++d)
@@ -1274,8 +1275,9 @@ int fm_widen(const float* in, double* out, long long n, void* stream) {
   return FM_OK;
 }
 
-int fm_energy(fm_state* st, double* E, double* F, double* KE) {
-  if (!st) return FM_EINVAL;
+// Weighted energy sums of the current state into q[0..4]: KE, then the PFC
+// terms or F_id, F_ex (CDFT; q[3] = q[4] = 0).
+static int energy_sums(fm_state* st, double* q) {
   const Geo G = st->lv[0].g;
   const double h = st->lv[0].h;
   cudaStream_t s = st->stream;
@@ -1299,13 +1301,25 @@ int fm_energy(fm_state* st, double* E, double* F, double* KE) {
   FM_CUDA(cudaMemcpyAsync(st->hscal + 8, st->dscal + 8, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
   FM_CUDA(cudaStreamSynchronize(s));
   const double w = st->dim == 3 ? h * h * h : h * h;
-  const double* q = st->hscal + 8;
-  const double ke = w * q[0];
-  const double f = w * (q[1] + q[2] + q[3] + q[4]);
-  if (E) *E = ke + f;
-  if (F) *F = f;
-  if (KE) *KE = ke;
+  for (int t = 0; t < 5; ++t) q[t] = w * st->hscal[8 + t];
   return FM_OK;
+}
+
+int fm_energy(fm_state* st, double* E, double* F, double* KE) {
+  if (!st) return FM_EINVAL;
+  double q[5];
+  const int rc = energy_sums(st, q);
+  if (rc) return rc;
+  const double f = q[1] + q[2] + q[3] + q[4];
+  if (E) *E = q[0] + f;
+  if (F) *F = f;
+  if (KE) *KE = q[0];
+  return FM_OK;
+}
+
+int fm_energy_terms(fm_state* st, double* terms) {
+  if (!st || !terms) return FM_EINVAL;
+  return energy_sums(st, terms);
 }
 
 int fm_mass(fm_state* st, double* M) {

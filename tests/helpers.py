@@ -34,3 +34,27 @@ def rel(a, b):
     nb = float(np.linalg.norm(b))
     d = float(np.linalg.norm(a - b))
     return d / nb if nb > 0 else d
+
+
+def maxrel(a, b):
+    """max |a - b| / max |b| (absolute when b vanishes): the element-wise
+    bound, which a single wrong point cannot hide under a whole-field norm."""
+    mb = float(np.max(np.abs(b)))
+    d = float(np.max(np.abs(a - b)))
+    return d / mb if mb > 0 else d
+
+
+def field_errors(rg, vg, ro, vo):
+    """Per field (rho, then each velocity component): (2-norm relative error,
+    element-wise relative error) of the GPU fields against the oracle's."""
+    pairs = [(rg, ro)] + list(zip(vg, vo))
+    return [(rel(a, b), maxrel(a, b)) for a, b in pairs]
+
+
+def assert_parity(rg, vg, ro, vo, bound, ctx=None):
+    """Both bounds per field: ||a - b||_2 <= bound ||b||_2 and
+    max |a - b| <= bound max |b|."""
+    errs = field_errors(rg, vg, ro, vo)
+    worst = max(max(e) for e in errs)
+    assert worst <= bound, (ctx, errs)
+    return worst

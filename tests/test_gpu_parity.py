@@ -15,7 +15,7 @@ import pytest
 
 from oracle import scheme as S
 from paper_1503_07416_gb300 import fm, inputs
-from tests.helpers import gpu_solver, oracle_setup, rel
+from tests.helpers import assert_parity, gpu_solver, oracle_setup, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -44,9 +44,7 @@ def _compare_step(rho, vel, prm, precision, tol=1e-12, w_damp=None, steps=1, bou
         rg, vg = sol.get_fields()
         ro, vo, oinfo = S.step(rho, vel, P, opts, J=J)
         assert info.res <= tol
-        errs = [rel(rg, ro)] + [rel(a, b) for a, b in zip(vg, vo)]
-        worst = max(worst, max(errs))
-        assert max(errs) <= bound, (errs, info.cycles, oinfo["cycles"])
+        worst = max(worst, assert_parity(rg, vg, ro, vo, bound, (info.cycles, oinfo["cycles"])))
         rho, vel = ro, vo
     sol.close()
     return worst
@@ -55,9 +53,10 @@ def _compare_step(rho, vel, prm, precision, tol=1e-12, w_damp=None, steps=1, bou
 # --------------------------------------------------------------- full steps
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
 def test_pfc64_steps(precision):
-    """2-D PFC 64x64 (L = 32, eps = 0.025, s = 0.01), 3 steps, per-step parity."""
+    """2-D PFC 64x64 (L = 32, eps = 0.025, s = 0.01), the workload's full 10
+    steps, per-step parity."""
     rho, vel, prm = inputs.pfc64()
-    _compare_step(rho, vel, prm, precision, steps=3)
+    _compare_step(rho, vel, prm, precision, steps=prm["steps"])
 
 
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
@@ -261,6 +260,68 @@ def test_full_size_pfc512_one_step(precision):
     _compare_step(rho, vel, prm, precision, tol=1e-11, w_damp=0.0, steps=1, **inputs.BENCH_MG_2D)
 
 
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_full_size_cdft256_two_steps(precision):
+    """The 256^2 CDFT workload at full size (h = 17/128, nu = 2.362, delta =
+    1e-10) in the configuration the benchmark times (undamped, the benchmark
+    hierarchy): two steps against the oracle, the convolution through the
+    hand-written FFT at full size."""
+    rho, vel, prm = inputs.cdft256()
+    _compare_step(rho, vel, prm, precision, tol=1e-13, w_damp=0.0, steps=2, **inputs.BENCH_MG_2D)
+
+
+@functools.lru_cache(maxsize=1)
+def _pfc3d128_reference():
+    """The 128^3 PFC workload and one oracle step of it (converged to 1e-11;
+    shared by both precisions)."""
+    rho, vel, prm = inputs.pfc3d128()
+    P, opts, J = oracle_setup(rho, prm, w_damp=0.0, tol=1e-11)
+    ro, vo, _ = S.step(rho, vel, P, opts, J=J)
+    return rho, vel, prm, ro, vo
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_full_size_pfc3d128_one_step(precision):
+    """The 3-D 128^3 PFC workload at full size (one spherical nucleus, s =
+    0.02, undamped, the library's 3-D hierarchy as the benchmark runs it): one
+    step against the oracle, whole fields, element by element."""
+    rho, vel, prm, ro, vo = _pfc3d128_reference()
+    sol = gpu_solver(rho, prm, precision=precision, w_damp=0.0, tol=1e-11)
+    sol.set_fields(rho, vel)
+    info = sol.step(prm["dt"])
+    rg, vg = sol.get_fields()
+    sol.close()
+    assert info.res <= 1e-11
+    assert_parity(rg, vg, ro, vo, TOL64 if precision == fm.FM_FP64 else TOLMIX, info.cycles)
+
+
+def _vacuum_blob(n, floor, seed=3):
+    """CDFT density with a near-vacuum region: a Gaussian blob (amplitude 0.5,
+    width L/8) on a floor, the sharp-peak-and-vacuum shape for which Sec. 6
+    introduces the projection; seeded small velocities."""
+    L = 17.0
+    h = L / n
+    x = np.arange(n) * h
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    r2 = (X - L / 2) ** 2 + (Y - L / 2) ** 2
+    rho = floor + 0.5 * np.exp(-r2 / (2 * (L / 8) ** 2))
+    rng = np.random.default_rng(seed)
+    vel = [0.01 * rng.standard_normal((n, n)) for _ in range(2)]
+    prm = dict(kind="cdft", dim=2, h=h, dt=0.02, nu=2.362, delta=1e-10, w_damp=0.5)
+    return rho, vel, prm
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_cdft_near_vacuum_steps(precision):
+    """CDFT with densities down to ~6e-8 between the blob and its periodic
+    images (ln rho ~ -16.7, where the projection of Sec. 6 changes rho by
+    delta^2 / (2 rho) and the damped smoother of App. G.3 is needed): two
+    steps against the oracle with the paper's damping w = 0.5."""
+    rho, vel, prm = _vacuum_blob(32, 1e-9)
+    assert rho.min() < 1e-7
+    _compare_step(rho, vel, prm, precision, tol=1e-12, w_damp=0.5, steps=2)
+
+
 # --------------------------------------------------------------- failure paths
 def test_no_convergence_leaves_state_unchanged():
     rho, vel, prm = inputs.pfc64()
@@ -280,6 +341,32 @@ def test_nan_input_reports_enan():
     sol.set_fields(rho, vel)
     code, _ = fm.fm_step_raw(sol.handle, prm["dt"])
     assert code == fm.FM_ENAN
+
+
+@pytest.mark.parametrize("delta", [1e-10, 0.0])
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_nonpositive_density_reports_enonpos(precision, delta):
+    """A CDFT state whose density is <= 0 somewhere cannot enter ln rho: the
+    step returns FM_ENONPOS (not FM_ENAN) and leaves the state unchanged,
+    with and without the projection floor; the flag does not outlive the
+    step (a valid state then steps normally on the same solver)."""
+    n = 32
+    rng = np.random.default_rng(21)
+    rho = 0.3 + 0.05 * rng.uniform(0, 1, (n, n))
+    vel = [0.02 * rng.standard_normal((n, n)) for _ in range(2)]
+    prm = dict(kind="cdft", dim=2, h=17.0 / 32, dt=0.02, nu=2.362, delta=delta)
+    sol = gpu_solver(rho, prm, precision=precision)
+    for bad_value in (0.0, -0.01):
+        bad = rho.copy()
+        bad[7, 11] = bad_value
+        sol.set_fields(bad, vel)
+        code, _ = fm.fm_step_raw(sol.handle, prm["dt"])
+        assert code == fm.FM_ENONPOS, (bad_value, code)
+        rg, vg = sol.get_fields()
+        assert np.array_equal(rg, bad) and all(np.array_equal(a, b) for a, b in zip(vg, vel))
+    sol.set_fields(rho, vel)
+    assert sol.step(prm["dt"]).res <= 1e-10
+    sol.close()
 
 
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
@@ -352,8 +439,7 @@ def test_two_sweep_smoother_in_the_cycle(precision, variant, nu, monkeypatch):
         sol.set_fields(rho, vel)
         assert sol.step(prm["dt"]).res <= tol
         rg, vg = sol.get_fields()
-        errs = [rel(rg, ro)] + [rel(a, b) for a, b in zip(vg, vo)]
-        assert max(errs) <= bound, errs
+        assert_parity(rg, vg, ro, vo, bound)
         rho, vel = ro, vo
     sol.close()
 
@@ -374,8 +460,7 @@ def test_large_coarsest_level_uses_fused_sweeps(precision, ncoarse):
         sol.set_fields(rho, vel)
         assert sol.step(prm["dt"]).res <= tol
         rg, vg = sol.get_fields()
-        errs = [rel(rg, ro)] + [rel(a, b) for a, b in zip(vg, vo)]
-        assert max(errs) <= bound, errs
+        assert_parity(rg, vg, ro, vo, bound)
         rho, vel = ro, vo
     sol.close()
 
