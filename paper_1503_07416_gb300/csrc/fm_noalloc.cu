@@ -79,8 +79,9 @@ extern "C" int fm_mass_noalloc(const double* rho, int dim, const int* n, double 
   if (!rho || !n || !out || (dim != 2 && dim != 3) || !(h > 0.0)) return FM_EINVAL;
   long long npts = 1;
   for (int d = 0; d < dim; ++d) {
-    if (n[d] < 1) return FM_EINVAL;
-    npts *= n[d];
+    if (n[d] < 1 || n[d] > FM_NOALLOC_MAX_POINTS) return FM_EINVAL;
+    npts *= n[d];  // at most FM_NOALLOC_MAX_POINTS^2 < 2^63: no overflow
+    if (npts > FM_NOALLOC_MAX_POINTS) return FM_EINVAL;  // checked before the next factor
   }
   const long long per_block = (long long)NA_THREADS * NA_PER_THREAD;
   const long long nblk = (npts + per_block - 1) / per_block;

@@ -75,6 +75,7 @@ _SIGS = {
     "fm_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                             C.POINTER(C.c_double)]),
     "fm_mass": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "fm_energy_terms": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "fm_strerror": (C.c_char_p, [C.c_int]),
     "fm_prepare": (C.c_int, [C.c_void_p, C.c_double]),
     "fm_get_aux": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]),
@@ -237,6 +238,14 @@ def fm_energy(st):
     return E.value, F.value, K.value
 
 
+def fm_energy_terms(st):
+    """[KE, then the PFC terms (quartic, quadratic, (Lap rho)^2/2, rho Lap rho)
+    or CDFT (F_id, F_ex, 0, 0)]."""
+    t = (C.c_double * 5)()
+    _check(lib().fm_energy_terms(st, t), "fm_energy_terms")
+    return list(t)
+
+
 def fm_mass(st):
     M = C.c_double()
     _check(lib().fm_mass(st, C.byref(M)), "fm_mass")
@@ -361,7 +370,20 @@ def fm_batch_time_sweep_variant(b, variant, iters):
 
 def fm_mass_noalloc(rho, h, out, stream=0):
     """Mass of a float64 CUDA tensor into a 1-element float64 CUDA tensor,
-    without any device allocation by the library (see include/fm.h)."""
+    without any device allocation by the library (see include/fm.h).
+
+    rho must be a contiguous float64 CUDA tensor with 2 or 3 dimensions and
+    out a float64 CUDA tensor with at least one element; anything else raises
+    ValueError before the C call (the kernel reads rho and writes out as
+    device float64 arrays)."""
+    import torch
+    for name, t in (("rho", rho), ("out", out)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+            raise ValueError(f"{name} must be a float64 CUDA tensor")
+    if rho.dim() not in (2, 3) or not rho.is_contiguous():
+        raise ValueError("rho must be a contiguous 2-D or 3-D tensor")
+    if out.numel() < 1:
+        raise ValueError("out must hold at least one element")
     dims = list(reversed(rho.shape))
     n = (C.c_int * 3)(*(dims + [1] * (3 - len(dims))))
     code = lib().fm_mass_noalloc(C.c_void_p(rho.data_ptr()), len(dims), n, C.c_double(h),
@@ -513,6 +535,9 @@ class Solver:
 
     def mass(self):
         return fm_mass(self.handle)
+
+    def energy_terms(self):
+        return fm_energy_terms(self.handle)
 
     def aux(self, what, comp):
         out = np.empty(self.shape)

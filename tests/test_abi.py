@@ -74,3 +74,28 @@ def test_null_handles_are_rejected(lib):
     assert L.fm_mass(None, None) == fm.FM_EINVAL
     assert L.fm_set_stream(None, None) == fm.FM_EINVAL
     L.fm_destroy(None)
+
+
+def test_mass_noalloc_rejects_oversized_grids_before_any_cuda_call(lib):
+    """Sizes whose product overflows 64 bits, or exceeds the static scratch,
+    are rejected by the host-side checks (the pointers are never touched)."""
+    L = fm.lib()
+    fake = C.c_void_p(0x1000)
+    for dims, n in ((3, (2 ** 31 - 1, 2 ** 31 - 1, 2 ** 31 - 1)), (2, (4096, 1025, 1)),
+                    (3, (1 << 20, 1 << 20, 4)), (2, (0, 8, 1))):
+        arr = (C.c_int * 3)(*n)
+        assert L.fm_mass_noalloc(fake, dims, arr, C.c_double(1.0), fake, None) == fm.FM_EINVAL
+
+
+def test_mass_noalloc_wrapper_checks_its_arguments(lib):
+    """The binding raises ValueError for host arrays, CPU tensors, float32
+    tensors and non-contiguous views before calling the library."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    out_cpu = torch.zeros(1, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        fm.fm_mass_noalloc(np.zeros((8, 8)), 1.0, out_cpu)
+    with pytest.raises(ValueError):
+        fm.fm_mass_noalloc(torch.zeros((8, 8), dtype=torch.float64), 1.0, out_cpu)
+    with pytest.raises(ValueError):
+        fm.fm_mass_noalloc(torch.zeros((8, 8), dtype=torch.float32), 1.0, out_cpu)
