@@ -39,6 +39,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "implicit steps/s at 512^2 (FP32-smoothed FAS, float64 residual 1e-10)"
+
+# Algorithmic float32 words per grid point of one smoother sweep (the method's
+# traffic): read the unknowns, the right-hand sides and the coefficients
+# rho^k, omega^k once, write the unknowns once.
+SWEEP_WORDS = {"pfc2d": 17, "cdft2d": 11, "pfc3d": 22}
 UNIT = "steps/s"
 WORKLOAD = "pfc512: 2-D PFC 512x512, eps=0.4, s=0.02, 4 nuclei, undamped, V(2,2) to 1e-10"
 
@@ -304,6 +309,12 @@ def run_ours(args):
     for r in results.values():
         r["sol"].close()
 
+    peak, peak_kind = load_peaks()
+    sec_batch = None
+    if not args.no_secondary:
+        # every rank steps its shard of the ensemble
+        sec_batch = secondary_batch48(torch, fm, inputs, flush, peak, dist=dist, rank=rank, world=world)
+
     if rank != 0:
         dist.destroy_process_group() if world > 1 else None
         return
@@ -312,7 +323,6 @@ def run_ours(args):
     steps = args.steps
     value = job_throughput(world, steps, mix["total_ms"])
     ms_per_step = mix["total_ms"] / steps
-    peak, peak_kind = load_peaks()
     # smoother roofline: one launch of the fused 2-D kernel runs one (or, for
     # the two-sweep variants, two) red-black sweeps of the finest level and
     # moves the same algorithmic bytes either way: 20 words/point x N points
@@ -322,7 +332,12 @@ def run_ours(args):
     words = 20
     bytes_launch = words * 4 * N
     avg_ms = sm_ms / max(1, sm_n)
-    achieved = bytes_launch / (avg_ms * 1e-3) / 1e9 if sm_n else None
+    # the method's bytes: 17 float32 words per point per sweep (read 5
+    # unknowns, 5 right-hand sides, rho^k, omega^k; write 5), times the sweeps
+    # one launch runs
+    bytes_method = SWEEP_WORDS["pfc2d"] * 4 * N * spl
+    achieved = bytes_method / (avg_ms * 1e-3) / 1e9 if sm_n else None
+    achieved_launch = bytes_launch / (avg_ms * 1e-3) / 1e9 if sm_n else None
     traffic = profiled_traffic("k_smooth_pfc512_level0", tuning["mixed"][0][0])
     f64_sm_ms, f64_sm_n = f64["prof"]
     f64_avg = f64_sm_ms / max(1, f64_sm_n)
@@ -369,9 +384,17 @@ def run_ours(args):
             "peak": peak,
             "unit": "GB/s",
             "frac": round(achieved / peak, 4) if achieved else None,
+            "frac_survey": round(achieved / peak, 4) if achieved else None,
             "peak_source": peak_kind,
             "traffic": traffic,
-            "algorithmic_bytes_per_launch": bytes_launch,
+            "algorithmic_bytes_per_launch": bytes_method,
+            "bytes_count": "17 float32 words per point per sweep x sweeps per launch (the method's traffic)",
+            "per_launch_20_words": {
+                "bytes": bytes_launch,
+                "achieved": round(achieved_launch, 1) if achieved_launch else None,
+                "frac": round(achieved_launch / peak, 4) if achieved_launch else None,
+                "count": "20 float32 words per point per launch: the 17 plus the coefficient iterate "
+                         "rho, u, v that the correction form reads"},
             "launch_ms": round(avg_ms, 6),
             "dof_sweeps_per_s": round(5 * N * spl / (avg_ms * 1e-3), 1) if sm_n else None,  # 5 unknowns/point
             "launches_timed": sm_n,
@@ -389,7 +412,7 @@ def run_ours(args):
         "clocks": mix["clocks"],
     }
     if not args.no_secondary:
-        out["secondary"] = secondary_all(torch, fm, inputs, flush, peak)
+        out["secondary"] = dict(batch48=sec_batch, **secondary_all(torch, fm, inputs, flush, peak))
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     print(json.dumps(out))
@@ -412,10 +435,15 @@ def _timed_steps(torch, step_fn, steps, flush):
     return [a.elapsed_time(b) for a, b in ev], out
 
 
-def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2):
+def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2, dist=None, rank=0, world=1):
     """48 independent PFC instances (n from {128..1024}, per-instance dt),
-    mixed precision, stepped together (fm_step_batch)."""
-    ens = inputs.batch48()
+    mixed precision, stepped together (fm_step_batch).  Under torchrun each
+    rank steps its shard of the ensemble as one batch (instances are
+    independent: no collective on the data path); the ensemble's time is the
+    slowest rank's."""
+    full = inputs.batch48()
+    mine = shard(len(full), rank, world)
+    ens = [full[i] for i in mine]
     sizes = [prm["n"] for _, _, prm in ens]
     p0 = ens[0][2]
     stream = torch.cuda.current_stream().cuda_stream
@@ -430,6 +458,8 @@ def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2):
         b.set_fields(i, rho, vel)
     torch.cuda.synchronize()
     l0 = fm.fm_batch_launches(b.handle)
+    if world > 1:
+        dist.barrier()
     times, infos = _timed_steps(torch, lambda: b.step(dts), steps, flush)
     launches = fm.fm_batch_launches(b.handle) - l0
     ms_sm, pts = fm.fm_batch_time_smoother(b.handle, 20)
@@ -439,32 +469,40 @@ def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2):
         # the fastest one-sweep variant of the autotuner's table, timed the same way
         v1 = min((v for v in range(18) if tune0[1][v] > 0), key=lambda v: tune0[1][v])
         ms1, _ = fm.fm_batch_time_sweep_variant(b.handle, v1, 20)
-        g1 = 20 * 4 * pts / (ms1 * 1e-3) / 1e9
+        g1 = SWEEP_WORDS["pfc2d"] * 4 * pts / (ms1 * 1e-3) / 1e9
         one = {"kernel": sweep_kernel(v1, True), "variant": v1, "launch_ms": round(ms1, 5),
-               "achieved": round(g1, 1), "frac": round(g1 / peak, 4),
+               "achieved": round(g1, 1), "frac": round(g1 / peak, 4), "frac_survey": round(g1 / peak, 4),
+               "frac_20_words": round(g1 * 20 / SWEEP_WORDS["pfc2d"] / peak, 4),
                "dof_sweeps_per_s": round(5 * pts / (ms1 * 1e-3), 1),
                "traffic": profiled_traffic("kb_smooth_batch48", v1)}
     b.close()
     cyc = [i.cycles for inf in infos for i in inf]
     total = sum(times)
-    words = 20
-    gbs = words * 4 * pts / (ms_sm * 1e-3) / 1e9
+    if world > 1:
+        total = max_over_ranks(dist, total, "cuda")
+    spl = sweeps_per_launch(tune0[0])
+    gbs = SWEEP_WORDS["pfc2d"] * 4 * pts * spl / (ms_sm * 1e-3) / 1e9
     return {
         "workload": "batch48: 48 PFC instances, n in {128,256,512,1024}, dt log-uniform [1e-3,1e-1], "
                     "eps=0.4, mixed, V(2,2) to 1e-10",
-        "points": int(sum(n * n for n in sizes)),
-        "instance_steps_per_s": round(len(sizes) * steps / (total / 1e3), 2),
+        "points": int(sum(prm["n"] ** 2 for _, _, prm in full)),
+        "ranks": world,
+        "instances_on_rank0": len(sizes),
+        "instance_steps_per_s": round(len(full) * steps / (total / 1e3), 2),
         "batch_steps_per_s": round(steps / (total / 1e3), 3),
         "ms_per_batch_step": round(total / steps, 3),
         "cycles_mean": round(sum(cyc) / len(cyc), 3), "cycles_max": max(cyc),
         "gpu_launches": launches,
         "smoother_roofline": {"kernel": sweep_kernel(tune0[0], True) + ", finest level of all instances",
                               "bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
-                              "frac": round(gbs / peak, 4), "launch_ms": round(ms_sm, 5),
-                              "sweeps_per_launch": sweeps_per_launch(tune0[0]),
+                              "frac": round(gbs / peak, 4), "frac_survey": round(gbs / peak, 4),
+                              "frac_20_words_per_launch": round(20 * 4 * pts / (ms_sm * 1e-3) / 1e9 / peak, 4),
+                              "bytes_count": "17 float32 words per point per sweep x sweeps per launch",
+                              "launch_ms": round(ms_sm, 5),
+                              "sweeps_per_launch": spl,
                               "dof_sweeps_per_s": round(5 * pts * sweeps_per_launch(tune0[0]) / (ms_sm * 1e-3),
                                                         1),
-                              "algorithmic_bytes_per_launch": words * 4 * pts,
+                              "algorithmic_bytes_per_launch": SWEEP_WORDS["pfc2d"] * 4 * pts * spl,
                               "timing": "20 back-to-back launches after a warm-up, CUDA events",
                               "traffic": profiled_traffic("kb_smooth_batch48", tune0[0]),
                               "autotuned_variant": tune0[0],
@@ -475,7 +513,22 @@ def secondary_batch48(torch, fm, inputs, flush, peak, steps=3, warmup=2):
     }
 
 
-def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, warmup=2, dim=2, smoother=False):
+def smoother_sweeps_per_launch(fm, sol, dim):
+    """Red-black sweeps one finest-level smoother launch runs: the fused 2-D
+    variants run one or two; the 3-D smoother's variant is reported by
+    fm_tuning too (see sweeps_per_launch_3d)."""
+    v = fm.fm_tuning(sol.handle, 0)[0]
+    return sweeps_per_launch_3d(v) if dim == 3 else sweeps_per_launch(v)
+
+
+def sweeps_per_launch_3d(variant):
+    """3-D smoother variants: 0 = a red and a black launch per sweep (half a
+    sweep per launch); 1.. = fused z-marching sweeps (see fm_tuning)."""
+    return 0.5 if variant == 0 else 1
+
+
+def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, warmup=2, dim=2, smoother=False,
+                     peak=None):
     n = list(reversed(rho.shape))
     stream = torch.cuda.current_stream().cuda_stream
     from paper_1503_07416_gb300 import inputs
@@ -496,16 +549,20 @@ def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, wa
     if smoother:
         ms, n = time_smoother(torch, fm, sol, rho_d, vel_d, prm["dt"], 2, flush)
         per = ms / max(1, n)
-        # finest level, one launch: one colour of the 3-D sweep (half the points)
-        # or one full fused 2-D sweep
-        pts = rho.size // 2 if dim == 3 else rho.size
-        words = 26 if dim == 3 else 20  # 3-D PFC: e 6, f 6, rho^k, omega 3, rho, u 3 read; e 6 written
+        spl = smoother_sweeps_per_launch(fm, sol, dim)
+        key = "pfc3d" if dim == 3 else ("pfc2d" if kind == "pfc" else "cdft2d")
         wb = 4 if precision == fm.FM_MIXED else 8
         nu = (5 if kind == "pfc" else 3) + (1 if dim == 3 else 0)
-        out["smoother"] = {"launch_ms": round(per, 5), "points_per_launch": pts,
-                           "dof_sweeps_per_s": round(nu * pts / (per * 1e-3), 1),
-                           "achieved_gbs": round(words * wb * pts / (per * 1e-3) / 1e9, 1),
-                           "algorithmic_bytes_per_launch": words * wb * pts}
+        bytes_launch = SWEEP_WORDS[key] * wb * rho.size * spl
+        gbs = bytes_launch / (per * 1e-3) / 1e9
+        out["smoother"] = {"kernel_variant": fm.fm_tuning(sol.handle, 0)[0], "launch_ms": round(per, 5),
+                           "sweeps_per_launch": spl, "launches_timed": n,
+                           "dof_sweeps_per_s": round(nu * rho.size * spl / (per * 1e-3), 1),
+                           "achieved_gbs": round(gbs, 1), "bound": "hbm", "unit": "GB/s", "peak": peak,
+                           "frac": round(gbs / peak, 4) if peak else None,
+                           "frac_survey": round(gbs / peak, 4) if peak else None,
+                           "algorithmic_bytes_per_launch": bytes_launch,
+                           "bytes_count": f"{SWEEP_WORDS[key]} words per point per sweep x sweeps per launch"}
     sol.close()
     return out
 
@@ -555,17 +612,18 @@ def profile_single(name):
 
 
 def secondary_all(torch, fm, inputs, flush, peak):
-    out = {"batch48": secondary_batch48(torch, fm, inputs, flush, peak)}
+    out = {}
     rho, vel, prm = inputs.cdft256()
     out["cdft256"] = {
         "workload": "cdft256: 2-D CDFT 256x256, h=17/128, nu=2.362, s=0.02, delta 1e-10, undamped, V(2,2) to 1e-10",
-        "mixed": secondary_single(torch, fm, flush, "cdft", rho, vel, prm, fm.FM_MIXED, 20),
+        "mixed": secondary_single(torch, fm, flush, "cdft", rho, vel, prm, fm.FM_MIXED, 20, smoother=True, peak=peak),
         "fp64": secondary_single(torch, fm, flush, "cdft", rho, vel, prm, fm.FM_FP64, 10),
     }
     rho, vel, prm = inputs.pfc3d128()
     out["pfc3d128"] = {
         "workload": "pfc3d128: 3-D PFC 128^3, eps=0.4, s=0.02, one nucleus, undamped, V(2,2) to 1e-10",
-        "mixed": secondary_single(torch, fm, flush, "pfc", rho, vel, prm, fm.FM_MIXED, 5, dim=3, smoother=True),
+        "mixed": secondary_single(torch, fm, flush, "pfc", rho, vel, prm, fm.FM_MIXED, 5, dim=3, smoother=True,
+                                  peak=peak),
         "fp64": secondary_single(torch, fm, flush, "pfc", rho, vel, prm, fm.FM_FP64, 2, warmup=1, dim=3),
     }
     return out
