@@ -135,6 +135,23 @@ def pfc3d128(seed=5, n=128):
     return rho, vel, prm
 
 
+def freezing(kind, n=128, seed=11):
+    """Sec. 6.2 freezing runs: rho = rho_bar (1 + 0.1 eta), eta ~ U[0, 1],
+    u = 0.  CDFT: rho_bar = 0.1 pi (packing fraction 0.6), [0, 17)^2,
+    nu = 2.362, s = 0.02, delta = 1e-10.  PFC: rho_bar = 3/2 - 0.07 sqrt 3
+    (the 3/2 offset of the psi <-> rho map, see the design notes),
+    [0, 32)^2, eps = 0.025 (alpha = 0.975), s = 0.01."""
+    eta = np.random.default_rng(seed).uniform(0.0, 1.0, size=(n, n))
+    vel = [np.zeros((n, n)), np.zeros((n, n))]
+    if kind == "cdft":
+        rb, L = 0.1 * math.pi, 17.0
+        prm = dict(kind="cdft", dim=2, n=n, h=L / n, dt=0.02, nu=2.362, gamma=2.0, delta=1e-10)
+    else:
+        rb, L = 1.5 - 0.07 * math.sqrt(3.0), 32.0
+        prm = dict(kind="pfc", dim=2, n=n, h=L / n, dt=0.01, alpha=0.975, gamma=2.0, delta=0.0)
+    return rb * (1.0 + 0.1 * eta), vel, prm
+
+
 def smooth_convergence_field(n, L=32.0, kind="pfc"):
     """The smooth initial density of the convergence tests (Sec. 6.1.1 CDFT,
     Sec. 6.1.2 PFC; for PFC the offset 3/2 is used, see the design notes)."""
