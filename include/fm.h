@@ -62,6 +62,11 @@ extern "C" {
 #define FM_HOST   0
 #define FM_DEVICE 1
 
+#define FM_HYDRO    0     /* the hydrodynamic scheme of Sec. 4-5 (default) */
+#define FM_GRADFLOW 1     /* the conservative gradient-flow scheme of Sec. 3,
+                             Thm 3.3: rho^{k+1} - rho^k = s Lap_h (dF_c[rho^{k+1}]
+                             - dF_e[rho^k]); no velocity */
+
 /* Periodic grid: dim = 2 or 3; n[d] points along x, y, z (n[2] ignored in
  * 2-D); spacing h.  Every n[d] must be even (red-black ordering). */
 typedef struct {
@@ -92,6 +97,13 @@ typedef struct {
     int coarsest;   /* coarsen while every n[d]/2 >= coarsest and is even [16] */
     int ncoarse;    /* smoothing iterations on the coarsest grid [4] */
     int precision;  /* FM_FP64 or FM_MIXED [FM_FP64] */
+    int model;      /* FM_HYDRO or FM_GRADFLOW [FM_HYDRO].  The gradient flow
+                       has the unknowns (rho, mu, kappa) (PFC) or rho (CDFT),
+                       solved by the same FAS cycle with a point block of its
+                       own (damping w_damp = 0.5 is needed for PFC); its state
+                       has no velocity: fm_set_fields / fm_step_host accept
+                       null velocity arrays, fm_get_fields returns zeros,
+                       fm_smooth and the batch calls return FM_EINVAL. */
 } fm_params;
 
 typedef struct {

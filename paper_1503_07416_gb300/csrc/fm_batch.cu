@@ -998,6 +998,7 @@ int fm_create_batch(int count, const fm_grid* grids, const fm_params* prm, const
                     fm_batch** out) {
   if (!out || !grids || !prm || !fn || count < 1 || count > 4096) return FM_EINVAL;
   *out = nullptr;
+  if (prm->model != FM_HYDRO) return FM_EINVAL;  // batched ensembles run the hydrodynamic scheme
   for (int i = 0; i < count; ++i)
     if (grids[i].dim != 2) return FM_EINVAL;  // batched ensembles are 2-D
   fm_batch* b = new (std::nothrow) fm_batch();

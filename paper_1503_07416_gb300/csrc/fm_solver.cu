@@ -28,6 +28,7 @@
 
 #include "fm_state.h"
 #include "fm_device.cuh"
+#include "fm_stepper.cuh"
 
 namespace fm {
 
@@ -114,20 +115,6 @@ static cudaMemcpyKind kind_out(int where) {
   return where == FM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
 }
 
-#define FM_CUDA(call)                                   \
-  do {                                                  \
-    cudaError_t err__ = (call);                         \
-    if (err__ != cudaSuccess) return FM_ECUDA;          \
-  } while (0)
-
-#define FM_LAUNCHED()                                   \
-  do {                                                  \
-    ++st->launches;                                     \
-    if (cudaPeekAtLastError() != cudaSuccess) {         \
-      cudaGetLastError();                               \
-      return FM_ECUDA;                                  \
-    }                                                   \
-  } while (0)
 
 // Launch variant (TX, TY, SF, PIPE) of the 2-D fused sweep on level L.
 template <typename T, int KIND, int TX, int TY, bool SF, bool PIPE, int NS = 1>
@@ -250,18 +237,6 @@ static Lvl<T> swap_er(Lvl<T> L) {
   return L;
 }
 
-// Sum the durations of the recorded (start, end) event pairs; call only after
-// the stream has been synchronised.
-static int harvest_profile(fm_state* st) {
-  for (int i = 0; i + 1 < st->npev; i += 2) {
-    float ms = 0.f;
-    FM_CUDA(cudaEventElapsedTime(&ms, st->pev[i], st->pev[i + 1]));
-    st->prof_ms += ms;
-    st->prof_count += 1;
-  }
-  st->npev = 0;
-  return FM_OK;
-}
 
 // The step is issued in three parts:
 //   pre  : omega^k, (J * rho^k), S, g^0, coefficients rho^k/omega^k down the
@@ -277,6 +252,7 @@ static int harvest_profile(fm_state* st) {
 template <typename T, int KIND, int DIM>
 struct Solver {
   using LY = Layout<KIND, DIM>;
+  static constexpr int NVEL = DIM;  // velocity arrays of the state (copied by step_host)
 
   static int inject_all(fm_state* st, bool coefficients_only) {
     if (st->nlev < 2) return FM_OK;
@@ -650,163 +626,10 @@ struct Solver {
     return FM_OK;
   }
 
-  static int read_ctl(fm_state* st, Ctl* out) {
-    FM_CUDA(cudaMemcpyAsync(st->hscal + 32, st->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st->stream));
-    FM_CUDA(cudaStreamSynchronize(st->stream));
-    memcpy(out, st->hscal + 32, sizeof(Ctl));
-    return harvest_profile(st);
-  }
-
-  static int finish(fm_state* st, fm_step_info* info) {
-    Ctl c;
-    memcpy(&c, st->hscal + 32, sizeof(Ctl));
-    st->prepared = false;
-    if (info) {
-      info->cycles = c.cycles;
-      info->res0 = c.norm0;
-      info->res = c.norm;
-    }
-    return c.status;
-  }
-
-  static int step_hostloop(fm_state* st, fm_step_info* info) {
-    int rc = enqueue_prepare(st);
-    if (rc) return rc;
-    rc = enqueue_resid_norm(st, 0, 0, 0);
-    if (rc) return rc;
-    Ctl c;
-    for (;;) {
-      rc = read_ctl(st, &c);
-      if (rc) return rc;
-      if (c.status != FM_OK || !(c.norm > st->prm.tol)) break;
-      rc = enqueue_body(st, 0, 0);
-      if (rc) return rc;
-    }
-    rc = enqueue_post(st);
-    if (rc) return rc;
-    FM_CUDA(cudaStreamSynchronize(st->stream));
-    return finish(st, info);
-  }
-
-  static int build_graph(fm_state* st) {
-    if (st->gexec) {
-      cudaGraphExecDestroy(st->gexec);
-      st->gexec = nullptr;
-    }
-    if (st->graph) {
-      cudaGraphDestroy(st->graph);
-      st->graph = nullptr;
-    }
-    cudaStream_t saved = st->stream;
-    cudaStream_t s0 = st->cap[0], s1 = st->cap[1];
-    st->capturing = true;
-    st->stream = s0;
-    int rc = FM_OK;
-    cudaGraph_t g = nullptr;
-    do {
-      if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = FM_ECUDA; break; }
-      const long long l0 = st->launches;
-      rc = enqueue_prepare(st);
-      if (rc) break;
-      cudaStreamCaptureStatus cs;
-      const cudaGraphNode_t* deps = nullptr;
-      size_t nd = 0;
-      cudaGraph_t cg = nullptr;
-      if (cudaStreamGetCaptureInfo(s0, &cs, nullptr, &cg, nullptr, nullptr, nullptr) != cudaSuccess) { rc = FM_ECUDA; break; }
-      cudaGraphConditionalHandle hdl;
-      if (cudaGraphConditionalHandleCreate(&hdl, cg, 0, cudaGraphCondAssignDefault) != cudaSuccess) { rc = FM_ECUDA; break; }
-      rc = enqueue_resid_norm(st, 0, hdl, 1);
-      if (rc) break;
-      st->cnt_pre = st->launches - l0;
-      if (cudaStreamGetCaptureInfo(s0, &cs, nullptr, &cg, &deps, nullptr, &nd) != cudaSuccess) { rc = FM_ECUDA; break; }
-      cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-      cp.conditional.handle = hdl;
-      cp.conditional.type = cudaGraphCondTypeWhile;
-      cp.conditional.size = 1;
-      cudaGraphNode_t wnode;
-      if (cudaGraphAddNode(&wnode, cg, deps, nullptr, nd, &cp) != cudaSuccess) { rc = FM_ECUDA; break; }
-      cudaGraph_t body = cp.conditional.phGraph_out[0];
-      if (cudaStreamUpdateCaptureDependencies(s0, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess) { rc = FM_ECUDA; break; }
-      st->stream = s1;
-      if (cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = FM_ECUDA; break; }
-      const long long l1 = st->launches;
-      rc = enqueue_body(st, hdl, 1);
-      st->cnt_body = st->launches - l1;
-      cudaGraph_t bodyout = nullptr;
-      if (cudaStreamEndCapture(s1, &bodyout) != cudaSuccess && rc == FM_OK) rc = FM_ECUDA;
-      if (rc) break;
-      st->stream = s0;
-      const long long l2 = st->launches;
-      rc = enqueue_post(st);
-      st->cnt_post = st->launches - l2;
-      st->launches = l0;
-    } while (0);
-    st->stream = s0;
-    if (cudaStreamEndCapture(s0, &g) != cudaSuccess && rc == FM_OK) rc = FM_ECUDA;
-    st->stream = saved;
-    st->capturing = false;
-    if (rc) {
-      cudaGetLastError();
-      if (g) cudaGraphDestroy(g);
-      return rc;
-    }
-    if (cudaGraphInstantiate(&st->gexec, g, 0) != cudaSuccess) {
-      cudaGetLastError();
-      cudaGraphDestroy(g);
-      return FM_ECUDA;
-    }
-    st->graph = g;
-    st->graph_dt = st->dt;
-    return FM_OK;
-  }
-
-  // One step for host-resident fields: the input copies, the step and the
-  // output copies on the state's stream, one host synchronisation (graph
-  // mode).  On failure the state and the outputs keep time level k.
+  static int step(fm_state* st, fm_step_info* info) { return Stepper<Solver>::step(st, info); }
   static int step_host(fm_state* st, const double* rho_in, const double* const* vel_in, double* rho_out,
                        double* const* vel_out, fm_step_info* info) {
-    const size_t bytes = (size_t)st->lv[0].g.N * sizeof(double);
-    const bool graph = !(st->prof || !st->use_graph);
-    if (graph && (!st->gexec || st->graph_dt != st->dt)) {
-      const int rc = build_graph(st);  // captured on private streams
-      if (rc) return rc;
-    }
-    FM_CUDA(cudaMemcpyAsync(st->rho, rho_in, bytes, cudaMemcpyHostToDevice, st->stream));
-    for (int d = 0; d < DIM; ++d)
-      FM_CUDA(cudaMemcpyAsync(st->vel[d], vel_in[d], bytes, cudaMemcpyHostToDevice, st->stream));
-    st->prepared = false;
-    int rc;
-    if (graph) {
-      FM_CUDA(cudaGraphLaunch(st->gexec, st->stream));
-      rc = FM_OK;
-    } else {
-      rc = step_hostloop(st, nullptr);  // synchronises; status read below
-      if (rc != FM_OK && rc != FM_ENOCONV && rc != FM_ENAN && rc != FM_ENONPOS) return rc;
-    }
-    FM_CUDA(cudaMemcpyAsync(rho_out, st->rho, bytes, cudaMemcpyDeviceToHost, st->stream));
-    for (int d = 0; d < DIM; ++d)
-      FM_CUDA(cudaMemcpyAsync(vel_out[d], st->vel[d], bytes, cudaMemcpyDeviceToHost, st->stream));
-    FM_CUDA(cudaStreamSynchronize(st->stream));
-    if (graph) {
-      Ctl c;
-      memcpy(&c, st->hscal + 32, sizeof(Ctl));
-      st->launches += st->cnt_pre + (long long)c.cycles * st->cnt_body + st->cnt_post;
-    }
-    return finish(st, info);
-  }
-
-  static int step(fm_state* st, fm_step_info* info) {
-    if (st->prof || !st->use_graph) return step_hostloop(st, info);
-    if (!st->gexec || st->graph_dt != st->dt) {
-      int rc = build_graph(st);
-      if (rc) return rc;
-    }
-    FM_CUDA(cudaGraphLaunch(st->gexec, st->stream));
-    FM_CUDA(cudaStreamSynchronize(st->stream));
-    Ctl c;
-    memcpy(&c, st->hscal + 32, sizeof(Ctl));
-    st->launches += st->cnt_pre + (long long)c.cycles * st->cnt_body + st->cnt_post;
-    return finish(st, info);
+    return Stepper<Solver>::step_host(st, rho_in, vel_in, rho_out, vel_out, info);
   }
 };
 
@@ -889,10 +712,13 @@ static size_t carve(fm_state* st, char* base) {
   }
   for (int d = 0; d < 3; ++d) st->om[d] = d < st->nom ? (double*)C.take(N0 * d8) : nullptr;
   st->conv = st->kind == FM_CDFT ? (double*)C.take(N0 * d8) : nullptr;
+  st->emu = (st->kind == FM_CDFT && st->model == FM_GRADFLOW) ? (double*)C.take(N0 * d8) : nullptr;
   st->tmp = (double*)C.take(N0 * d8);
   for (int q = 0; q < MAXU; ++q) st->r64[q] = q < st->nu ? (double*)C.take(N0 * d8) : nullptr;
   for (int q = 0; q < 5; ++q)
-    st->x64[q] = (st->dim == 3 && (q < 4 || st->kind == FM_CDFT)) ? (double*)C.take(N0 * d8) : nullptr;
+    st->x64[q] = (st->model == FM_HYDRO && st->dim == 3 && (q < 4 || st->kind == FM_CDFT))
+                     ? (double*)C.take(N0 * d8)
+                     : nullptr;
   st->partials = (double*)C.take((size_t)st->nblk * 8 * d8);
   st->dscal = (double*)C.take(64 * d8);
   st->ctl = C.take(64);
@@ -906,19 +732,20 @@ static size_t carve(fm_state* st, char* base) {
       B.eh[q] = (q < st->nu && l > 0) ? C.take(N * es) : nullptr;
     }
     const bool alias = (l == 0 && st->prm.precision == FM_FP64);
+    const int nvel = st->model == FM_HYDRO ? st->dim : 0;  // velocity coefficients
     if (alias) {
       B.rk = st->rho;
       B.cr = st->g[0];
       for (int d = 0; d < 3; ++d) {
         B.om[d] = st->om[d];
-        B.cv[d] = d < st->dim ? st->g[1 + d] : nullptr;
+        B.cv[d] = d < nvel ? st->g[1 + d] : nullptr;
       }
     } else {
-      B.rk = C.take(N * es);
+      B.rk = st->model == FM_HYDRO ? C.take(N * es) : nullptr;
       B.cr = C.take(N * es);
       for (int d = 0; d < 3; ++d) {
         B.om[d] = d < st->nom ? C.take(N * es) : nullptr;
-        B.cv[d] = d < st->dim ? C.take(N * es) : nullptr;
+        B.cv[d] = d < nvel ? C.take(N * es) : nullptr;
       }
     }
   }
@@ -951,6 +778,7 @@ void fm_default_params(fm_params* p) {
   p->coarsest = 16;
   p->ncoarse = 4;
   p->precision = FM_FP64;
+  p->model = FM_HYDRO;
 }
 
 const char* fm_strerror(int code) {
@@ -974,6 +802,7 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
   if (fn->kind != FM_PFC && fn->kind != FM_CDFT) return FM_EINVAL;
   if (fn->kind == FM_CDFT && !(fn->nu > 0.0)) return FM_EINVAL;
   if (prm->precision != FM_FP64 && prm->precision != FM_MIXED) return FM_EINVAL;
+  if (prm->model != FM_HYDRO && prm->model != FM_GRADFLOW) return FM_EINVAL;
   if (prm->nu1 < 0 || prm->nu2 < 0 || prm->nu1 + prm->nu2 < 1 || prm->ncoarse < 1 || prm->max_cycles < 0)
     return FM_EINVAL;
   if (!(prm->w_damp >= 0.0 && prm->w_damp < 1.0) || !(prm->gamma >= 0.0) || !(prm->tol > 0.0) ||
@@ -998,9 +827,15 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
   st->prm = *prm;
   st->fn = *fn;
   st->kind = fn->kind;
+  st->model = prm->model;
   st->dim = grid->dim;
-  st->nu = 1 + grid->dim + (fn->kind == FM_PFC ? 2 : 0);
-  st->nom = grid->dim == 2 ? 1 : 3;
+  if (st->model == FM_GRADFLOW) {
+    st->nu = fn->kind == FM_PFC ? 3 : 1;  // (rho, mu, kappa) or rho
+    st->nom = 0;
+  } else {
+    st->nu = 1 + grid->dim + (fn->kind == FM_PFC ? 2 : 0);
+    st->nom = grid->dim == 2 ? 1 : 3;
+  }
   st->elem = prm->precision == FM_MIXED ? (int)sizeof(float) : (int)sizeof(double);
   st->stream = 0;
   // hierarchy
@@ -1092,7 +927,7 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
       return rc;
     }
   }
-  {
+  if (st->model == FM_HYDRO) {
     const int rc = prm->precision == FM_MIXED ? dispatch_autotune<float>(st) : dispatch_autotune<double>(st);
     if (rc) {
       fm_destroy(st);
@@ -1162,10 +997,10 @@ int fm_profile_read(const fm_state* st, double* smoother_ms, long long* smoother
 }
 
 int fm_set_fields(fm_state* st, const double* rho, const double* const* vel, int where) {
-  if (!st || !rho || !vel || (where != FM_HOST && where != FM_DEVICE)) return FM_EINVAL;
+  if (!st || !rho || (!vel && st->model == FM_HYDRO) || (where != FM_HOST && where != FM_DEVICE)) return FM_EINVAL;
   const size_t bytes = (size_t)st->lv[0].g.N * sizeof(double);
   FM_CUDA(cudaMemcpyAsync(st->rho, rho, bytes, kind_in(where), st->stream));
-  for (int d = 0; d < st->dim; ++d) {
+  for (int d = 0; d < st->dim && st->model == FM_HYDRO; ++d) {  // the gradient flow keeps u = 0
     if (!vel[d]) return FM_EINVAL;
     FM_CUDA(cudaMemcpyAsync(st->vel[d], vel[d], bytes, kind_in(where), st->stream));
   }
@@ -1187,6 +1022,11 @@ int fm_get_fields(fm_state* st, double* rho, double* const* vel, int where) {
 
 int fm_step_host(fm_state* st, double dt, const double* rho_in, const double* const* vel_in, double* rho_out,
                  double* const* vel_out, fm_step_info* info) {
+  if (st && st->model == FM_GRADFLOW) {
+    if (!(dt > 0.0) || !rho_in || !rho_out) return FM_EINVAL;
+    st->dt = dt;
+    return gf_step_host(st, rho_in, rho_out, info);
+  }
   if (!st || !(dt > 0.0) || !rho_in || !vel_in || !rho_out || !vel_out) return FM_EINVAL;
   for (int d = 0; d < st->dim; ++d)
     if (!vel_in[d] || !vel_out[d]) return FM_EINVAL;
@@ -1198,12 +1038,14 @@ int fm_step_host(fm_state* st, double dt, const double* rho_in, const double* co
 int fm_prepare(fm_state* st, double dt) {
   if (!st || !(dt > 0.0)) return FM_EINVAL;
   st->dt = dt;
+  if (st->model == FM_GRADFLOW) return gf_prepare(st);
   return st->prm.precision == FM_MIXED ? dispatch_prepare<float>(st) : dispatch_prepare<double>(st);
 }
 
 int fm_step(fm_state* st, double dt, fm_step_info* info) {
   if (!st || !(dt > 0.0)) return FM_EINVAL;
   st->dt = dt;
+  if (st->model == FM_GRADFLOW) return gf_step(st, info);
   return st->prm.precision == FM_MIXED ? dispatch_step<float>(st, info) : dispatch_step<double>(st, info);
 }
 
@@ -1232,8 +1074,9 @@ int fm_residual(fm_state* st, const double* const* g, double* const* r, double* 
     if (!g[q]) return FM_EINVAL;
     FM_CUDA(cudaMemcpyAsync(st->g[q], g[q], bytes, kind_in(where), st->stream));
   }
-  int rc = st->prm.precision == FM_MIXED ? dispatch_resid<float>(st, st->r64, norm)
-                                         : dispatch_resid<double>(st, st->r64, norm);
+  int rc = st->model == FM_GRADFLOW         ? gf_residual(st, st->r64, norm)
+           : st->prm.precision == FM_MIXED ? dispatch_resid<float>(st, st->r64, norm)
+                                           : dispatch_resid<double>(st, st->r64, norm);
   if (rc == FM_OK && r) {
     for (int q = 0; q < st->nu; ++q)
       if (r[q]) FM_CUDA(cudaMemcpyAsync(r[q], st->r64[q], bytes, kind_out(where), st->stream));
@@ -1244,6 +1087,7 @@ int fm_residual(fm_state* st, const double* const* g, double* const* r, double* 
 
 int fm_smooth(fm_state* st, double* const* e, const double* const* f, int sweeps, int variant, int where) {
   if (!st || !e || !f || sweeps < 0 || (where != FM_HOST && where != FM_DEVICE)) return FM_EINVAL;
+  if (st->model != FM_HYDRO) return FM_EINVAL;
   if (!st->prepared) return FM_EINVAL;
   for (int q = 0; q < st->nu; ++q)
     if (!e[q] || !f[q]) return FM_EINVAL;

@@ -36,6 +36,7 @@ struct fm_state {
   fm_grid grid;
   fm_params prm;
   fm_functional fn;
+  int model;                      // FM_HYDRO or FM_GRADFLOW
   int kind, dim, nu, nom, nlev;
   int elem;                       // sizeof(T) of the hierarchy
   fm::LevelBufs lv[fm::MAXLEV];
@@ -46,6 +47,7 @@ struct fm_state {
   double* S[fm::MAXU];
   double* om[3];
   double* conv;                   // J * rho^k (CDFT)
+  double* emu;                    // gradient flow, CDFT: -(2 c_e rho^k + J * rho^k)
   double* tmp;                    // float64 scratch of N values
   double* r64[fm::MAXU];          // float64 residual scratch (row-level entry points)
   double* x64[5];                 // 3-D: per-point quantities shared by the residual
@@ -85,6 +87,11 @@ struct fm_state {
 };
 
 namespace fm {
+// fm_gradflow.cu: the gradient-flow model (fm_params.model = FM_GRADFLOW)
+int gf_step(fm_state* st, fm_step_info* info);
+int gf_step_host(fm_state* st, const double* rho_in, double* rho_out, fm_step_info* info);
+int gf_prepare(fm_state* st);
+int gf_residual(fm_state* st, double* const* r64, double* norm);
 // fm_fft.cu
 int fft_init(fm_state* st);                                    // twiddles, J, c_e, Jhat
 int fft_convolve(fm_state* st, const double* rho, double* out);  // out = J * rho

@@ -28,6 +28,8 @@ FM_FP64 = 0
 FM_MIXED = 1
 FM_HOST = 0
 FM_DEVICE = 1
+FM_HYDRO = 0
+FM_GRADFLOW = 1
 FM_AUX_OMEGA = 1
 FM_AUX_SOURCE = 2
 FM_AUX_CONV = 3
@@ -46,7 +48,7 @@ class fm_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("w_damp", C.c_double), ("delta", C.c_double),
                 ("tol", C.c_double), ("sigma", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("max_cycles", C.c_int), ("coarsest", C.c_int), ("ncoarse", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("model", C.c_int)]
 
 
 class fm_step_info(C.Structure):
@@ -180,8 +182,10 @@ def fm_set_stream(st, stream_handle: int):
 
 
 def fm_set_fields(st, rho, vel):
+    """vel may be None (gradient-flow states have no velocity)."""
+    vel = list(vel) if vel is not None else []
     w = _where([rho, *vel])
-    _check(lib().fm_set_fields(st, C.c_void_p(_ptr(rho)[0]), _vec(vel), w), "fm_set_fields")
+    _check(lib().fm_set_fields(st, C.c_void_p(_ptr(rho)[0]), _vec(vel) if vel else None, w), "fm_set_fields")
 
 
 def fm_get_fields(st, rho, vel):
@@ -197,10 +201,12 @@ def fm_step(st, dt):
 
 def fm_step_host(st, dt, rho_in, vel_in, rho_out, vel_out):
     """fm_step_host: one step of host-resident fields (numpy or CPU tensors,
-    float64, C-contiguous); returns (code, info) without raising."""
+    float64, C-contiguous); returns (code, info) without raising.  vel_in and
+    vel_out may be None for gradient-flow states."""
     info = fm_step_info()
-    code = lib().fm_step_host(st, C.c_double(dt), C.c_void_p(_ptr(rho_in)[0]), _vec(vel_in),
-                              C.c_void_p(_ptr(rho_out)[0]), _vec(vel_out), C.byref(info))
+    code = lib().fm_step_host(st, C.c_double(dt), C.c_void_p(_ptr(rho_in)[0]),
+                              _vec(vel_in) if vel_in else None, C.c_void_p(_ptr(rho_out)[0]),
+                              _vec(vel_out) if vel_out else None, C.byref(info))
     return code, info
 
 
@@ -487,7 +493,11 @@ class Solver:
             setattr(p, k, v)
         self.dim = dim
         self.shape = tuple(reversed(ns[:dim]))
-        self.nu = 1 + dim + (2 if f.kind == FM_PFC else 0)
+        self.model = p.model
+        if p.model == FM_GRADFLOW:
+            self.nu = 3 if f.kind == FM_PFC else 1
+        else:
+            self.nu = 1 + dim + (2 if f.kind == FM_PFC else 0)
         self.handle = fm_create(g, p, f)
         if stream is not None:
             fm_set_stream(self.handle, stream)

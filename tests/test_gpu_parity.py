@@ -316,10 +316,13 @@ def test_cdft_near_vacuum_steps(precision):
     """CDFT with densities down to ~6e-8 between the blob and its periodic
     images (ln rho ~ -16.7, where the projection of Sec. 6 changes rho by
     delta^2 / (2 rho) and the damped smoother of App. G.3 is needed): two
-    steps against the oracle with the paper's damping w = 0.5."""
+    steps against the oracle with the paper's damping w = 0.5 and the
+    oracle's hierarchy (down to 4^2, 20 coarse sweeps): near vacuum the
+    two-level default hierarchy of a 32^2 grid does not converge in 80
+    cycles."""
     rho, vel, prm = _vacuum_blob(32, 1e-9)
     assert rho.min() < 1e-7
-    _compare_step(rho, vel, prm, precision, tol=1e-12, w_damp=0.5, steps=2)
+    _compare_step(rho, vel, prm, precision, tol=1e-12, w_damp=0.5, steps=2, coarsest=4, ncoarse=20)
 
 
 # --------------------------------------------------------------- failure paths
