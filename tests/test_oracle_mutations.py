@@ -151,3 +151,42 @@ def test_gradflow_pins_catch_planted_mistake(monkeypatch, name, fn, checks):
         except (AssertionError, S.NoConvergence, np.linalg.LinAlgError, FloatingPointError):
             caught += 1
     assert caught == len(checks), f"planted mistake in gradflow.{name} not caught"
+
+
+# ---------------------------------------------------------------- channel walls
+from oracle import channel as Ch  # noqa: E402
+import tests.test_oracle_channel as cpins  # noqa: E402
+
+_corig = {"ghost": Ch.ghost}
+
+
+def _normal_even(row, typ, U):
+    return row if typ == Ch.VN else _corig["ghost"](row, typ, U)
+
+
+def _wall_speed_once(row, typ, U):
+    return U - row if typ == Ch.UT else _corig["ghost"](row, typ, U)
+
+
+def _scalar_dirichlet(row, typ, U):
+    return 0.0 * row if typ == Ch.SCAL else _corig["ghost"](row, typ, U)
+
+
+C_MUTATIONS = [
+    ("normal_velocity_even", _normal_even, [cpins.test_mass_energy_and_kinetic_identity_walls_at_rest]),
+    ("wall_speed_not_doubled", _wall_speed_once, [cpins.test_couette_flow_is_an_exact_fixed_point]),
+    ("scalar_ghost_zero", _scalar_dirichlet, [cpins.test_uniform_state_is_a_fixed_point]),
+]
+
+
+@pytest.mark.parametrize("label,fn,checks", C_MUTATIONS, ids=[m[0] for m in C_MUTATIONS])
+def test_channel_pins_catch_planted_mistake(monkeypatch, label, fn, checks):
+    monkeypatch.setattr(Ch, "ghost", fn)
+    caught = 0
+    for chk in checks:
+        try:
+            with np.errstate(all="ignore"):
+                chk()
+        except (AssertionError, S.NoConvergence, np.linalg.LinAlgError, FloatingPointError):
+            caught += 1
+    assert caught == len(checks), f"planted mistake {label} not caught"
