@@ -135,7 +135,7 @@ def pfc3d128(seed=5, n=128):
     return rho, vel, prm
 
 
-def freezing(kind, n=128, seed=11):
+def freezing(kind, n=128, seed=11, nu=2.362):
     """Sec. 6.2 freezing runs: rho = rho_bar (1 + 0.1 eta), eta ~ U[0, 1],
     u = 0.  CDFT: rho_bar = 0.1 pi (packing fraction 0.6), [0, 17)^2,
     nu = 2.362, s = 0.02, delta = 1e-10.  PFC: rho_bar = 3/2 - 0.07 sqrt 3
@@ -145,16 +145,43 @@ def freezing(kind, n=128, seed=11):
     vel = [np.zeros((n, n)), np.zeros((n, n))]
     if kind == "cdft":
         rb, L = 0.1 * math.pi, 17.0
-        prm = dict(kind="cdft", dim=2, n=n, h=L / n, dt=0.02, nu=2.362, gamma=2.0, delta=1e-10)
+        prm = dict(kind="cdft", dim=2, n=n, h=L / n, dt=0.02, nu=nu, gamma=2.0, delta=1e-10)
     else:
         rb, L = 1.5 - 0.07 * math.sqrt(3.0), 32.0
         prm = dict(kind="pfc", dim=2, n=n, h=L / n, dt=0.01, alpha=0.975, gamma=2.0, delta=0.0)
     return rb * (1.0 + 0.1 * eta), vel, prm
 
 
-def smooth_convergence_field(n, L=32.0, kind="pfc"):
+def nanocrystal(n=256, eps=0.4, rho_s=0.90073, rho_l=0.72958, diag_atoms=13.0):
+    """Sec. 6.3 channel test: an n x n grid with h = pi/(2 sqrt 3) (L = n h),
+    liquid rho_l everywhere except a regular hexagon of long diagonal
+    13 a centred at (L/2, L/2), a = 4 pi / sqrt 3, filled with the one-mode
+    solid rho_s + A (cos(sqrt(3)/2 x + pi) cos(y/2) - cos(y)/2) with the
+    amplitude A printed in Sec. 6.3 (A = 4/(5 sqrt 3) (rho_s - 3/2)
+    - (4 sqrt 3 / 15) sqrt(15 eps - 12 (rho_s - 3/2)^2)); u = 0.  y is measured
+    at the cell centres (j + 1/2) h between the walls."""
+    h = H_HEX
+    L = n * h
+    x = np.arange(n) * h
+    y = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    d = rho_s - 1.5
+    A = 4.0 / (5.0 * math.sqrt(3.0)) * d - 4.0 * math.sqrt(3.0) / 15.0 * math.sqrt(15.0 * eps - 12.0 * d * d)
+    solid = rho_s + A * (np.cos(math.sqrt(3.0) / 2.0 * X + math.pi) * np.cos(Y / 2.0) - 0.5 * np.cos(Y))
+    R = 0.5 * diag_atoms * A_ATOM              # circumradius of the hexagon
+    px, py = np.abs(X - L / 2), np.abs(Y - L / 2)
+    inside = (py <= R * math.sqrt(3.0) / 2.0) & (math.sqrt(3.0) * px + py <= math.sqrt(3.0) * R)
+    rho = np.where(inside, solid, rho_l)
+    vel = [np.zeros((n, n)), np.zeros((n, n))]
+    prm = dict(kind="pfc", dim=2, n=n, h=h, dt=0.02, alpha=1.0 - eps, gamma=2.0, delta=0.0)
+    return rho, vel, prm
+
+
+def smooth_convergence_field(n, L=32.0, kind="pfc", pfc_offset=1.5):
     """The smooth initial density of the convergence tests (Sec. 6.1.1 CDFT,
-    Sec. 6.1.2 PFC; for PFC the offset 3/2 is used, see the design notes)."""
+    Sec. 6.1.2 PFC; for PFC the offset 3/2 of the psi <-> rho map is used by
+    default, pfc_offset = 0.5 gives the text's literal value, see the design
+    notes)."""
     h = L / n
     x = np.arange(n) * h
     X, Y = np.meshgrid(x, x, indexing="xy")
@@ -162,5 +189,5 @@ def smooth_convergence_field(n, L=32.0, kind="pfc"):
             + 0.02 * np.cos(math.pi * (X + 10.0) / 32.0) ** 2 * np.cos(math.pi * (Y + 3.0) / 32.0) ** 2
             - 0.01 * np.sin(4 * math.pi * X / 32.0) ** 2 * np.sin(4 * math.pi * (Y - 6.0) / 32.0) ** 2)
     if kind == "pfc":
-        return math.sqrt(3.0) * (-0.07 + pert) + 1.5, h
+        return math.sqrt(3.0) * (-0.07 + pert) + pfc_offset, h
     return math.pi / 6.0 * 0.6 + pert, h

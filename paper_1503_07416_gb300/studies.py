@@ -58,13 +58,13 @@ def _solver(kind, n, h, precision, tol, stream=None, **kw):
     return fm.Solver(kind, (n, n), h, precision=precision, tol=tol, max_cycles=200, stream=stream, **extra)
 
 
-def evolve(kind, n, t_final=T_FINAL, tol=1e-12, precision=fm.FM_FP64, w_damp=0.0):
+def evolve(kind, n, t_final=T_FINAL, tol=1e-12, precision=fm.FM_FP64, w_damp=0.0, pfc_offset=1.5):
     """Evolve the smooth convergence-test field on an n^2 grid to t_final
     along s = 0.025 h^2.  Returns (rho, [u, v], info dict).  The tolerance is
     raised by decades (up to 1e-9) if the first step cannot reach it (the
     round-off floor of the weighted residual grows as h falls)."""
     import torch
-    rho0, h = inputs.smooth_convergence_field(n, L=L_CONV, kind=kind)
+    rho0, h = inputs.smooth_convergence_field(n, L=L_CONV, kind=kind, pfc_offset=pfc_offset)
     s = 0.025 * h * h
     nsteps = int(round(t_final / s))
     vel0 = [np.zeros_like(rho0), np.zeros_like(rho0)]
@@ -102,13 +102,13 @@ def cauchy_errors(coarse, fine, h_coarse):
     return math.sqrt(h_coarse * h_coarse * float(np.sum(e * e)))
 
 
-def convergence(kind, sizes=(16, 32, 64, 128, 256), t_final=T_FINAL, tol=1e-12):
+def convergence(kind, sizes=(16, 32, 64, 128, 256), t_final=T_FINAL, tol=1e-12, pfc_offset=1.5):
     """Run the refinement study; returns a dict with the per-grid runs, the
     Cauchy errors and rates of rho, u, v, and the paper's values beside them."""
     sols = {}
     runs = []
     for n in sizes:
-        rho, vel, info = evolve(kind, n, t_final=t_final, tol=tol)
+        rho, vel, info = evolve(kind, n, t_final=t_final, tol=tol, pfc_offset=pfc_offset)
         sols[n] = (rho, vel[0], vel[1], info["h"])
         runs.append(info)
     fields = ["rho", "u", "v"]
@@ -126,7 +126,7 @@ def convergence(kind, sizes=(16, 32, 64, 128, 256), t_final=T_FINAL, tol=1e-12):
         idx = [int(math.log2(a // 16)) for a in sizes[:-1]]
         paper[f] = [tab[i] if 0 <= i < len(tab) else None for i in idx]
     return dict(kind=kind, t_final=t_final, sizes=list(sizes), pairs=pairs, runs=runs, errors=errs,
-                rates=rates, paper=paper)
+                rates=rates, paper=paper, pfc_offset=pfc_offset if kind == "pfc" else None)
 
 
 def convergence_markdown(res):
@@ -134,7 +134,9 @@ def convergence_markdown(res):
     kind = res["kind"]
     tabs = {"cdft": "Tables 1-3", "pfc": "Tables 4-6"}[kind]
     lines = [f"# Convergence study, {kind.upper()} (Sec. 6.1, {tabs})", "",
-             f"Smooth initial density of Sec. 6.1 on [0, 32)^2, u = 0, t_f = {res['t_final']}, "
+             f"Smooth initial density of Sec. 6.1 on [0, 32)^2"
+             + (f" (PFC offset {res['pfc_offset']})" if res.get("pfc_offset") is not None else "")
+             + f", u = 0, t_f = {res['t_final']}, "
              "s = 0.025 h^2, float64 path of libfm on one GB300.  ||e|| = sqrt(h^2 sum e^2) with the "
              "coarse spacing; rate = log2 of consecutive error ratios.", "",
              "| pair | field | ||e|| (ours) | rate (ours) | ||e|| (paper) | rate (paper) |",
@@ -157,13 +159,14 @@ def convergence_markdown(res):
     return "\n".join(lines) + "\n"
 
 
-def freezing(kind, steps, every=100, n=128, precision=fm.FM_MIXED, tol=1e-10, w_damp=0.5, seed=11, out=None):
+def freezing(kind, steps, every=100, n=128, precision=fm.FM_MIXED, tol=1e-10, w_damp=0.5, seed=11, out=None,
+             nu=2.362):
     """Freeze a supercooled liquid for `steps` steps; returns the list of
     logged records (every `every` steps and the first and last) and a
     summary.  E is evaluated at every step and must not increase (beyond
     1e-12 relative, the solver tolerance's effect)."""
     import torch
-    rho, vel, prm = inputs.freezing(kind, n, seed)
+    rho, vel, prm = inputs.freezing(kind, n, seed, nu=nu)
     h, dt = prm["h"], prm["dt"]
     extra = dict(nu=prm["nu"], delta=prm["delta"]) if kind == "cdft" else dict(alpha=prm["alpha"])
     stream = torch.cuda.current_stream().cuda_stream
@@ -201,12 +204,59 @@ def freezing(kind, steps, every=100, n=128, precision=fm.FM_MIXED, tol=1e-10, w_
     if fh:
         fh.close()
     sol.close()
-    summary = dict(kind=kind, n=n, h=h, dt=dt, steps=steps, precision="mixed" if precision else "fp64",
+    summary = dict(kind=kind, n=n, h=h, dt=dt, nu=prm.get("nu"), steps=steps, precision="mixed" if precision else "fp64",
                    tol=tol, w_damp=w_damp, energy_max_relative_rise=worst_rise,
                    mass_drift=abs(recs[-1]["mass"] - M0) / abs(M0), KE_peak_t=max(recs, key=lambda r: r["KE"])["t"],
                    wall_s=recs[-1]["wall_s"])
     if kind == "cdft":
         summary.update(F_id_change=recs[-1]["F_id"] - recs[0]["F_id"], F_ex_change=recs[-1]["F_ex"] - recs[0]["F_ex"])
+    return recs, summary
+
+
+def shear(n=256, anneal=2000, drive=2000, u_wall=0.1, every=50, precision=fm.FM_MIXED, tol=1e-10, out=None):
+    """Sec. 6.3: the hexagonal nanocrystal in its liquid between walls,
+    annealed with the walls at rest for `anneal` steps (the energy must not
+    increase: Thm 5.1 with no-slip walls at rest), then driven with the walls
+    at -u_wall (bottom) and +u_wall (top) for `drive` steps (a driven system:
+    the energy may rise).  Returns the logged records and a summary."""
+    import torch
+    rho, vel, prm = inputs.nanocrystal(n)
+    stream = torch.cuda.current_stream().cuda_stream
+    recs = []
+    fh = open(out, "w") if out else None
+    t0 = time.perf_counter()
+    worst_rise = 0.0
+    k = 0
+    for phase, nsteps, walls in (("anneal", anneal, (0.0, 0.0)), ("drive", drive, (-u_wall, u_wall))):
+        sol = fm.Solver("pfc", (n, n), prm["h"], alpha=prm["alpha"], precision=precision, tol=tol, w_damp=0.0,
+                        max_cycles=200, walls=fm.FM_WALLS_Y, u_wall=walls, stream=stream)
+        sol.set_fields(rho, vel)
+        E_prev = None
+        for j in range(nsteps + 1):
+            info = sol.step(prm["dt"]) if j > 0 else None
+            if j > 0:
+                k += 1
+            if j % every == 0 or j == nsteps:
+                E, F, KE = sol.energy()
+                if phase == "anneal" and E_prev is not None:
+                    worst_rise = max(worst_rise, (E - E_prev) / max(1.0, abs(E_prev)))
+                E_prev = E if phase == "anneal" else None
+                rec = dict(phase=phase, step=k, t=round(k * prm["dt"], 10), E=E, F=F, KE=KE, mass=sol.mass(),
+                           cycles=info.cycles if info else 0, wall_s=round(time.perf_counter() - t0, 3))
+                recs.append(rec)
+                if fh:
+                    fh.write(json.dumps(rec) + "\n")
+        rho, vel = sol.get_fields()
+        sol.close()
+    if fh:
+        fh.close()
+    an = [r for r in recs if r["phase"] == "anneal"]
+    dr = [r for r in recs if r["phase"] == "drive"]
+    summary = dict(n=n, h=prm["h"], dt=prm["dt"], anneal_steps=anneal, drive_steps=drive, u_wall=u_wall,
+                   anneal_energy_max_relative_rise_between_logs=worst_rise,
+                   anneal_E=(an[0]["E"], an[-1]["E"]), drive_E=(dr[0]["E"], dr[-1]["E"]),
+                   drive_KE=(dr[0]["KE"], dr[-1]["KE"]), mass_drift=abs(recs[-1]["mass"] - recs[0]["mass"]) / recs[0]["mass"],
+                   wall_s=recs[-1]["wall_s"])
     return recs, summary
 
 
@@ -217,6 +267,7 @@ def main():
     c.add_argument("--kind", choices=["cdft", "pfc"], required=True)
     c.add_argument("--max-n", type=int, default=256)
     c.add_argument("--t-final", type=float, default=T_FINAL)
+    c.add_argument("--pfc-offset", type=float, default=1.5)
     c.add_argument("--out", default=None)
     f = sub.add_parser("freezing")
     f.add_argument("--kind", choices=["cdft", "pfc"], required=True)
@@ -224,6 +275,15 @@ def main():
     f.add_argument("--every", type=int, default=100)
     f.add_argument("--out", default=None, help="JSONL log of the records")
     f.add_argument("--summary", default=None)
+    f.add_argument("--nu", type=float, default=2.362)
+    sh = sub.add_parser("shear")
+    sh.add_argument("--n", type=int, default=256)
+    sh.add_argument("--anneal", type=int, default=2000)
+    sh.add_argument("--drive", type=int, default=2000)
+    sh.add_argument("--u-wall", type=float, default=0.1)
+    sh.add_argument("--every", type=int, default=50)
+    sh.add_argument("--out", default=None)
+    sh.add_argument("--summary", default=None)
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -231,7 +291,7 @@ def main():
     build.build_library()
     if args.cmd == "convergence":
         sizes = tuple(16 << k for k in range(int(math.log2(args.max_n // 16)) + 1))
-        res = convergence(args.kind, sizes, t_final=args.t_final)
+        res = convergence(args.kind, sizes, t_final=args.t_final, pfc_offset=args.pfc_offset)
         md = convergence_markdown(res)
         print(md)
         if args.out:
@@ -241,7 +301,10 @@ def main():
             with open(os.path.splitext(args.out)[0] + ".json", "w") as fh:
                 json.dump(res, fh, indent=1)
     else:
-        recs, summary = freezing(args.kind, args.steps, args.every, out=args.out)
+        if args.cmd == "freezing":
+            recs, summary = freezing(args.kind, args.steps, args.every, out=args.out, nu=args.nu)
+        else:
+            recs, summary = shear(args.n, args.anneal, args.drive, args.u_wall, args.every, out=args.out)
         print(json.dumps(summary))
         if args.summary:
             with open(args.summary, "w") as fh:
