@@ -62,6 +62,13 @@ extern "C" {
 #define FM_HOST   0
 #define FM_DEVICE 1
 
+#define FM_WALLS_NONE 0   /* periodic in every direction (default) */
+#define FM_WALLS_Y    1   /* 2-D PFC channel: periodic in x, no-slip walls at
+                             y = 0 and y = n_y h (App. E.2, Sec. 6.3) */
+
+#define FM_INIT_PREVIOUS    0  /* initial iterate of a step: the previous time level (default) */
+#define FM_INIT_EXTRAPOLATE 1  /* the linear extrapolation in time of the last two converged iterates */
+
 #define FM_HYDRO    0     /* the hydrodynamic scheme of Sec. 4-5 (default) */
 #define FM_GRADFLOW 1     /* the conservative gradient-flow scheme of Sec. 3,
                              Thm 3.3: rho^{k+1} - rho^k = s Lap_h (dF_c[rho^{k+1}]
@@ -104,6 +111,29 @@ typedef struct {
                        has no velocity: fm_set_fields / fm_step_host accept
                        null velocity arrays, fm_get_fields returns zeros,
                        fm_smooth and the batch calls return FM_EINVAL. */
+    int walls;      /* FM_WALLS_NONE or FM_WALLS_Y [FM_WALLS_NONE].  Walls
+                       (2-D hydrodynamic PFC only): the n_y rows are cells
+                       whose centres lie at (j + 1/2) h, the walls half a cell
+                       beyond the first and last rows, with the ghost rules of
+                       App. E.2 -- rho, mu, kappa mirrored (no flux), v odd,
+                       u = 2 u_wall - u (no slip on a wall moving along x);
+                       the multigrid transfers are cell-centred in y.  fm_smooth
+                       and the batch calls return FM_EINVAL. */
+    double u_wall[2]; /* speeds along x of the walls at y = 0 and y = n_y h [0, 0];
+                       with both at rest the step is energy stable (Thm 5.1) */
+    int init;       /* initial iterate of a step [FM_INIT_PREVIOUS] (periodic
+                       hydrodynamic solver; FM_EINVAL elsewhere).  The paper
+                       fixes only the solution, not the iterate that reaches
+                       it: FM_INIT_PREVIOUS starts from (rho^k, u^k) with
+                       kappa^0 = Lap_h rho^k and mu^0 the mu row at rho^k, so
+                       a step depends on (rho^k, u^k) alone; FM_INIT_EXTRAPOLATE
+                       starts from 2 g^k - g^{k-1}, the converged iterates
+                       of the last two steps of this state, which fewer
+                       V-cycles then correct.  The history is kept across
+                       fm_step and fm_step_host calls and cleared by
+                       fm_set_fields, fm_prepare, fm_residual, a change of
+                       the step size and a failed step; the converged
+                       solution is the same either way (to the tolerance). */
 } fm_params;
 
 typedef struct {

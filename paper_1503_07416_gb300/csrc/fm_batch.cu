@@ -998,7 +998,8 @@ int fm_create_batch(int count, const fm_grid* grids, const fm_params* prm, const
                     fm_batch** out) {
   if (!out || !grids || !prm || !fn || count < 1 || count > 4096) return FM_EINVAL;
   *out = nullptr;
-  if (prm->model != FM_HYDRO) return FM_EINVAL;  // batched ensembles run the hydrodynamic scheme
+  if (prm->model != FM_HYDRO || prm->walls != FM_WALLS_NONE || prm->init != FM_INIT_PREVIOUS)
+    return FM_EINVAL;  // periodic hydrodynamic, each step from its previous time level
   for (int i = 0; i < count; ++i)
     if (grids[i].dim != 2) return FM_EINVAL;  // batched ensembles are 2-D
   fm_batch* b = new (std::nothrow) fm_batch();

@@ -1408,6 +1408,7 @@ struct Fields64 {
   float* rk32;                // float copies for the mixed path (or null)
   float* om32[3];
   int* nonpos;                // CDFT: set to 1 where a density <= 0 would reach ln (or null)
+  const int* hist;            // extrapolated initial iterate: g already holds g^0 when *hist > 0 (or null)
 };
 
 // omega^k, S and the initial iterate g^0 (kappa^0 = Lap_h rho^k for PFC).
@@ -1456,17 +1457,18 @@ __device__ __forceinline__ void prepare_point(const Fields64& F, const Geo& G, c
     sv[a] = sa;
   }
   const double lapr = (KIND == KPFC) ? (nbsum<double, DIM>(F.rho, n) - 2.0 * DIM * rkc) * ih2 : 0.0;
+  const bool keep = F.hist && *F.hist > 0;  // g^0 extrapolated in time already (k_extrapolate)
   F.S[0][idx] = s0;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     F.S[1 + a][idx] = sv[a];
-    F.g[1 + a][idx] = uc[a];
+    if (!keep) F.g[1 + a][idx] = uc[a];
   }
-  F.g[0][idx] = rkc;
+  if (!keep) F.g[0][idx] = rkc;
   if constexpr (KIND == KPFC) {
     F.S[LY::IMU][idx] = 2.0 * lapr;
     F.S[LY::IKA][idx] = 0.0;
-    F.g[LY::IKA][idx] = lapr;
+    if (!keep) F.g[LY::IKA][idx] = lapr;
   }
 #pragma unroll
   for (int d = 0; d < LY::NOM; ++d) F.om[d][idx] = w[d];
@@ -1488,6 +1490,7 @@ __device__ __forceinline__ void prepare_mu_point(const Fields64& F, const Geo& G
                                                  const Phys<double>& P, int idx) {
   using LY = Layout<KPFC, DIM>;
   if (idx >= G.N) return;
+  if (F.hist && *F.hist > 0) return;  // mu^0 extrapolated with the rest of g^0
   int i, j, k;
   coords(idx, G, i, j, k);
   const Nb n = neighbours(i, j, k, G);
@@ -1982,7 +1985,44 @@ struct Ctl {
   int status;
   int active;   // batch: the instance still iterates
   int nonpos;   // CDFT: a density <= 0 reached ln this step (FM_ENONPOS)
+  int hist;     // converged iterates kept for the extrapolated initial iterate (0, 1 or 2)
+  int pad;
 };
+
+// Initial iterate extrapolated in time (fm_params.init = FM_INIT_EXTRAPOLATE),
+// before the prepare of a step: with the converged iterate g^k of the last
+// step still in g and the one before in gp, g^0 = 2 g^k - g^{k-1} when two
+// are known (hist = 2), g^k when one is (hist = 1); gp <- g^k.  A density the
+// extrapolation would make non-positive keeps g^k.  Nothing is done when no
+// converged iterate is known (hist = 0): the prepare then writes the
+// previous time level.
+struct Ptr6 {
+  double* p[MAXU];
+};
+
+template <int NU>
+__global__ void __launch_bounds__(TPB) k_extrapolate(Ptr6 g, Ptr6 gp, int N, const Ctl* ctl) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = ctl->hist;
+  if (idx >= N || h == 0) return;
+#pragma unroll
+  for (int q = 0; q < NU; ++q) {
+    const double gc = g.p[q][idx];
+    double gn = gc;
+    if (h >= 2) {
+      gn = 2.0 * gc - gp.p[q][idx];
+      if (q == 0 && !(gn > 0.0)) gn = gc;
+    }
+    gp.p[q][idx] = gc;
+    g.p[q][idx] = gn;
+  }
+}
+
+// After the step's commit: one more converged iterate kept (at most 2), or
+// none after a failed step (its iterate is not a solution).
+static __global__ void k_hist_advance(Ctl* ctl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ctl->hist = ctl->status == FM_OK ? min(ctl->hist + 1, 2) : 0;
+}
 
 // Finishes the residual norm max_q sqrt(w * sum_q), updates the control
 // block (cycles += in_body) and, in graph mode, sets the WHILE condition:
@@ -2196,6 +2236,7 @@ static Fields64 make_fields(fm_state* st) {
   }
   F.rk32 = nullptr;
   F.nonpos = st->kind == FM_CDFT ? &static_cast<Ctl*>(st->ctl)->nonpos : nullptr;
+  F.hist = st->prm.init == FM_INIT_EXTRAPOLATE ? &static_cast<Ctl*>(st->ctl)->hist : nullptr;
   if (st->prm.precision == FM_MIXED) {
     F.rk32 = (float*)st->lv[0].rk;
     for (int d = 0; d < st->nom; ++d) F.om32[d] = (float*)st->lv[0].om[d];

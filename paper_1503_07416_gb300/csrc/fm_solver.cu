@@ -351,6 +351,15 @@ struct Solver {
     const double h = st->lv[0].h;
     Phys<double> P = make_phys<double>(st);
     cudaStream_t s = st->stream;
+    if (st->prm.init == FM_INIT_EXTRAPOLATE) {
+      Ptr6 g, gp;
+      for (int q = 0; q < MAXU; ++q) {
+        g.p[q] = st->g[q];
+        gp.p[q] = st->gp[q];
+      }
+      k_extrapolate<LY::NU><<<nblocks(G.N), TPB, 0, s>>>(g, gp, G.N, (const Ctl*)st->ctl);
+      FM_LAUNCHED();
+    }
     if (KIND == KCDFT) {
       FM_CUDA(cudaMemsetAsync(&static_cast<Ctl*>(st->ctl)->nonpos, 0, sizeof(int), s));
       int rc = fft_convolve(st, st->rho, st->conv);
@@ -622,6 +631,10 @@ struct Solver {
     Vel3 gv{{st->g[1], st->g[2], DIM == 3 ? st->g[3] : nullptr}};
     k_commit<DIM><<<nblocks(G.N), TPB, 0, st->stream>>>(st->rho, vw, st->tmp, gv, G.N, ctl);
     FM_LAUNCHED();
+    if (st->prm.init == FM_INIT_EXTRAPOLATE) {
+      k_hist_advance<<<1, 32, 0, st->stream>>>((Ctl*)st->ctl);
+      FM_LAUNCHED();
+    }
     FM_CUDA(cudaMemcpyAsync(st->hscal + 32, st->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st->stream));
     return FM_OK;
   }
@@ -709,6 +722,7 @@ static size_t carve(fm_state* st, char* base) {
   for (int q = 0; q < MAXU; ++q) {
     st->g[q] = q < st->nu ? (double*)C.take(N0 * d8) : nullptr;
     st->S[q] = q < st->nu ? (double*)C.take(N0 * d8) : nullptr;
+    st->gp[q] = (q < st->nu && st->prm.init == FM_INIT_EXTRAPOLATE) ? (double*)C.take(N0 * d8) : nullptr;
   }
   for (int d = 0; d < 3; ++d) st->om[d] = d < st->nom ? (double*)C.take(N0 * d8) : nullptr;
   st->conv = st->kind == FM_CDFT ? (double*)C.take(N0 * d8) : nullptr;
@@ -763,6 +777,20 @@ static size_t carve(fm_state* st, char* base) {
 
 using namespace fm;
 
+// Forget the converged iterates kept for FM_INIT_EXTRAPOLATE (stream-ordered).
+static int reset_history(fm_state* st) {
+  if (st->prm.init != FM_INIT_EXTRAPOLATE) return FM_OK;
+  FM_CUDA(cudaMemsetAsync(&static_cast<Ctl*>(st->ctl)->hist, 0, sizeof(int), st->stream));
+  return FM_OK;
+}
+
+// A step of another size than the kept iterates' starts without them.
+static int check_history_dt(fm_state* st, double dt) {
+  if (st->prm.init != FM_INIT_EXTRAPOLATE || st->hist_dt == dt) return FM_OK;
+  st->hist_dt = dt;
+  return reset_history(st);
+}
+
 extern "C" {
 
 void fm_default_params(fm_params* p) {
@@ -779,6 +807,9 @@ void fm_default_params(fm_params* p) {
   p->ncoarse = 4;
   p->precision = FM_FP64;
   p->model = FM_HYDRO;
+  p->walls = FM_WALLS_NONE;
+  p->u_wall[0] = p->u_wall[1] = 0.0;
+  p->init = FM_INIT_PREVIOUS;
 }
 
 const char* fm_strerror(int code) {
@@ -803,6 +834,14 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
   if (fn->kind == FM_CDFT && !(fn->nu > 0.0)) return FM_EINVAL;
   if (prm->precision != FM_FP64 && prm->precision != FM_MIXED) return FM_EINVAL;
   if (prm->model != FM_HYDRO && prm->model != FM_GRADFLOW) return FM_EINVAL;
+  if (prm->walls != FM_WALLS_NONE && prm->walls != FM_WALLS_Y) return FM_EINVAL;
+  if (prm->walls == FM_WALLS_Y &&
+      (grid->dim != 2 || fn->kind != FM_PFC || prm->model != FM_HYDRO ||
+       !(prm->u_wall[0] == prm->u_wall[0]) || !(prm->u_wall[1] == prm->u_wall[1])))
+    return FM_EINVAL;  // walls: the 2-D hydrodynamic PFC channel only
+  if (prm->init != FM_INIT_PREVIOUS && prm->init != FM_INIT_EXTRAPOLATE) return FM_EINVAL;
+  if (prm->init == FM_INIT_EXTRAPOLATE && (prm->model != FM_HYDRO || prm->walls != FM_WALLS_NONE))
+    return FM_EINVAL;  // the periodic hydrodynamic solver only
   if (prm->nu1 < 0 || prm->nu2 < 0 || prm->nu1 + prm->nu2 < 1 || prm->ncoarse < 1 || prm->max_cycles < 0)
     return FM_EINVAL;
   if (!(prm->w_damp >= 0.0 && prm->w_damp < 1.0) || !(prm->gamma >= 0.0) || !(prm->tol > 0.0) ||
@@ -927,7 +966,7 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
       return rc;
     }
   }
-  if (st->model == FM_HYDRO) {
+  if (st->model == FM_HYDRO && prm->walls == FM_WALLS_NONE) {
     const int rc = prm->precision == FM_MIXED ? dispatch_autotune<float>(st) : dispatch_autotune<double>(st);
     if (rc) {
       fm_destroy(st);
@@ -999,6 +1038,10 @@ int fm_profile_read(const fm_state* st, double* smoother_ms, long long* smoother
 int fm_set_fields(fm_state* st, const double* rho, const double* const* vel, int where) {
   if (!st || !rho || (!vel && st->model == FM_HYDRO) || (where != FM_HOST && where != FM_DEVICE)) return FM_EINVAL;
   const size_t bytes = (size_t)st->lv[0].g.N * sizeof(double);
+  {
+    const int rc = reset_history(st);
+    if (rc) return rc;
+  }
   FM_CUDA(cudaMemcpyAsync(st->rho, rho, bytes, kind_in(where), st->stream));
   for (int d = 0; d < st->dim && st->model == FM_HYDRO; ++d) {  // the gradient flow keeps u = 0
     if (!vel[d]) return FM_EINVAL;
@@ -1028,6 +1071,16 @@ int fm_step_host(fm_state* st, double dt, const double* rho_in, const double* co
     return gf_step_host(st, rho_in, rho_out, info);
   }
   if (!st || !(dt > 0.0) || !rho_in || !vel_in || !rho_out || !vel_out) return FM_EINVAL;
+  if (st->prm.walls == FM_WALLS_Y) {
+    for (int d = 0; d < 2; ++d)
+      if (!vel_in[d] || !vel_out[d]) return FM_EINVAL;
+    st->dt = dt;
+    return ch_step_host(st, rho_in, vel_in, rho_out, vel_out, info);
+  }
+  {
+    const int rc = check_history_dt(st, dt);
+    if (rc) return rc;
+  }
   for (int d = 0; d < st->dim; ++d)
     if (!vel_in[d] || !vel_out[d]) return FM_EINVAL;
   st->dt = dt;
@@ -1039,6 +1092,11 @@ int fm_prepare(fm_state* st, double dt) {
   if (!st || !(dt > 0.0)) return FM_EINVAL;
   st->dt = dt;
   if (st->model == FM_GRADFLOW) return gf_prepare(st);
+  if (st->prm.walls == FM_WALLS_Y) return ch_prepare(st);
+  {
+    const int rc = reset_history(st);  // the row call replaces the step's iterate
+    if (rc) return rc;
+  }
   return st->prm.precision == FM_MIXED ? dispatch_prepare<float>(st) : dispatch_prepare<double>(st);
 }
 
@@ -1046,6 +1104,11 @@ int fm_step(fm_state* st, double dt, fm_step_info* info) {
   if (!st || !(dt > 0.0)) return FM_EINVAL;
   st->dt = dt;
   if (st->model == FM_GRADFLOW) return gf_step(st, info);
+  if (st->prm.walls == FM_WALLS_Y) return ch_step(st, info);
+  {
+    const int rc = check_history_dt(st, dt);
+    if (rc) return rc;
+  }
   return st->prm.precision == FM_MIXED ? dispatch_step<float>(st, info) : dispatch_step<double>(st, info);
 }
 
@@ -1074,9 +1137,14 @@ int fm_residual(fm_state* st, const double* const* g, double* const* r, double* 
     if (!g[q]) return FM_EINVAL;
     FM_CUDA(cudaMemcpyAsync(st->g[q], g[q], bytes, kind_in(where), st->stream));
   }
-  int rc = st->model == FM_GRADFLOW         ? gf_residual(st, st->r64, norm)
-           : st->prm.precision == FM_MIXED ? dispatch_resid<float>(st, st->r64, norm)
-                                           : dispatch_resid<double>(st, st->r64, norm);
+  {
+    const int rc = reset_history(st);  // the caller's iterate replaced the converged one
+    if (rc) return rc;
+  }
+  int rc = st->model == FM_GRADFLOW           ? gf_residual(st, st->r64, norm)
+           : st->prm.walls == FM_WALLS_Y     ? ch_residual(st, st->r64, norm)
+           : st->prm.precision == FM_MIXED   ? dispatch_resid<float>(st, st->r64, norm)
+                                             : dispatch_resid<double>(st, st->r64, norm);
   if (rc == FM_OK && r) {
     for (int q = 0; q < st->nu; ++q)
       if (r[q]) FM_CUDA(cudaMemcpyAsync(r[q], st->r64[q], bytes, kind_out(where), st->stream));
@@ -1087,7 +1155,7 @@ int fm_residual(fm_state* st, const double* const* g, double* const* r, double* 
 
 int fm_smooth(fm_state* st, double* const* e, const double* const* f, int sweeps, int variant, int where) {
   if (!st || !e || !f || sweeps < 0 || (where != FM_HOST && where != FM_DEVICE)) return FM_EINVAL;
-  if (st->model != FM_HYDRO) return FM_EINVAL;
+  if (st->model != FM_HYDRO || st->prm.walls != FM_WALLS_NONE) return FM_EINVAL;
   if (!st->prepared) return FM_EINVAL;
   for (int q = 0; q < st->nu; ++q)
     if (!e[q] || !f[q]) return FM_EINVAL;
@@ -1131,7 +1199,11 @@ static int energy_sums(fm_state* st, double* q) {
   }
   Vel3 v3{{st->vel[0], st->vel[1], st->vel[2]}};
   const double a = st->fn.alpha;
-  if (st->kind == FM_PFC && st->dim == 2)
+  if (st->prm.walls == FM_WALLS_Y) {
+    const int rc = ch_energy_launch(st);
+    if (rc) return rc;
+    ++st->launches;
+  } else if (st->kind == FM_PFC && st->dim == 2)
     k_energy<KPFC, 2><<<st->nblk, TPB, 0, s>>>(st->rho, v3, nullptr, G, h, a, st->partials);
   else if (st->kind == FM_PFC)
     k_energy<KPFC, 3><<<st->nblk, TPB, 0, s>>>(st->rho, v3, nullptr, G, h, a, st->partials);
@@ -1139,7 +1211,7 @@ static int energy_sums(fm_state* st, double* q) {
     k_energy<KCDFT, 2><<<st->nblk, TPB, 0, s>>>(st->rho, v3, st->tmp, G, h, a, st->partials);
   else
     k_energy<KCDFT, 3><<<st->nblk, TPB, 0, s>>>(st->rho, v3, st->tmp, G, h, a, st->partials);
-  FM_LAUNCHED();
+  if (st->prm.walls != FM_WALLS_Y) FM_LAUNCHED();
   k_final_sum<5><<<1, TPB, 0, s>>>(st->partials, st->nblk, st->dscal + 8);
   FM_LAUNCHED();
   FM_CUDA(cudaMemcpyAsync(st->hscal + 8, st->dscal + 8, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));

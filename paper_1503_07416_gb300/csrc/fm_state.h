@@ -44,6 +44,7 @@ struct fm_state {
   double* rho;
   double* vel[3];
   double* g[fm::MAXU];
+  double* gp[fm::MAXU];           // FM_INIT_EXTRAPOLATE: converged iterate of the step before
   double* S[fm::MAXU];
   double* om[3];
   double* conv;                   // J * rho^k (CDFT)
@@ -60,6 +61,7 @@ struct fm_state {
   double ce;                      // (J_e * 1) (CDFT)
   fm::FFTBufs fft;
   double dt;                      // step of the last fm_prepare
+  double hist_dt;                 // step size the kept converged iterates belong to
   bool prepared;
   cudaStream_t stream;
   cudaStream_t cap[2];            // private streams used to capture the step graph
@@ -92,6 +94,13 @@ int gf_step(fm_state* st, fm_step_info* info);
 int gf_step_host(fm_state* st, const double* rho_in, double* rho_out, fm_step_info* info);
 int gf_prepare(fm_state* st);
 int gf_residual(fm_state* st, double* const* r64, double* norm);
+// fm_channel.cu: the 2-D PFC channel (fm_params.walls = FM_WALLS_Y)
+int ch_step(fm_state* st, fm_step_info* info);
+int ch_step_host(fm_state* st, const double* rho_in, const double* const* vel_in, double* rho_out,
+                 double* const* vel_out, fm_step_info* info);
+int ch_prepare(fm_state* st);
+int ch_residual(fm_state* st, double* const* r64, double* norm);
+int ch_energy_launch(fm_state* st);  // energy partial sums (Neumann Laplacian) into st->partials
 // fm_fft.cu
 int fft_init(fm_state* st);                                    // twiddles, J, c_e, Jhat
 int fft_convolve(fm_state* st, const double* rho, double* out);  // out = J * rho

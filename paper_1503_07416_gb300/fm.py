@@ -30,6 +30,10 @@ FM_HOST = 0
 FM_DEVICE = 1
 FM_HYDRO = 0
 FM_GRADFLOW = 1
+FM_WALLS_NONE = 0
+FM_WALLS_Y = 1
+FM_INIT_PREVIOUS = 0
+FM_INIT_EXTRAPOLATE = 1
 FM_AUX_OMEGA = 1
 FM_AUX_SOURCE = 2
 FM_AUX_CONV = 3
@@ -48,7 +52,8 @@ class fm_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("w_damp", C.c_double), ("delta", C.c_double),
                 ("tol", C.c_double), ("sigma", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("max_cycles", C.c_int), ("coarsest", C.c_int), ("ncoarse", C.c_int),
-                ("precision", C.c_int), ("model", C.c_int)]
+                ("precision", C.c_int), ("model", C.c_int), ("walls", C.c_int), ("u_wall", C.c_double * 2),
+                ("init", C.c_int)]
 
 
 class fm_step_info(C.Structure):
@@ -490,7 +495,10 @@ class Solver:
         p = fm_default_params()
         p.precision = precision
         for k, v in params.items():
-            setattr(p, k, v)
+            if k == "u_wall":
+                p.u_wall[0], p.u_wall[1] = v
+            else:
+                setattr(p, k, v)
         self.dim = dim
         self.shape = tuple(reversed(ns[:dim]))
         self.model = p.model

@@ -62,7 +62,9 @@ def _create(dim=2, n=(8, 8, 1), h=0.5, kind=fm.FM_PFC, nu=1.0, **kw):
     dict(dim=4), dict(n=(7, 8, 1)), dict(n=(0, 8, 1)), dict(h=0.0), dict(kind=9),
     dict(kind=fm.FM_CDFT, n=(12, 8, 1)), dict(kind=fm.FM_CDFT, nu=0.0), dict(tol=0.0),
     dict(w_damp=1.0), dict(nu1=0, nu2=0), dict(ncoarse=0), dict(precision=7), dict(coarsest=1),
-    dict(dim=3, n=(8, 8, 5)), dict(model=7),
+    dict(dim=3, n=(8, 8, 5)), dict(model=7), dict(walls=3), dict(init=5),
+    dict(walls=1, kind=fm.FM_CDFT, n=(8, 8, 1)), dict(walls=1, dim=3, n=(8, 8, 8)),
+    dict(init=1, model=1),
 ])
 def test_create_rejects_invalid_arguments(lib, bad):
     assert _create(**bad) == fm.FM_EINVAL

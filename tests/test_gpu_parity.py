@@ -270,6 +270,28 @@ def test_full_size_cdft256_two_steps(precision):
     _compare_step(rho, vel, prm, precision, tol=1e-13, w_damp=0.0, steps=2, **inputs.BENCH_MG_2D)
 
 
+def test_mixed_coarsest_solve_costs_no_cycles_at_512():
+    """The mixed path runs its whole cycle, the coarsest-grid sweeps
+    included, in float32 inside the float64 residual loop.  At the benchmark's
+    512^2 configuration it takes the same V-cycles per step as the float64
+    path over five steps, and its fields stay within 1e-8 (per field, 2-norm
+    and element-wise) of the float64 path's."""
+    rho, vel, prm = inputs.pfc512()
+    sols = {p: gpu_solver(rho, prm, precision=p, w_damp=0.0, tol=1e-10, **inputs.BENCH_MG_2D)
+            for p in (fm.FM_FP64, fm.FM_MIXED)}
+    for sol in sols.values():
+        sol.set_fields(rho, vel)
+    for _ in range(5):
+        c64 = sols[fm.FM_FP64].step(prm["dt"]).cycles
+        cmx = sols[fm.FM_MIXED].step(prm["dt"]).cycles
+        assert c64 == cmx, (c64, cmx)
+    r64, v64 = sols[fm.FM_FP64].get_fields()
+    rmx, vmx = sols[fm.FM_MIXED].get_fields()
+    assert_parity(rmx, vmx, r64, v64, TOLMIX)
+    for sol in sols.values():
+        sol.close()
+
+
 @functools.lru_cache(maxsize=1)
 def _pfc3d128_reference():
     """The 128^3 PFC workload and one oracle step of it (converged to 1e-11;
@@ -646,3 +668,67 @@ def test_two_sweep_smoother_in_the_cycle_cdft(precision, variant, nu, monkeypatc
     rng = np.random.default_rng(9)
     vel = [0.02 * rng.standard_normal(rho.shape) for _ in range(2)]
     _compare_step(rho, vel, prm, precision, steps=2, nu1=nu[0], nu2=nu[1])
+
+
+# --------------------------------------------------------------- extrapolated initial iterate
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_extrapolated_initial_iterate_same_solutions_fewer_cycles(precision):
+    """FM_INIT_EXTRAPOLATE starts each step from 2 g^k - g^{k-1}: eight steps of
+    the 128^2 supercooled PFC workload each match the oracle's step (which
+    starts from the previous time level) within the usual tolerance, and take
+    no more V-cycles in total than the previous-time-level start."""
+    rho, vel, prm = inputs.pfc_supercooled(128, seed=33)
+    P, opts, J = oracle_setup(rho, prm, w_damp=0.0, tol=1e-11)
+    ext = gpu_solver(rho, prm, precision=precision, w_damp=0.0, tol=1e-11, init=fm.FM_INIT_EXTRAPOLATE)
+    prev = gpu_solver(rho, prm, precision=precision, w_damp=0.0, tol=1e-11)
+    ext.set_fields(rho, vel)
+    prev.set_fields(rho, vel)
+    bound = TOL64 if precision == fm.FM_FP64 else TOLMIX
+    ce, cp = [], []
+    for _ in range(8):
+        ie = ext.step(prm["dt"])
+        ip = prev.step(prm["dt"])
+        ce.append(ie.cycles)
+        cp.append(ip.cycles)
+        assert ie.res <= 1e-11
+        rg, vg = ext.get_fields()
+        ro, vo, _ = S.step(rho, vel, P, opts, J=J)
+        assert_parity(rg, vg, ro, vo, bound, (ce, cp))
+        rho, vel = ro, vo
+    assert sum(ce) <= sum(cp), (ce, cp)
+    ext.close()
+    prev.close()
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_extrapolation_history_is_cleared_and_graph_modes_agree(precision):
+    """fm_set_fields clears the history (the next step is bit for bit a fresh
+    solver's first step), and the graph and launch-by-launch modes give the
+    same bits over four extrapolated steps."""
+    rho, vel, prm = inputs.pfc_supercooled(128, seed=35)
+    kw = dict(precision=precision, w_damp=0.0, tol=1e-10, init=fm.FM_INIT_EXTRAPOLATE)
+    a = gpu_solver(rho, prm, **kw)
+    a.set_fields(rho, vel)
+    for _ in range(3):
+        a.step(prm["dt"])
+    a.set_fields(rho, vel)
+    ia = a.step(prm["dt"])
+    ra, va = a.get_fields()
+    b = gpu_solver(rho, prm, **kw)
+    b.set_fields(rho, vel)
+    ib = b.step(prm["dt"])
+    rb, vb = b.get_fields()
+    assert ia.cycles == ib.cycles and np.array_equal(ra, rb) and all(np.array_equal(x, y) for x, y in zip(va, vb))
+    a.close()
+    b.close()
+    out = []
+    for profile in (False, True):
+        sol = gpu_solver(rho, prm, **kw)
+        fm.fm_profile(sol.handle, profile)
+        sol.set_fields(rho, vel)
+        cyc = [sol.step(prm["dt"]).cycles for _ in range(4)]
+        out.append((sol.get_fields(), cyc))
+        sol.close()
+    (r1, v1), c1 = out[0]
+    (r2, v2), c2 = out[1]
+    assert c1 == c2 and np.array_equal(r1, r2) and all(np.array_equal(x, y) for x, y in zip(v1, v2))
