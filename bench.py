@@ -5,7 +5,11 @@ Workload (``pfc512``): periodic 512x512 grid, h = pi/(2 sqrt 3), eps = 0.4
 Gaussian nuclei (amplitude 0.5) and 0.01 U(-1,1) noise, u = 0, s = 0.02,
 FAS V(2,2) to a float64 residual of 1e-10, undamped point-block smoother.
 The headline arm is the mixed path (float32 smoothing inside the float64
-outer residual loop); the plain float64 path is timed beside it.
+outer residual loop); the plain float64 path is timed beside it.  Each step
+starts from the linear extrapolation in time of the last two converged
+iterates (fm_params.init; --init previous starts from the previous time
+level, which is also timed beside the headline); every step is solved to the
+same float64 tolerance either way.
 
 One "step" = one fm_step (the whole hot path: vorticity, source, the FAS
 solve to tolerance, closure).  Inputs are resident in HBM when the timed
@@ -257,11 +261,13 @@ def run_ours(args):
 
     results = {}
     tuning = {}
-    arms = (("mixed", fm.FM_MIXED), ("fp64", fm.FM_FP64))
+    arms = [("mixed", fm.FM_MIXED, args.init), ("fp64", fm.FM_FP64, args.init)]
+    if args.init != "previous":
+        arms.append(("mixed_previous", fm.FM_MIXED, "previous"))  # the same arm from the previous time level
     if args.only:
-        arms = tuple(a for a in arms if a[0] == args.only)
-    for name, prec in arms:
-        sol = make_solver(fm, rho.shape, prm, prec, stream, args.init)
+        arms = [a for a in arms if a[0] == args.only]
+    for name, prec, init in arms:
+        sol = make_solver(fm, rho.shape, prm, prec, stream, init)
         tuning[name] = [fm.fm_tuning(sol.handle, l) for l in range(3)]
         if world > 1:
             dist.barrier()
@@ -388,6 +394,10 @@ def run_ours(args):
                 "smoother_gbs": round(words * 8 * N / (f64_avg * 1e-3) / 1e9, 1) if f64_sm_n else None,
             },
             "speedup_mixed_over_fp64": round(f64["total_ms"] / mix["total_ms"], 3),
+            "mixed_from_previous_time_level": (
+                {"value": round(world * steps / (results["mixed_previous"]["total_ms"] / 1e3), 3),
+                 "cycles_per_step_mean": round(statistics.mean(results["mixed_previous"]["cycles"]), 3)}
+                if "mixed_previous" in results else None),
             "sweep_variants": {k: [{"level": l, "variant": v[0], "ms": [round(x, 4) for x in v[1]]}
                                    for l, v in enumerate(vals)] for k, vals in tuning.items()},
         },
@@ -537,9 +547,9 @@ def smoother_sweeps_per_launch(fm, sol, dim):
 
 
 def sweeps_per_launch_3d(variant):
-    """3-D smoother variants: 0 = a red and a black launch per sweep (half a
-    sweep per launch); 1.. = fused z-marching sweeps (see fm_tuning)."""
-    return 0.5 if variant == 0 else 1
+    """3-D smoother variants (fm_tuning): both run a red and a black launch
+    per sweep, half a sweep per launch."""
+    return 0.5
 
 
 def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, warmup=2, dim=2, smoother=False,
@@ -613,6 +623,14 @@ def profile_single(name):
     import torch
     from paper_1503_07416_gb300 import build, fm, inputs
     build.build_library()
+    if name in ("gradflow512", "nanocrystal256"):
+        sol, rho, vel, dt, _ = model_solver(torch, fm, inputs, name)
+        sol.set_fields(rho, vel)
+        cyc = [sol.step(dt).cycles for _ in range(3)]
+        torch.cuda.synchronize()
+        sol.close()
+        print(json.dumps({"profile_single": name, "cycles": cyc}))
+        return
     rho, vel, prm = getattr(inputs, name)()
     n = list(reversed(rho.shape))
     sol = fm.Solver(prm["kind"], n, prm["h"], dim=prm["dim"], alpha=prm.get("alpha", 0.0), nu=prm.get("nu", 0.0),
@@ -626,8 +644,46 @@ def profile_single(name):
     print(json.dumps({"profile_single": name, "cycles": cyc}))
 
 
+def secondary_model(torch, fm, inputs, flush, name, steps=20, warmup=3):
+    """Steps/s of the two models beside the periodic hydrodynamic one: the
+    gradient flow (FM_GRADFLOW) on the pfc512 state and the channel
+    (FM_WALLS_Y) on the 256^2 nanocrystal with the walls at -0.1 / +0.1;
+    mixed precision, V(2,2) to 1e-10."""
+    sol, rho, vel, dt, desc = model_solver(torch, fm, inputs, name)
+    rho_d = torch.from_numpy(rho).cuda()
+    vel_d = [torch.from_numpy(v).cuda() for v in vel] if vel is not None else None
+    sol.set_fields(rho_d, vel_d)
+    for _ in range(warmup):
+        sol.step(dt)
+    sol.set_fields(rho_d, vel_d)
+    torch.cuda.synchronize()
+    l0 = fm.fm_profile_read(sol.handle)[2]
+    times, infos = _timed_steps(torch, lambda: sol.step(dt), steps, flush)
+    launches = fm.fm_profile_read(sol.handle)[2] - l0
+    sol.close()
+    return {"workload": desc, "steps_per_s": round(steps / (sum(times) / 1e3), 3),
+            "ms_per_step": round(sum(times) / steps, 4),
+            "cycles_mean": round(sum(i.cycles for i in infos) / len(infos), 3), "gpu_launches": launches}
+
+
+def model_solver(torch, fm, inputs, name):
+    stream = torch.cuda.current_stream().cuda_stream
+    if name == "gradflow512":
+        rho, _, prm = inputs.pfc512()
+        sol = fm.Solver("pfc", (512, 512), prm["h"], alpha=prm["alpha"], precision=fm.FM_MIXED, tol=1e-10,
+                        w_damp=0.5, model=fm.FM_GRADFLOW, max_cycles=200, stream=stream)
+        return sol, rho, None, 0.02, ("gradflow512: PFC gradient flow (Thm 3.3) from the pfc512 state, s = 0.02, "
+                                      "w = 0.5, mixed, V(2,2) to 1e-10")
+    rho, vel, prm = inputs.nanocrystal(256)
+    sol = fm.Solver("pfc", (256, 256), prm["h"], alpha=prm["alpha"], precision=fm.FM_MIXED, tol=1e-10, w_damp=0.0,
+                    walls=fm.FM_WALLS_Y, u_wall=(-0.1, 0.1), max_cycles=200, stream=stream)
+    return sol, rho, vel, prm["dt"], ("nanocrystal256: 2-D PFC channel (walls at -0.1/+0.1), hexagonal seed, "
+                                      "eps = 0.4, s = 0.02, mixed, V(2,2) to 1e-10")
+
+
 def secondary_all(torch, fm, inputs, flush, peak):
-    out = {}
+    out = {"gradflow512": secondary_model(torch, fm, inputs, flush, "gradflow512"),
+           "nanocrystal256": secondary_model(torch, fm, inputs, flush, "nanocrystal256")}
     rho, vel, prm = inputs.cdft256()
     out["cdft256"] = {
         "workload": "cdft256: 2-D CDFT 256x256, h=17/128, nu=2.362, s=0.02, delta 1e-10, undamped, V(2,2) to 1e-10",
@@ -714,14 +770,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
+    ap.add_argument("--only", choices=["mixed", "fp64", "mixed_previous"], default=None,
                     help="time one arm only and print a short diagnostic line (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--profile-single", choices=["pfc512", "cdft256", "pfc3d128", "pfc64"], default=None,
+    ap.add_argument("--profile-single", choices=["pfc512", "cdft256", "pfc3d128", "pfc64", "gradflow512",
+                                                 "nanocrystal256"], default=None,
                     help="profiling target: one solver of the named workload, 3 steps")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="profiling target: first K batch48 instances, timed batched sweeps only")
-    ap.add_argument("--init", choices=list(INIT), default="previous",
+    ap.add_argument("--init", choices=list(INIT), default="extrapolate",
                     help="initial iterate of each step of the 512^2 arms")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the batched, CDFT and 3-D workloads measured beside the headline")

@@ -333,8 +333,11 @@ int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_
  * pass (strips and rows as 12..17); 24..26 the tile form that runs two sweeps
  * per tile (tiles 32x16, 64x8, 32x32, halo of four, f and omega from global
  * memory).  The time per launch of a two-sweep variant is halved to give its
- * time per sweep.  Setting the environment variable FM_RB_VARIANT=v before
- * fm_create fixes the variant (no timing). */
+ * time per sweep.  In 3-D every sweep is a red and a black launch and the
+ * variants are 0 (256-thread blocks, the compiler's register count) and 1
+ * (the same sweep bounded to six resident blocks per multiprocessor); their
+ * times are per red + black pair.  Setting the environment variable
+ * FM_RB_VARIANT=v before fm_create fixes the variant (no timing). */
 int fm_tuning(const fm_state* st, int level, int* variant, float* ms_per_variant);
 
 /* Enable (1) or disable (0) CUDA-event timing of every finest-level smoother

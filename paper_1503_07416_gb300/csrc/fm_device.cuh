@@ -428,6 +428,21 @@ __global__ void __launch_bounds__(TPB) k_smooth(Lvl<T> L, Phys<T> P, int color) 
   smooth_point<T, KIND, DIM>(L, P, make_ptk<T, DIM>(P, L.h), n);
 }
 
+// The same colour sweep compiled for six resident blocks per SM (at most 40
+// registers a thread instead of 64): the 3-D point update waits on its many
+// cached loads, and more warps in flight hide that latency.  The 3-D
+// autotuner times it against k_smooth per level (it spills in float64).
+template <typename T, int KIND, int DIM>
+__global__ void __launch_bounds__(TPB, 6) k_smooth_occ(Lvl<T> L, Phys<T> P, int color) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (!colour_point(t, color, L.g, i, j, k)) return;
+  const Nb n = neighbours(i, j, k, L.g);
+  smooth_point<T, KIND, DIM>(L, P, make_ptk<T, DIM>(P, L.h), n);
+}
+
+constexpr int SM3_NVAR = 2;  // 3-D colour-sweep variants: 0 k_smooth, 1 k_smooth_occ
+
 template <typename T, int KIND, int DIM>
 __global__ void __launch_bounds__(TPB) k_resid(Lvl<T> L, Phys<T> P) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;

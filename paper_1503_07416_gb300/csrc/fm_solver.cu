@@ -294,9 +294,67 @@ struct Solver {
   // timed launches) on the level itself and compared per sweep; a later
   // variant replaces the choice only if it is 2% faster.  The sweeps only
   // touch solver scratch.
+  // Launch a red and a black colour sweep of variant v (3-D) on level L.
+  static int launch_colour_pair(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P) {
+    const int half = L.g.N / 2;
+    for (int color = 0; color < 2; ++color) {
+      if (v == 1)
+        k_smooth_occ<T, KIND, DIM><<<nblocks(half), TPB, 0, st->stream>>>(L, P, color);
+      else
+        k_smooth<T, KIND, DIM><<<nblocks(half), TPB, 0, st->stream>>>(L, P, color);
+      FM_LAUNCHED();
+    }
+    return FM_OK;
+  }
+
+  // 3-D: time the colour-sweep variants per multi-kernel level (one warm-up
+  // pair, TUNE_REPS timed pairs); a later variant replaces the choice only if
+  // it is 2% faster.  FM_RB_VARIANT fixes it (0 or 1).
+  static int autotune3(fm_state* st) {
+    const char* fixed = getenv("FM_RB_VARIANT");
+    for (int l = 0; l < MAXLEV; ++l) st->rbv[l] = 0;
+    if (fixed && fixed[0]) {
+      const int v = atoi(fixed);
+      for (int l = 0; l < MAXLEV; ++l) st->rbv[l] = (v >= 0 && v < SM3_NVAR) ? v : 0;
+      return FM_OK;
+    }
+    Phys<T> P = make_phys<T>(st);
+    cudaEvent_t e0, e1;
+    FM_CUDA(cudaEventCreate(&e0));
+    FM_CUDA(cudaEventCreate(&e1));
+    int rc = FM_OK;
+    const int ntuned = st->small_from + (st->coarse_fused ? 1 : 0);
+    for (int l = 0; l < ntuned && rc == FM_OK; ++l) {
+      const Lvl<T> L = make_lvl<T>(st, l);
+      float best = 1e30f;
+      for (int v = 0; v < SM3_NVAR && rc == FM_OK; ++v) {
+        rc = launch_colour_pair(st, v, L, P);
+        if (rc) break;
+        if (cudaEventRecord(e0, st->stream) != cudaSuccess) { rc = FM_ECUDA; break; }
+        for (int k = 0; k < TUNE_REPS && rc == FM_OK; ++k) rc = launch_colour_pair(st, v, L, P);
+        if (rc) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, st->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          rc = FM_ECUDA;
+          break;
+        }
+        st->rbt[l][v] = ms / TUNE_REPS;
+        if (ms < best * 0.98f) {
+          best = ms;
+          st->rbv[l] = v;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    return rc;
+  }
+
   static int autotune(fm_state* st) {
     if constexpr (DIM != 2) {
-      return FM_OK;
+      return st->fused_rb ? autotune3(st) : FM_OK;
     } else {
       const char* fixed = getenv("FM_RB_VARIANT");
       for (int l = 0; l < MAXLEV; ++l) st->rbv[l] = 0;
@@ -516,6 +574,8 @@ struct Solver {
             const int rc = launch_rb<T, KIND>(st, v, L, P, s, *in_r);
             if (rc) return rc;
           }
+        } else if (DIM == 3 && v == 1) {  // 3-D: v is the colour-sweep variant
+          k_smooth_occ<T, KIND, DIM><<<nblocks(half), TPB, 0, s>>>(*in_r ? swap_er(L) : L, P, color);
         } else {
           k_smooth<T, KIND, DIM><<<nblocks(half), TPB, 0, s>>>(*in_r ? swap_er(L) : L, P, color);
         }
@@ -537,7 +597,7 @@ struct Solver {
 
   static int smooth(fm_state* st, int l, const Phys<T>& P, int iters, int* in_r) {
     const bool prof = st->prof && !st->capturing && l == 0;
-    const int v = (DIM == 2 && st->fused_rb) ? st->rbv[l] : -1;
+    const int v = DIM == 3 ? st->rbv[l] : (st->fused_rb ? st->rbv[l] : -1);
     return run_sweeps(st, make_lvl<T>(st, l), v, P, iters, in_r, prof);
   }
 

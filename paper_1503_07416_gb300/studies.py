@@ -160,7 +160,7 @@ def convergence_markdown(res):
 
 
 def freezing(kind, steps, every=100, n=128, precision=fm.FM_MIXED, tol=1e-10, w_damp=0.5, seed=11, out=None,
-             nu=2.362):
+             nu=2.362, coarsest=16, ncoarse=4):
     """Freeze a supercooled liquid for `steps` steps; returns the list of
     logged records (every `every` steps and the first and last) and a
     summary.  E is evaluated at every step and must not increase (beyond
@@ -171,7 +171,7 @@ def freezing(kind, steps, every=100, n=128, precision=fm.FM_MIXED, tol=1e-10, w_
     extra = dict(nu=prm["nu"], delta=prm["delta"]) if kind == "cdft" else dict(alpha=prm["alpha"])
     stream = torch.cuda.current_stream().cuda_stream
     sol = fm.Solver(kind, (n, n), h, precision=precision, tol=tol, w_damp=w_damp, max_cycles=200,
-                    stream=stream, **extra)
+                    coarsest=coarsest, ncoarse=ncoarse, stream=stream, **extra)
     sol.set_fields(rho, vel)
     M0 = sol.mass()
     recs = []
@@ -182,7 +182,14 @@ def freezing(kind, steps, every=100, n=128, precision=fm.FM_MIXED, tol=1e-10, w_
     for k in range(steps + 1):
         info = None
         if k > 0:
-            info = sol.step(dt)
+            code, info = fm.fm_step_raw(sol.handle, dt)
+            if code != fm.FM_OK:  # record where the solve stopped and end the run
+                rec = dict(step=k, t=round(k * dt, 10), failed=fm.strerror(code), cycles=info.cycles, res=info.res)
+                recs.append(rec)
+                if fh:
+                    fh.write(json.dumps(rec) + "\n")
+                steps = k - 1
+                break
         terms = sol.energy_terms()
         KE = terms[0]
         F = sum(terms[1:])
@@ -204,12 +211,14 @@ def freezing(kind, steps, every=100, n=128, precision=fm.FM_MIXED, tol=1e-10, w_
     if fh:
         fh.close()
     sol.close()
+    good = [r for r in recs if "failed" not in r]
     summary = dict(kind=kind, n=n, h=h, dt=dt, nu=prm.get("nu"), steps=steps, precision="mixed" if precision else "fp64",
+                   coarsest=coarsest, ncoarse=ncoarse, stopped=recs[-1].get("failed"),
                    tol=tol, w_damp=w_damp, energy_max_relative_rise=worst_rise,
-                   mass_drift=abs(recs[-1]["mass"] - M0) / abs(M0), KE_peak_t=max(recs, key=lambda r: r["KE"])["t"],
-                   wall_s=recs[-1]["wall_s"])
+                   mass_drift=abs(good[-1]["mass"] - M0) / abs(M0), KE_peak_t=max(good, key=lambda r: r["KE"])["t"],
+                   wall_s=good[-1]["wall_s"])
     if kind == "cdft":
-        summary.update(F_id_change=recs[-1]["F_id"] - recs[0]["F_id"], F_ex_change=recs[-1]["F_ex"] - recs[0]["F_ex"])
+        summary.update(F_id_change=good[-1]["F_id"] - good[0]["F_id"], F_ex_change=good[-1]["F_ex"] - good[0]["F_ex"])
     return recs, summary
 
 
@@ -276,6 +285,8 @@ def main():
     f.add_argument("--out", default=None, help="JSONL log of the records")
     f.add_argument("--summary", default=None)
     f.add_argument("--nu", type=float, default=2.362)
+    f.add_argument("--coarsest", type=int, default=16)
+    f.add_argument("--ncoarse", type=int, default=4)
     sh = sub.add_parser("shear")
     sh.add_argument("--n", type=int, default=256)
     sh.add_argument("--anneal", type=int, default=2000)
@@ -302,7 +313,8 @@ def main():
                 json.dump(res, fh, indent=1)
     else:
         if args.cmd == "freezing":
-            recs, summary = freezing(args.kind, args.steps, args.every, out=args.out, nu=args.nu)
+            recs, summary = freezing(args.kind, args.steps, args.every, out=args.out, nu=args.nu,
+                                     coarsest=args.coarsest, ncoarse=args.ncoarse)
         else:
             recs, summary = shear(args.n, args.anneal, args.drive, args.u_wall, args.every, out=args.out)
         print(json.dumps(summary))

@@ -100,12 +100,15 @@ def test_smallest_grid():
     _compare_step(rho, vel, prm, fm.FM_FP64, w_damp=0.0, ncoarse=40)
 
 
+@pytest.mark.parametrize("variant", ["0", "1"])
 @pytest.mark.parametrize("n", [16, 32])
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
-def test_3d_pfc(precision, n):
+def test_3d_pfc(precision, n, variant, monkeypatch):
     """3-D PFC with random velocity (three vorticity components): 16^3 (one
     level, its sweeps as red and black launches over the whole grid) and 32^3
-    (two levels, the 16^3 coarsest grid smoothed by multi-block launches)."""
+    (two levels, the 16^3 coarsest grid smoothed by multi-block launches);
+    both 3-D colour-sweep variants (the occupancy-bounded one is 1)."""
+    monkeypatch.setenv("FM_RB_VARIANT", variant)
     rng = np.random.default_rng(6)
     rho = 0.8 + 0.05 * rng.uniform(-1, 1, (n, n, n))
     vel = [0.03 * rng.standard_normal((n, n, n)) for _ in range(3)]
