@@ -547,9 +547,10 @@ def smoother_sweeps_per_launch(fm, sol, dim):
 
 
 def sweeps_per_launch_3d(variant):
-    """3-D smoother variants (fm_tuning): both run a red and a black launch
-    per sweep, half a sweep per launch."""
-    return 0.5
+    """3-D smoother variants (fm_tuning): 0 and 1 run a red and a black launch
+    per sweep (half a sweep per timed launch); 2 runs a sweep in z-chunks and
+    its timing events bracket the whole sweep."""
+    return 1 if variant == 2 else 0.5
 
 
 def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, warmup=2, dim=2, smoother=False,
@@ -671,9 +672,10 @@ def model_solver(torch, fm, inputs, name):
     if name == "gradflow512":
         rho, _, prm = inputs.pfc512()
         sol = fm.Solver("pfc", (512, 512), prm["h"], alpha=prm["alpha"], precision=fm.FM_MIXED, tol=1e-10,
-                        w_damp=0.5, model=fm.FM_GRADFLOW, max_cycles=200, stream=stream)
+                        w_damp=0.3, model=fm.FM_GRADFLOW, max_cycles=200, stream=stream)
         return sol, rho, None, 0.02, ("gradflow512: PFC gradient flow (Thm 3.3) from the pfc512 state, s = 0.02, "
-                                      "w = 0.5, mixed, V(2,2) to 1e-10")
+                                      "w = 0.3 (the damping this sixth-order flow converges fastest with), mixed, "
+                                      "V(2,2) to 1e-10")
     rho, vel, prm = inputs.nanocrystal(256)
     sol = fm.Solver("pfc", (256, 256), prm["h"], alpha=prm["alpha"], precision=fm.FM_MIXED, tol=1e-10, w_damp=0.0,
                     walls=fm.FM_WALLS_Y, u_wall=(-0.1, 0.1), max_cycles=200, stream=stream)

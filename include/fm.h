@@ -333,10 +333,13 @@ int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_
  * pass (strips and rows as 12..17); 24..26 the tile form that runs two sweeps
  * per tile (tiles 32x16, 64x8, 32x32, halo of four, f and omega from global
  * memory).  The time per launch of a two-sweep variant is halved to give its
- * time per sweep.  In 3-D every sweep is a red and a black launch and the
- * variants are 0 (256-thread blocks, the compiler's register count) and 1
- * (the same sweep bounded to six resident blocks per multiprocessor); their
- * times are per red + black pair.  Setting the environment variable
+ * time per sweep.  In 3-D the variants are 0 (a red and a black launch,
+ * 256-thread blocks, the compiler's register count), 1 (the same bounded to
+ * six resident blocks per multiprocessor) and 2 (the sweep in z-chunks sized
+ * to stay in L2: red over a chunk, then black over the planes whose
+ * neighbours are red by then; levels whose arrays fit in 48 MB are not
+ * chunked and report 0 for it); their times are per sweep.  Setting the
+ * environment variable
  * FM_RB_VARIANT=v before fm_create fixes the variant (no timing). */
 int fm_tuning(const fm_state* st, int level, int* variant, float* ms_per_variant);
 

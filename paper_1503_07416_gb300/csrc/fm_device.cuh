@@ -441,7 +441,41 @@ __global__ void __launch_bounds__(TPB, 6) k_smooth_occ(Lvl<T> L, Phys<T> P, int 
   smooth_point<T, KIND, DIM>(L, P, make_ptk<T, DIM>(P, L.h), n);
 }
 
-constexpr int SM3_NVAR = 2;  // 3-D colour-sweep variants: 0 k_smooth, 1 k_smooth_occ
+// One colour of a sweep over the rows [row0, row0 + nrows) of a 3-D level
+// (a row is one (j, k); rows past the last wrap to the first), bounded to six
+// blocks per SM like k_smooth_occ.  Used to sweep the level in z-chunks.
+template <typename T, int KIND, int DIM>
+__global__ void __launch_bounds__(TPB, 6) k_smooth_rows(Lvl<T> L, Phys<T> P, int color, int row0, int nrows) {
+  const int half = L.g.nx >> 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nrows * half) return;
+  const int nr = L.g.ny * L.g.nz;
+  int rowid = row0 + (int)(t / half);
+  if (rowid >= nr) rowid -= nr;
+  const int j = rowid % L.g.ny, k = rowid / L.g.ny;
+  const int i = 2 * (int)(t % half) + ((j + k + color) & 1);
+  const Nb n = neighbours(i, j, k, L.g);
+  smooth_point<T, KIND, DIM>(L, P, make_ptk<T, DIM>(P, L.h), n);
+}
+
+// 3-D colour-sweep variants: 0 k_smooth, 1 k_smooth_occ, 2 the same sweep in
+// z-chunks (z_chunk_planes): red over a chunk, then black over the planes
+// whose z-neighbours are all red by then, so the black launch finds the
+// chunk's arrays in L2; the same updates in the same order of dependence as
+// a red and a black launch over the whole level.
+constexpr int SM3_NVAR = 3;
+
+// Planes per chunk: the largest divisor of nz whose arrays (about 20 float
+// words a point) stay within 48 MB, at least 2; 0 (no chunking) when the
+// whole level does.
+static inline int z_chunk_planes(const Geo& g) {
+  const double plane = 80.0 * g.nx * (double)g.ny;
+  if (plane * g.nz <= 48e6 || g.nz < 4) return 0;
+  int best = 0;
+  for (int z = 2; z <= g.nz / 2; ++z)
+    if (g.nz % z == 0 && plane * z <= 48e6) best = z;
+  return best;
+}
 
 template <typename T, int KIND, int DIM>
 __global__ void __launch_bounds__(TPB) k_resid(Lvl<T> L, Phys<T> P) {

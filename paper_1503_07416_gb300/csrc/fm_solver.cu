@@ -294,9 +294,35 @@ struct Solver {
   // timed launches) on the level itself and compared per sweep; a later
   // variant replaces the choice only if it is 2% faster.  The sweeps only
   // touch solver scratch.
-  // Launch a red and a black colour sweep of variant v (3-D) on level L.
+  // One 3-D sweep in z-chunks of Z planes (variant 2): red over planes
+  // [cZ, (c+1)Z), then black over the planes whose neighbours are all red by
+  // then -- [max(1, cZ - 1), (c+1)Z - 1), the last chunk through nz - 1 and
+  // plane 0.  Every black plane is swept once, after the red planes beside it.
+  static int chunked_sweep(fm_state* st, const Lvl<T>& L, const Phys<T>& P, int Z, cudaStream_t s) {
+    const int ny = L.g.ny, nz = L.g.nz, half = L.g.nx >> 1;
+    const int nch = nz / Z;
+    for (int c = 0; c < nch; ++c) {
+      int rows = Z * ny;
+      k_smooth_rows<T, KIND, DIM><<<nblocks((long long)rows * half), TPB, 0, s>>>(L, P, 0, c * Z * ny, rows);
+      FM_LAUNCHED();
+      const int b0 = c == 0 ? 1 : c * Z - 1;
+      const int b1 = c == nch - 1 ? nz + 1 : (c + 1) * Z - 1;  // nz + 1: through nz - 1 and plane 0
+      rows = (b1 - b0) * ny;
+      if (rows > 0) {
+        k_smooth_rows<T, KIND, DIM><<<nblocks((long long)rows * half), TPB, 0, s>>>(L, P, 1, b0 * ny, rows);
+        FM_LAUNCHED();
+      }
+    }
+    return FM_OK;
+  }
+
+  // Launch one sweep (a red and a black colour pass) of variant v (3-D) on level L.
   static int launch_colour_pair(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P) {
     const int half = L.g.N / 2;
+    if (v == 2) {
+      const int Z = z_chunk_planes(L.g);
+      return Z ? chunked_sweep(st, L, P, Z, st->stream) : FM_EINVAL;  // no chunking at this size
+    }
     for (int color = 0; color < 2; ++color) {
       if (v == 1)
         k_smooth_occ<T, KIND, DIM><<<nblocks(half), TPB, 0, st->stream>>>(L, P, color);
@@ -329,6 +355,10 @@ struct Solver {
       float best = 1e30f;
       for (int v = 0; v < SM3_NVAR && rc == FM_OK; ++v) {
         rc = launch_colour_pair(st, v, L, P);
+        if (rc == FM_EINVAL) {  // not applicable at this size
+          rc = FM_OK;
+          continue;
+        }
         if (rc) break;
         if (cudaEventRecord(e0, st->stream) != cudaSuccess) { rc = FM_ECUDA; break; }
         for (int k = 0; k < TUNE_REPS && rc == FM_OK; ++k) rc = launch_colour_pair(st, v, L, P);
@@ -564,6 +594,23 @@ struct Solver {
     const int half = L.g.N / 2;
     const int nfused = (DIM == 2 && v >= 0) ? (iters & ~1) : 0;
     const int per = v >= 0 ? sweeps_per_launch(v) : 1;
+    if (DIM == 3 && v == 2) {  // z-chunked sweeps (in place, like the colour launches)
+      const int Z = z_chunk_planes(L.g);
+      if (Z) {
+        const Lvl<T> E = *in_r ? swap_er(L) : L;
+        for (int it = 0; it < iters; ++it) {
+          if (prof && st->npev + 2 <= MAXEV) FM_CUDA(cudaEventRecord(st->pev[st->npev], s));
+          const int rc = chunked_sweep(st, E, P, Z, s);
+          if (rc) return rc;
+          if (prof && st->npev + 2 <= MAXEV) {
+            FM_CUDA(cudaEventRecord(st->pev[st->npev + 1], s));
+            st->npev += 2;
+          }
+        }
+        return FM_OK;
+      }
+      v = 1;  // no chunking at this size
+    }
     for (int it = 0; it < iters;) {
       const bool fused = it < nfused;
       const int nlaunch = fused ? 1 : 2;
