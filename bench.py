@@ -672,15 +672,15 @@ def model_solver(torch, fm, inputs, name):
     if name == "gradflow512":
         rho, _, prm = inputs.pfc512()
         sol = fm.Solver("pfc", (512, 512), prm["h"], alpha=prm["alpha"], precision=fm.FM_MIXED, tol=1e-10,
-                        w_damp=0.3, model=fm.FM_GRADFLOW, max_cycles=200, stream=stream)
+                        w_damp=0.3, model=fm.FM_GRADFLOW, max_cycles=200, stream=stream, **inputs.BENCH_MG_2D)
         return sol, rho, None, 0.02, ("gradflow512: PFC gradient flow (Thm 3.3) from the pfc512 state, s = 0.02, "
                                       "w = 0.3 (the damping this sixth-order flow converges fastest with), mixed, "
-                                      "V(2,2) to 1e-10")
+                                      "V(2,2) to 1e-10, the benchmark hierarchy (coarsest 64, 2 coarse sweeps)")
     rho, vel, prm = inputs.nanocrystal(256)
     sol = fm.Solver("pfc", (256, 256), prm["h"], alpha=prm["alpha"], precision=fm.FM_MIXED, tol=1e-10, w_damp=0.0,
-                    walls=fm.FM_WALLS_Y, u_wall=(-0.1, 0.1), max_cycles=200, stream=stream)
+                    walls=fm.FM_WALLS_Y, u_wall=(-0.1, 0.1), max_cycles=200, stream=stream, **inputs.BENCH_MG_2D)
     return sol, rho, vel, prm["dt"], ("nanocrystal256: 2-D PFC channel (walls at -0.1/+0.1), hexagonal seed, "
-                                      "eps = 0.4, s = 0.02, mixed, V(2,2) to 1e-10")
+                                      "eps = 0.4, s = 0.02, mixed, V(2,2) to 1e-10, the benchmark hierarchy")
 
 
 def secondary_all(torch, fm, inputs, flush, peak):

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 
 #include "fm_state.h"
 
@@ -471,6 +472,11 @@ constexpr int SM3_NVAR = 3;
 static inline int z_chunk_planes(const Geo& g) {
   const double plane = 80.0 * g.nx * (double)g.ny;
   if (plane * g.nz <= 48e6 || g.nz < 4) return 0;
+  const char* fixed = getenv("FM_ZCHUNK");  // planes per chunk, for measurements (a divisor of nz)
+  if (fixed && fixed[0]) {
+    const int z = atoi(fixed);
+    if (z >= 2 && z <= g.nz / 2 && g.nz % z == 0) return z;
+  }
   int best = 0;
   for (int z = 2; z <= g.nz / 2; ++z)
     if (g.nz % z == 0 && plane * z <= 48e6) best = z;

@@ -185,17 +185,21 @@ static int fft_all(fm_state* st, int inverse) {
   }
   for (int ax = 1; ax < st->dim; ++ax) {
     const int n = ns[ax];
-    int TC = 4096 / n;
-    if (TC > 16) TC = 16;
-    if (TC < 1) TC = 1;
-    if (TC > G.nx) TC = G.nx;
-    const size_t smem = (size_t)n * TC * sizeof(double2);
     const int stride = ax == 1 ? G.nx : G.nx * G.ny;
     const int outer = ax == 1 ? G.nz : G.ny;
     const int ostride = ax == 1 ? G.nx * G.ny : G.nx;
+    // TC columns per block: as many as keep at least two blocks per SM (one
+    // column per block when the lines are too few), at most 16 and 64 KB of
+    // shared memory; a power of two, so it divides nx
+    int TC = 16;
+    while (TC > 1 && ((G.nx / TC) * outer < 2 * st->sms || (size_t)n * TC * sizeof(double2) > 65536)) TC >>= 1;
+    if (TC > G.nx) TC = G.nx;
+    const size_t smem = (size_t)n * TC * sizeof(double2);
+    int thr = n * TC / 2;  // one butterfly per thread and stage
+    thr = thr > FT ? FT : (thr < 32 ? 32 : thr);
     dim3 grid(G.nx / TC, outer);
-    k_fft_strided<<<grid, FT, smem, s>>>(st->fft.work, n, ilog2(n), stride, ostride, TC, st->fft.tw[ax],
-                                         inverse);
+    k_fft_strided<<<grid, thr, smem, s>>>(st->fft.work, n, ilog2(n), stride, ostride, TC, st->fft.tw[ax],
+                                          inverse);
     if (!launch_ok()) return FM_ECUDA;
   }
   return FM_OK;
