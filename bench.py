@@ -141,12 +141,18 @@ class ClockSampler:
 
 def sweeps_per_launch(variant):
     """Red-black sweeps one launch of fused-sweep variant `variant` runs."""
-    return 2 if variant >= 18 else 1
+    return 1 if variant == 28 else (2 if variant >= 18 else 1)
 
 
 def sweep_kernel(variant, batched):
     """Name of the fused-sweep kernel that variant `variant` launches."""
     pre = "kb_" if batched else "k_"
+    if variant >= 27 and not batched:
+        tile, ns = [("32x16", 2), ("32x16", 1), ("32x32", 2)][variant - 27]
+        return (f"k_smooth_rb2d_tma<float,PFC,{tile}> (tile staged by tensor copies, "
+                + ("two sweeps per launch, halo 4)" if ns == 2 else "one sweep per launch)"))
+    if variant >= 27:  # the batch runs the tensor-copy variants as their cp.async twins
+        variant = {27: 24, 28: 0, 29: 26}[variant]
     if variant >= 24:
         tile = ["32x16", "64x8", "32x32"][variant - 24]
         return f"{pre}smooth_rb2d<float,PFC,{tile}> (two sweeps per launch, halo 4)"

@@ -51,6 +51,8 @@ extern "C" {
                              rho^k <= 0, or (delta = 0, no projection floor) an
                              update that left rho <= 0; the state is unchanged */
 #define FM_ENAN     (-6)  /* non-finite residual */
+#define FM_ETIMEOUT (-7)  /* a bounded wait inside a kernel ran out (a tensor copy that
+                             did not complete within 1 s); the state is unusable */
 
 #define FM_PFC   1        /* local phase-field-crystal functional, Sec. 2.2 / 5.3 */
 #define FM_CDFT  2        /* non-local CDFT functional, Sec. 2.1 / 5.2 */
@@ -320,7 +322,7 @@ int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_
 /* ---- Measurement (no counterpart in the paper). ---- */
 
 /* Number of variants of the 2-D fused red-black sweep. */
-#define FM_SWEEP_VARIANTS 27
+#define FM_SWEEP_VARIANTS 30
 
 /* Variant of the 2-D fused red-black sweep the autotuner chose for `level`
  * at fm_create, and its timings of all FM_SWEEP_VARIANTS variants in ms per
@@ -332,8 +334,11 @@ int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_
  * rows per block); 18..23 the row-marching form that runs two sweeps in one
  * pass (strips and rows as 12..17); 24..26 the tile form that runs two sweeps
  * per tile (tiles 32x16, 64x8, 32x32, halo of four, f and omega from global
- * memory).  The time per launch of a two-sweep variant is halved to give its
- * time per sweep.  In 3-D the variants are 0 (a red and a black launch,
+ * memory); 27..29 the tile form with each tile staged by tensor copies (TMA)
+ * instead of cp.async: 27 as 24, 28 as 0, 29 as 26 (the same updates; on a
+ * level whose rows are not a whole number of 16 bytes they run the cp.async
+ * staging; batches run them as 24, 0 and 26 and do not time them).  The time
+ * per launch of a two-sweep variant is halved to give its time per sweep.  In 3-D the variants are 0 (a red and a black launch,
  * 256-thread blocks, the compiler's register count), 1 (the same bounded to
  * six resident blocks per multiprocessor) and 2 (the sweep in z-chunks sized
  * to stay in L2: red over a chunk, then black over the planes whose
@@ -367,6 +372,16 @@ int fm_narrow(const double* in, float* out, long long n, void* stream);
  * `stream`, synchronised.  For a bit-for-bit comparison with the CUDA
  * conversion. */
 int fm_widen(const float* in, double* out, long long n, void* stream);
+
+/* Diagnostic (no counterpart in the paper): runs the bounded mbarrier wait
+ * of the tensor-copy tile smoother in a one-block kernel on `stream`, on a
+ * barrier that one thread completes (complete = 1) or that nothing completes
+ * (complete = 0), giving up after limit_us microseconds (1 .. 1000000), and
+ * synchronises.  FM_OK when the wait saw the barrier complete, FM_ETIMEOUT
+ * when the limit ran out (the kernel then returns normally and the device
+ * stays usable), FM_EINVAL for a limit out of range.  Not reentrant: calls
+ * that overlap on the GPU share one status word. */
+int fm_wait_selftest(int complete, int limit_us, void* stream);
 
 /* ---- Allocation-free entry point (the paper has no counterpart). ---- */
 

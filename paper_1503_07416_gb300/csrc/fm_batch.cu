@@ -633,6 +633,10 @@ struct Batch {
       case 23: return launch_m2<128>(b, l, dir, 23);
       case 24: return launch_v<32, 16, false, false, 2>(b, l, dir);
       case 25: return launch_v<64, 8, false, false, 2>(b, l, dir);
+      // 27..29 (tile staging by tensor copies in the single-instance
+      // solver): the same tiles staged by cp.async here
+      case 27: return launch_v<32, 16, false, false, 2>(b, l, dir);
+      case 28: return launch_v<32, 16, false, false>(b, l, dir);
       default: return launch_v<32, 32, false, false, 2>(b, l, dir);
     }
   }
@@ -680,7 +684,7 @@ struct Batch {
     int rc = FM_OK;
     for (int l = 0; l < b->maxdepth && rc == FM_OK; ++l) {
       float best = 1e30f;
-      for (int v = 0; v < RB_NVAR && rc == FM_OK; ++v) {
+      for (int v = 0; v < RB_TMA0 && rc == FM_OK; ++v) {  // 27..29 repeat 24, 0, 26 here
         rc = launch_variant(b, v, l);
         if (rc == FM_EINVAL) {  // does not fit in shared memory: skip
           rc = FM_OK;

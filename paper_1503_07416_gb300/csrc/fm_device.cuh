@@ -5,6 +5,7 @@
 // level, each as a device function with a thin kernel wrapper.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the descriptor type only; no driver calls here)
 #include <cuda_runtime.h>
 #include <cmath>
 #include <cstring>
@@ -739,6 +740,125 @@ __global__ void __launch_bounds__(rb_threads(TX, TY), rb_minb<T>(TX, TY)) k_smoo
 }
 
 // --------------------------------------------------------------------------
+// Tile staging by tensor copies (TMA)
+// --------------------------------------------------------------------------
+// The staged arrays of the two-sweep tile form are one box each: SW x (TY +
+// 2H) values from (x0 - RB_XO, y0 - H), the layout the tile already has in
+// shared memory.  One thread issues one cp.async.bulk.tensor per array onto
+// an mbarrier that expects the bytes of all of them; every thread then waits
+// on it, with a time limit.  A box that crosses the periodic boundary gets
+// zeros there from the copy (the tensor map does not wrap), and those cells
+// are then loaded with their wrapped values by plain loads.  The x coordinate
+// x0 - RB_XO is a multiple of 4 elements (16 bytes) for every tile.
+struct RbMaps {
+  CUtensorMap m[MAXU + 4];  // staged arrays in rb2d_issue order: e (or r) [NU], rk, cr, cv0, cv1
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of the mbarrier for at most `limit_ns`; false when
+// the limit ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+constexpr unsigned long long TMA_WAIT_NS = 1000000000ull;  // 1 s: a tile's copies take microseconds
+
+// One tile per block, staged by tensor copies, then the passes of
+// rb2d_compute (the same updates, in the same order, as k_smooth_rb2d with
+// SF = false and PIPE = false).  If the copies do not complete within the
+// limit the block sets *fault, waits once more for them and returns without
+// writing its tile (the step then reports FM_ETIMEOUT).
+template <typename T, int KIND, int TX, int TY, int NS>
+__global__ void __launch_bounds__(rb_threads(TX, TY), rb_minb<T>(TX, TY))
+    k_smooth_rb2d_tma(Lvl<T> G, Phys<T> P, int ntx, int ntiles, int dir, const __grid_constant__ RbMaps maps,
+                      int* fault) {
+  using Gm = RBGeom<TX, TY, NS>;
+  constexpr int NU = Layout<KIND, 2>::NU;
+  constexpr int NA = rb_arrays<KIND, false>();
+  constexpr int SN = Gm::SN, SW = Gm::SW;
+  constexpr unsigned ABYTES = SN * sizeof(T);  // a multiple of 128 for the tiles instantiated
+  static_assert(ABYTES % 128 == 0, "each staged array must start on a 128-byte boundary");
+  __shared__ __align__(8) unsigned long long bar;
+  const int t = blockIdx.x;
+  if (t >= ntiles) return;
+  const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
+  const unsigned s0 = smem_u32(fm_dyn_smem);
+  const unsigned sa = (s0 + 127u) & ~127u;  // the launch adds 128 bytes for this
+  const int base = (int)((sa - s0) / sizeof(T));
+  const unsigned b = smem_u32(&bar);
+  if (threadIdx.x == 0) mbar_init(b, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(b, NA * ABYTES);
+#pragma unroll
+    for (int a = 0; a < NA; ++a) tma_load_2d(sa + a * ABYTES, &maps.m[a], x0 - RB_XO, y0 - Gm::H, b);
+  }
+  if (!__syncthreads_and(mbar_wait(b, 0, TMA_WAIT_NS))) {
+    if (threadIdx.x == 0) atomicExch(fault, 1);
+    mbar_wait(b, 0, TMA_WAIT_NS);  // the copies may still be in flight
+    return;
+  }
+  const int nx = G.g.nx, ny = G.g.ny;
+  if (x0 - RB_XO < 0 || x0 + TX + RB_XO > nx || y0 - Gm::H < 0 || y0 + TY + Gm::H > ny) {
+    T* buf = reinterpret_cast<T*>(fm_dyn_smem) + base;
+    const T* src[NA];
+#pragma unroll
+    for (int q = 0; q < NU; ++q) src[q] = dir ? G.r[q] : G.e[q];
+    src[NU + 0] = G.rk;
+    src[NU + 1] = G.cr;
+    src[NU + 2] = G.cv[0];
+    src[NU + 3] = G.cv[1];
+    for (int c = threadIdx.x; c < SN; c += blockDim.x) {
+      const int ly = c / SW, lx = c - ly * SW;
+      const int gx = x0 - RB_XO + lx, gy = y0 - Gm::H + ly;
+      if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) {
+        const int gi = wrapi(gy, ny) * nx + wrapi(gx, nx);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) buf[a * SN + c] = src[a][gi];
+      }
+    }
+    __syncthreads();
+  }
+  rb2d_compute<T, KIND, TX, TY, false, NS>(G, P, base, x0, y0, dir);
+}
+
+// --------------------------------------------------------------------------
 // 2-D fused red-black sweep, row-marching form
 // --------------------------------------------------------------------------
 // A block owns the columns [x0, x0 + TX) of rows [y0, y1) of one level and
@@ -1075,8 +1195,11 @@ __global__ void __launch_bounds__(march_threads(TX), march2_minb<T>(TX)) k_smoot
 // 12..17 marching form (strip width 64 or 128; rows per block 16, 32, 64),
 // 18..23 the two-sweep marching form with the same strips and rows, 24..26
 // the two-sweep tile form (tiles 32x16, 64x8, 32x32; f and omega from global
-// memory, one tile per block).
+// memory, one tile per block), 27..29 tiles staged by tensor copies (27: as
+// 24, 28: as 0, 29: as 26; single-instance solver only -- the batch runs
+// them as their cp.async twins).
 constexpr int RB_NVAR = FM_SWEEP_VARIANTS;
+constexpr int RB_TMA0 = 27;  // first variant staged by tensor copies
 constexpr int TUNE_REPS = 10;  // timed launches per variant and level in the autotuners
 constexpr int RB_NTILE = 12;
 constexpr int RB_NMARCH = 6;
@@ -1084,10 +1207,11 @@ constexpr int RB_TWO = RB_NTILE + RB_NMARCH;  // first two-sweep variant
 constexpr int RB_TWO_TILE = RB_TWO + RB_NMARCH;  // first two-sweep tile variant
 __host__ __device__ constexpr int march_tx(int v) { return (v - RB_NTILE) % RB_NMARCH < 3 ? 64 : 128; }
 __host__ __device__ constexpr int march_ly(int v) { return 16 << ((v - RB_NTILE) % 3); }
-__host__ __device__ constexpr int sweeps_per_launch(int v) { return v >= RB_TWO ? 2 : 1; }
+__host__ __device__ constexpr int sweeps_per_launch(int v) { return (v >= RB_TWO && v != RB_TMA0 + 1) ? 2 : 1; }
 // The one-sweep variant with the same blocks as two-sweep variant v.
 __host__ __device__ constexpr int one_sweep_twin(int v) {
-  return v >= RB_TWO_TILE ? (v - RB_TWO_TILE) * 4 : (v >= RB_TWO ? v - RB_NMARCH : v);
+  return v >= RB_TMA0 ? (v == RB_TMA0 ? RB_TMA0 + 1 : (v == RB_TMA0 + 2 ? 8 : v))
+                      : (v >= RB_TWO_TILE ? (v - RB_TWO_TILE) * 4 : (v >= RB_TWO ? v - RB_NMARCH : v));
 }
 
 // The whole V-cycle of the small levels (each at most SMALL_N points) in one
@@ -2041,7 +2165,7 @@ struct Ctl {
   int active;   // batch: the instance still iterates
   int nonpos;   // CDFT: a density <= 0 reached ln this step (FM_ENONPOS)
   int hist;     // converged iterates kept for the extrapolated initial iterate (0, 1 or 2)
-  int pad;
+  int fault;    // a bounded wait inside a kernel ran out (FM_ETIMEOUT; never cleared)
 };
 
 // Initial iterate extrapolated in time (fm_params.init = FM_INIT_EXTRAPOLATE),
@@ -2117,7 +2241,8 @@ __device__ __forceinline__ bool norm_ctl_body(const double* partials, int nblk, 
     ctl->norm = nrm;
     if (!in_body) ctl->norm0 = nrm;
     int status = FM_OK;
-    if (ctl->nonpos) status = FM_ENONPOS;
+    if (ctl->fault) status = FM_ETIMEOUT;
+    else if (ctl->nonpos) status = FM_ENONPOS;
     else if (!finite) status = FM_ENAN;
     else if (nrm > tol && cycles >= max_cycles) status = FM_ENOCONV;
     ctl->status = status;

@@ -19,6 +19,8 @@
 //  * Transfers: nodal full weighting of r, injection of e and of the
 //    coefficients, bilinear/trilinear prolongation of the coarse correction.
 //  * Coarsest grid: one thread block runs ncoarse red-black iterations.
+#include <cuda.h>
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
 #include <cuda_runtime.h>
 #include <cstdio>
 #include <cstdlib>
@@ -141,6 +143,78 @@ static int launch_rb_v(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStre
   return FM_OK;
 }
 
+// cuTensorMapEncodeTiled, taken from the driver through the runtime (libfm
+// links only the runtime); null when the driver does not provide it.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tensor map of one level array (nx x ny values of T, rows contiguous) with
+// a box of bw x bh values; false where a tensor copy cannot address it (a
+// row that is not a whole number of 16 bytes, a base not on a 16-byte
+// boundary) or the driver refuses it.
+template <typename T>
+static bool encode_box_map(CUtensorMap* m, const void* base, const Geo& g, int bw, int bh) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || !base || g.nz != 1) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((size_t)g.nx * sizeof(T)) % 16) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)g.nx * sizeof(T)};
+  const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+             const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tile form (SF = PIPE = false) with the tile staged by tensor copies; on a
+// level whose arrays a tensor copy cannot address, the same tile form staged
+// by cp.async (the same updates).
+template <typename T, int KIND, int TX, int TY, int NS>
+static int launch_rb_tma(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int dir) {
+  using Gm = RBGeom<TX, TY, NS>;
+  constexpr int NU = Layout<KIND, 2>::NU;
+  constexpr size_t smem = rb_smem_bytes<T, KIND, TX, TY, false, false, NS>() + 128;  // + alignment to 128 B
+  if (smem + 4096 > (size_t)st->smem_optin) return FM_EINVAL;
+  if (!L.r[0]) return FM_EINVAL;
+  RbMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  const void* src[NU + 4];
+  for (int q = 0; q < NU; ++q) src[q] = dir ? L.r[q] : L.e[q];
+  src[NU + 0] = L.rk;
+  src[NU + 1] = L.cr;
+  src[NU + 2] = L.cv[0];
+  src[NU + 3] = L.cv[1];
+  bool ok = true;
+  for (int a = 0; a < NU + 4 && ok; ++a) ok = encode_box_map<T>(&maps.m[a], src[a], L.g, Gm::SW, TY + 2 * Gm::H);
+  if (!ok) return launch_rb_v<T, KIND, TX, TY, false, false, NS>(st, L, P, s, dir);
+  static bool attr = false;
+  if (!attr) {
+    FM_CUDA(cudaFuncSetAttribute(k_smooth_rb2d_tma<T, KIND, TX, TY, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    attr = true;
+  }
+  const int ntx = (L.g.nx + TX - 1) / TX;
+  const int ntiles = ntx * ((L.g.ny + TY - 1) / TY);
+  k_smooth_rb2d_tma<T, KIND, TX, TY, NS><<<ntiles, rb_threads(TX, TY), smem, s>>>(
+      L, P, ntx, ntiles, dir, maps, &static_cast<Ctl*>(st->ctl)->fault);
+  return FM_OK;
+}
+
 // Launch the row-marching form (strip width TX, ly rows per block) on level L.
 template <typename T, int KIND, int TX>
 static int launch_march(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int dir, int ly) {
@@ -209,7 +283,10 @@ static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cud
     case 23: return launch_march2<T, KIND, 128>(st, L, P, s, dir, 64);
     case 24: return launch_rb_v<T, KIND, 32, 16, false, false, 2>(st, L, P, s, dir);
     case 25: return launch_rb_v<T, KIND, 64, 8, false, false, 2>(st, L, P, s, dir);
-    default: return launch_rb_v<T, KIND, 32, 32, false, false, 2>(st, L, P, s, dir);
+    case 26: return launch_rb_v<T, KIND, 32, 32, false, false, 2>(st, L, P, s, dir);
+    case 27: return launch_rb_tma<T, KIND, 32, 16, 2>(st, L, P, s, dir);
+    case 28: return launch_rb_tma<T, KIND, 32, 16, 1>(st, L, P, s, dir);
+    default: return launch_rb_tma<T, KIND, 32, 32, 2>(st, L, P, s, dir);
   }
 }
 
@@ -237,6 +314,16 @@ static Lvl<T> swap_er(Lvl<T> L) {
   return L;
 }
 
+
+// FM_ETIMEOUT if a kernel of this state gave up a bounded wait (the control
+// block's fault flag; synchronises the stream).
+static int read_fault(fm_state* st) {
+  int fault = 0;
+  FM_CUDA(cudaMemcpyAsync(&fault, &static_cast<Ctl*>(st->ctl)->fault, sizeof(int), cudaMemcpyDeviceToHost,
+                          st->stream));
+  FM_CUDA(cudaStreamSynchronize(st->stream));
+  return fault ? FM_ETIMEOUT : FM_OK;
+}
 
 // The step is issued in three parts:
 //   pre  : omega^k, (J * rho^k), S, g^0, coefficients rho^k/omega^k down the
@@ -430,7 +517,7 @@ struct Solver {
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       cudaGetLastError();
-      return rc;
+      return rc ? rc : read_fault(st);
     }
   }
 
@@ -579,8 +666,7 @@ struct Solver {
       FM_LAUNCHED();
       FM_CUDA(cudaMemcpyAsync(e[q], st->r64[q], bytes, kind_out(where), s));
     }
-    FM_CUDA(cudaStreamSynchronize(s));
-    return FM_OK;
+    return read_fault(st);
   }
 
   // `iters` sweeps on level L (its physical buffers; the correction is in
@@ -928,6 +1014,7 @@ const char* fm_strerror(int code) {
     case FM_ENOCONV: return "no convergence within max_cycles";
     case FM_ENONPOS: return "non-positive density";
     case FM_ENAN: return "non-finite residual";
+    case FM_ETIMEOUT: return "a bounded wait inside a kernel ran out";
     default: return "unknown error";
   }
 }
@@ -1292,6 +1379,36 @@ int fm_widen(const float* in, double* out, long long n, void* stream) {
   if (cudaGetLastError() != cudaSuccess) return FM_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return FM_ECUDA;
   return FM_OK;
+}
+
+// Status word of fm_wait_selftest.
+__device__ int g_wait_status;
+
+// One block: an mbarrier of one arrival, completed by thread 0 or by nobody,
+// then the bounded wait of the tensor-copy smoother in every thread.
+__global__ void k_wait_selftest(int complete, unsigned long long limit_ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  const unsigned b = smem_u32(&bar);
+  if (threadIdx.x == 0) mbar_init(b, 1);
+  __syncthreads();
+  if (complete && threadIdx.x == 0) mbar_arrive(b);
+  const bool ok = __syncthreads_and(mbar_wait(b, 0, limit_ns));
+  if (threadIdx.x == 0) g_wait_status = ok ? FM_OK : FM_ETIMEOUT;
+}
+
+int fm_wait_selftest(int complete, int limit_us, void* stream) {
+  if (limit_us < 1 || limit_us > 1000000) return FM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int unset = FM_ECUDA;
+  if (cudaMemcpyToSymbolAsync(g_wait_status, &unset, sizeof(int), 0, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return FM_ECUDA;
+  k_wait_selftest<<<1, 64, 0, s>>>(complete ? 1 : 0, 1000ull * (unsigned long long)limit_us);
+  if (cudaGetLastError() != cudaSuccess) return FM_ECUDA;
+  int status = FM_ECUDA;
+  if (cudaMemcpyFromSymbolAsync(&status, g_wait_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FM_ECUDA;
+  return status;
 }
 
 // Weighted energy sums of the current state into q[0..4]: KE, then the PFC

@@ -22,6 +22,7 @@ FM_ECUDA = -3
 FM_ENOCONV = -4
 FM_ENONPOS = -5
 FM_ENAN = -6
+FM_ETIMEOUT = -7
 FM_PFC = 1
 FM_CDFT = 2
 FM_FP64 = 0
@@ -94,6 +95,7 @@ _SIGS = {
     "fm_levels": (C.c_int, [C.c_void_p]),
     "fm_narrow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "fm_widen": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
+    "fm_wait_selftest": (C.c_int, [C.c_int, C.c_int, C.c_void_p]),
     "fm_smooth": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int]),
     "fm_create_batch": (C.c_int, [C.c_int, C.POINTER(fm_grid), C.POINTER(fm_params), C.POINTER(fm_functional),
                                   C.POINTER(C.c_void_p)]),
@@ -280,7 +282,7 @@ def fm_residual(st, g, r=None):
     return nrm.value
 
 
-FM_SWEEP_VARIANTS = 27
+FM_SWEEP_VARIANTS = 30
 FM_SWEEP_AUTO = -1
 FM_SWEEP_TWO_COLOUR = -2
 
@@ -297,6 +299,12 @@ def fm_narrow(inp, out, stream=None):
     residual kernels narrow the float32 right-hand side."""
     _check(lib().fm_narrow(C.c_void_p(inp.data_ptr()), C.c_void_p(out.data_ptr()), inp.numel(),
                            C.c_void_p(stream)), "fm_narrow")
+
+
+def fm_wait_selftest(complete, limit_us, stream=None):
+    """Status (FM_OK or FM_ETIMEOUT) of the smoother's bounded mbarrier wait
+    on a barrier that is completed (complete=True) or that nothing completes."""
+    return lib().fm_wait_selftest(1 if complete else 0, int(limit_us), C.c_void_p(stream))
 
 
 def fm_widen(inp, out, stream=None):

@@ -37,8 +37,11 @@ def test_default_params_and_strerror(lib):
     p = fm.fm_default_params()
     assert p.gamma == 2.0 and p.nu1 == 2 and p.nu2 == 2 and p.sigma == 1.0
     assert p.precision == fm.FM_FP64 and p.tol == 1e-10
-    for code in (fm.FM_OK, fm.FM_EINVAL, fm.FM_ENOCONV, fm.FM_ENAN, fm.FM_ECUDA):
-        assert isinstance(fm.strerror(code), str) and fm.strerror(code)
+    codes = (fm.FM_OK, fm.FM_EINVAL, fm.FM_ENOMEM, fm.FM_ECUDA, fm.FM_ENOCONV, fm.FM_ENONPOS, fm.FM_ENAN,
+             fm.FM_ETIMEOUT)
+    msgs = [fm.strerror(code) for code in codes]
+    assert all(isinstance(m, str) and m and m != "unknown error" for m in msgs)
+    assert len(set(msgs)) == len(codes)
 
 
 def _create(dim=2, n=(8, 8, 1), h=0.5, kind=fm.FM_PFC, nu=1.0, **kw):
@@ -101,3 +104,9 @@ def test_mass_noalloc_wrapper_checks_its_arguments(lib):
         fm.fm_mass_noalloc(torch.zeros((8, 8), dtype=torch.float64), 1.0, out_cpu)
     with pytest.raises(ValueError):
         fm.fm_mass_noalloc(torch.zeros((8, 8), dtype=torch.float32), 1.0, out_cpu)
+
+
+def test_wait_selftest_rejects_limits_out_of_range(lib):
+    """Checked before any device work (no GPU needed)."""
+    for limit in (0, -5, 1000001):
+        assert fm.fm_wait_selftest(True, limit) == fm.FM_EINVAL

@@ -9,6 +9,7 @@ system; the two solvers' iterates differ, the fixed point does not.
 """
 import functools
 import math
+import time
 
 import numpy as np
 import pytest
@@ -385,6 +386,23 @@ def test_no_convergence_leaves_state_unchanged():
     assert code == fm.FM_ENOCONV
     rg, vg = sol.get_fields()
     assert np.array_equal(rg, rho) and all(np.array_equal(a, b) for a, b in zip(vg, vel))
+
+
+def test_bounded_wait_runs_out_with_etimeout_and_the_device_stays_usable():
+    """The tensor-copy smoother waits on its copies with a time limit; the
+    same wait on a barrier that nothing completes gives up after the limit
+    (2 ms here) and reports FM_ETIMEOUT instead of hanging, and a completed
+    barrier passes.  A step on the same device afterwards is normal."""
+    assert fm.fm_wait_selftest(True, 2000) == fm.FM_OK
+    t0 = time.perf_counter()
+    assert fm.fm_wait_selftest(False, 2000) == fm.FM_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert fm.fm_wait_selftest(True, 2000) == fm.FM_OK
+    rho, vel, prm = inputs.pfc64()
+    sol = gpu_solver(rho, prm)
+    sol.set_fields(rho, vel)
+    code, info = fm.fm_step_raw(sol.handle, prm["dt"])
+    assert code == fm.FM_OK and info.res <= prm["tol"]
 
 
 def test_nan_input_reports_enan():

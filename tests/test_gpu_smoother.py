@@ -162,6 +162,31 @@ def test_two_sweep_pass_equals_one_sweep_passes(kind, shape, precision, monkeypa
                 assert np.array_equal(a, b), (sweeps, v2, q, float(np.max(np.abs(a - b))))
 
 
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+@pytest.mark.parametrize("kind,shape", [("pfc", (256, 512)), ("pfc", (136, 200)), ("pfc", (64, 64)),
+                                        ("pfc", (1000, 1002)), ("cdft", (64, 128))])
+def test_tensor_copy_staging_equals_cp_async_staging(kind, shape, precision, monkeypatch):
+    """Variants 27..29 stage each tile with one tensor copy per array (zeros
+    outside the grid, then the wrapped values by plain loads) and run the same
+    updates as 24, 0 and 26, so the results agree bit for bit: on a grid of
+    interior and boundary tiles, a ragged one, one where every tile crosses
+    the periodic boundary, and one whose rows are not a whole number of 16
+    bytes (staged by cp.async there); 2 and 3 sweeps."""
+    monkeypatch.setenv("FM_RB_VARIANT", "0")  # no autotuning at create
+    rho, vel, prm = _case(kind, shape, 11)
+    f, _ = _oracle(rho, vel, prm, 0.0, 0)
+    for sweeps in (2, 3):
+        for vt, vc in ((27, 24), (28, 0), (29, 26)):
+            try:
+                ref = _gpu(rho, vel, prm, f, precision, 0.0, sweeps, vc)
+                tma = _gpu(rho, vel, prm, f, precision, 0.0, sweeps, vt)
+            except fm.FMError as err:
+                assert err.code == fm.FM_EINVAL and precision == fm.FM_FP64
+                continue
+            for q, (a, b) in enumerate(zip(tma, ref)):
+                assert np.array_equal(a, b), (sweeps, vt, q, float(np.max(np.abs(a - b))))
+
+
 def test_smooth_row_rejects_bad_arguments():
     rho, vel, prm = _case("cdft", (32, 32), 7)
     sol = gpu_solver(rho, prm)
