@@ -555,8 +555,9 @@ def smoother_sweeps_per_launch(fm, sol, dim):
 def sweeps_per_launch_3d(variant):
     """3-D smoother variants (fm_tuning): 0 and 1 run a red and a black launch
     per sweep (half a sweep per timed launch); 2 runs a sweep in z-chunks and
-    its timing events bracket the whole sweep."""
-    return 1 if variant == 2 else 0.5
+    its timing events bracket the whole sweep; 3 and 4 (z-marching) run one
+    sweep per launch."""
+    return 1 if variant >= 2 else 0.5
 
 
 def secondary_single(torch, fm, flush, kind, rho, vel, prm, precision, steps, warmup=2, dim=2, smoother=False,

@@ -258,10 +258,11 @@ int fm_levels(const fm_state* st);
  * as fm_step does (2-D: the autotuned fused sweep over the largest even
  * number of sweeps, an odd last sweep as two colour launches);
  * FM_SWEEP_TWO_COLOUR runs every sweep as a red launch and a black launch;
- * 0 .. FM_SWEEP_VARIANTS - 1 fixes the fused variant (2-D only, encoding as
- * fm_tuning).  FM_EINVAL before the first fm_prepare, for
- * sweeps < 0, an unknown variant, a fused variant in 3-D or one that does not
- * fit in shared memory. */
+ * 0 .. FM_SWEEP_VARIANTS - 1 fixes the fused variant (encoding as fm_tuning;
+ * in 3-D 0 .. 4, a z-marching variant falling back to the colour launches on
+ * a level it does not fit).  FM_EINVAL before the first fm_prepare, for
+ * sweeps < 0, an unknown variant or a 2-D variant that does not fit in
+ * shared memory. */
 #define FM_SWEEP_AUTO (-1)
 #define FM_SWEEP_TWO_COLOUR (-2)
 int fm_smooth(fm_state* st, double* const* e, const double* const* f, int sweeps, int variant,
@@ -343,8 +344,11 @@ int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_
  * six resident blocks per multiprocessor) and 2 (the sweep in z-chunks sized
  * to stay in L2: red over a chunk, then black over the planes whose
  * neighbours are red by then; levels whose arrays fit in 48 MB are not
- * chunked and report 0 for it); their times are per sweep.  Setting the
- * environment variable
+ * chunked and report 0 for it), 3 and 4 (one launch per sweep, marching up
+ * the planes of 32 x 8 or 32 x 16 point tiles staged plane by plane in
+ * shared memory by bulk copies; levels whose sides are not multiples of the
+ * tile report 0 for them and sweep with variant 1); their times are per
+ * sweep.  Setting the environment variable
  * FM_RB_VARIANT=v before fm_create fixes the variant (no timing). */
 int fm_tuning(const fm_state* st, int level, int* variant, float* ms_per_variant);
 

@@ -460,12 +460,15 @@ __global__ void __launch_bounds__(TPB, 6) k_smooth_rows(Lvl<T> L, Phys<T> P, int
   smooth_point<T, KIND, DIM>(L, P, make_ptk<T, DIM>(P, L.h), n);
 }
 
-// 3-D colour-sweep variants: 0 k_smooth, 1 k_smooth_occ, 2 the same sweep in
+// 3-D sweep variants: 0 k_smooth, 1 k_smooth_occ, 2 the same sweep in
 // z-chunks (z_chunk_planes): red over a chunk, then black over the planes
 // whose z-neighbours are all red by then, so the black launch finds the
 // chunk's arrays in L2; the same updates in the same order of dependence as
-// a red and a black launch over the whole level.
-constexpr int SM3_NVAR = 3;
+// a red and a black launch over the whole level; 3 and 4 the fused
+// z-marching sweep (fm_zmarch.cuh) with 32 x 8 and 32 x 16 tiles, one launch
+// per sweep, reading the correction from one buffer and writing the other.
+constexpr int SM3_NVAR = 5;
+constexpr int SM3_ZM = 3;  // first z-marching variant
 
 // Planes per chunk: the largest divisor of nz whose arrays (about 20 float
 // words a point) stay within 48 MB, at least 2; 0 (no chunking) when the

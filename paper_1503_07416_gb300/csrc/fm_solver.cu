@@ -31,6 +31,7 @@
 #include "fm_state.h"
 #include "fm_device.cuh"
 #include "fm_stepper.cuh"
+#include "fm_zmarch.cuh"
 
 namespace fm {
 
@@ -290,6 +291,58 @@ static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cud
   }
 }
 
+// Launch the 3-D z-marching sweep (tiles 32 x TY) on level L: one block per
+// tile and z-chunk, as many blocks as there are resident slots (at most nz / 2
+// chunks a tile): nchunks = slots / ntile chunks for the first nlong tiles,
+// one more for the others.  FM_EINVAL where it does not apply (sides not
+// multiples of the tile, no second correction buffer, shared memory too
+// small).
+template <typename T, int KIND, int TY>
+static bool zm3_applies_v(const fm_state* st, const Lvl<T>& L) {
+  constexpr size_t smem = zm_smem_bytes<T, KIND, TY>();
+  return smem + 1024 <= (size_t)st->smem_optin && L.r[0] && L.g.nx % ZmGeom<TY>::TX == 0 && L.g.ny % TY == 0 &&
+         L.g.nz >= 2 && (L.g.nz & 1) == 0;
+}
+
+template <typename T, int KIND>
+static bool zm3_applies(const fm_state* st, int v, const Lvl<T>& L) {
+  return v == SM3_ZM ? zm3_applies_v<T, KIND, 8>(st, L) : zm3_applies_v<T, KIND, 16>(st, L);
+}
+
+template <typename T, int KIND, int TY>
+static int launch_zm3_v(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int dir) {
+  constexpr size_t smem = zm_smem_bytes<T, KIND, TY>();
+  if constexpr (smem > 232448) {  // beyond any device's shared memory per block: not instantiated
+    return FM_EINVAL;
+  } else {
+  if (!zm3_applies_v<T, KIND, TY>(st, L)) return FM_EINVAL;
+  static int per_sm = 0;
+  if (!per_sm) {
+    if (cudaFuncSetAttribute(k_smooth_zm3<T, KIND, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_zm3<T, KIND, TY>, ZmGeom<TY>::THREADS,
+                                                      smem) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 0;
+      return FM_ECUDA;
+    }
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int ntile = (L.g.nx / ZmGeom<TY>::TX) * (L.g.ny / TY);
+  long long nblk = (long long)per_sm * st->sms;
+  if (nblk > (long long)ntile * (L.g.nz / 2)) nblk = (long long)ntile * (L.g.nz / 2);
+  if (nblk < ntile) nblk = ntile;
+  const int nchunks = (int)(nblk / ntile), nlong = ntile - (int)(nblk % ntile);
+  k_smooth_zm3<T, KIND, TY><<<(int)nblk, ZmGeom<TY>::THREADS, smem, s>>>(L, P, dir, nchunks, nlong);
+  return FM_OK;
+  }
+}
+
+template <typename T, int KIND>
+static int launch_zm3(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int dir) {
+  return v == SM3_ZM ? launch_zm3_v<T, KIND, 8>(st, L, P, s, dir) : launch_zm3_v<T, KIND, 16>(st, L, P, s, dir);
+}
+
 // e = r on every point of a level (the correction back in e).
 template <typename T, int NU>
 __global__ void __launch_bounds__(TPB) k_copy_back(Lvl<T> L) {
@@ -406,6 +459,14 @@ struct Solver {
   // Launch one sweep (a red and a black colour pass) of variant v (3-D) on level L.
   static int launch_colour_pair(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P) {
     const int half = L.g.N / 2;
+    if (v >= SM3_ZM) {
+      if constexpr (DIM == 3) {
+        const int rc = launch_zm3<T, KIND>(st, v, L, P, st->stream, 0);
+        if (rc == FM_OK) FM_LAUNCHED();
+        return rc;
+      }
+      return FM_EINVAL;
+    }
     if (v == 2) {
       const int Z = z_chunk_planes(L.g);
       return Z ? chunked_sweep(st, L, P, Z, st->stream) : FM_EINVAL;  // no chunking at this size
@@ -635,7 +696,7 @@ struct Solver {
   // staged through the float64 scratch r64 and rounded to T).
   static int smooth_row(fm_state* st, double* const* e, const double* const* f, int sweeps, int variant,
                         int where) {
-    if (variant < FM_SWEEP_TWO_COLOUR || variant >= RB_NVAR || (DIM == 3 && variant >= 0)) return FM_EINVAL;
+    if (variant < FM_SWEEP_TWO_COLOUR || variant >= (DIM == 3 ? SM3_NVAR : RB_NVAR)) return FM_EINVAL;
     const Geo G = st->lv[0].g;
     cudaStream_t s = st->stream;
     // coefficient copies of the iterate (mixed path), as at the start of a cycle
@@ -654,9 +715,10 @@ struct Solver {
       FM_LAUNCHED();
     }
     const Phys<T> P = make_phys<T>(st);
-    const int v = (DIM == 2 && variant != FM_SWEEP_TWO_COLOUR && (st->fused_rb || variant >= 0))
-                      ? (variant >= 0 ? variant : st->rbv[0])
-                      : -1;
+    int v = (DIM == 2 && variant != FM_SWEEP_TWO_COLOUR && (st->fused_rb || variant >= 0))
+                ? (variant >= 0 ? variant : st->rbv[0])
+                : -1;
+    if (DIM == 3 && variant != FM_SWEEP_TWO_COLOUR) v = variant >= 0 ? variant : st->rbv[0];
     int in_r = 0;
     rc = run_sweeps(st, L, v, P, sweeps, &in_r, false);
     if (rc) return rc;
@@ -680,6 +742,23 @@ struct Solver {
     const int half = L.g.N / 2;
     const int nfused = (DIM == 2 && v >= 0) ? (iters & ~1) : 0;
     const int per = v >= 0 ? sweeps_per_launch(v) : 1;
+    if (DIM == 3 && v >= SM3_ZM && !zm3_applies<T, KIND>(st, v, L)) v = 1;  // not at this level's size
+    if (DIM == 3 && v >= SM3_ZM) {  // fused z-marching sweeps, one launch each, e and r alternating
+      for (int it = 0; it < iters; ++it) {
+        if (prof && st->npev + 2 <= MAXEV) FM_CUDA(cudaEventRecord(st->pev[st->npev], s));
+        if constexpr (DIM == 3) {
+          const int rc = launch_zm3<T, KIND>(st, v, L, P, s, *in_r);
+          if (rc) return rc;
+        }
+        FM_LAUNCHED();
+        if (prof && st->npev + 2 <= MAXEV) {
+          FM_CUDA(cudaEventRecord(st->pev[st->npev + 1], s));
+          st->npev += 2;
+        }
+        *in_r ^= 1;
+      }
+      return FM_OK;
+    }
     if (DIM == 3 && v == 2) {  // z-chunked sweeps (in place, like the colour launches)
       const int Z = z_chunk_planes(L.g);
       if (Z) {

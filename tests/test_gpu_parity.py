@@ -101,15 +101,16 @@ def test_smallest_grid():
     _compare_step(rho, vel, prm, fm.FM_FP64, w_damp=0.0, ncoarse=40)
 
 
-@pytest.mark.parametrize("variant", ["0", "1", "2"])
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3", "4"])
 @pytest.mark.parametrize("n", [16, 32])
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
 def test_3d_pfc(precision, n, variant, monkeypatch):
     """3-D PFC with random velocity (three vorticity components): 16^3 (one
     level, its sweeps as red and black launches over the whole grid) and 32^3
     (two levels, the 16^3 coarsest grid smoothed by multi-block launches);
-    every 3-D colour-sweep variant (1 bounded to six blocks per SM; 2 falls
-    back to 1 at these sizes, whose arrays fit in L2)."""
+    every 3-D sweep variant (1 bounded to six blocks per SM; 2 falls back to 1
+    at these sizes, whose arrays fit in L2; 3 and 4, the z-marching sweep,
+    run on the 32^3 level and fall back to 1 on the 16^3 one)."""
     monkeypatch.setenv("FM_RB_VARIANT", variant)
     rng = np.random.default_rng(6)
     rho = 0.8 + 0.05 * rng.uniform(-1, 1, (n, n, n))
@@ -320,6 +321,33 @@ def test_3d_z_chunked_sweeps_match_whole_level_sweeps(precision, monkeypatch):
     (rb, vb), cb = res["2"]
     assert ca == cb
     assert_parity(rb, vb, ra, va, 1e-12 if precision == fm.FM_FP64 else 1e-9)
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_3d_z_marching_steps_match_colour_launches(precision, monkeypatch):
+    """Steps with the z-marching sweeps (variants 3 and 4) on every level
+    they fit, against the colour launches (variant 1): on a 96 x 64 x 128
+    grid (the finest level sweeps by z-marching, about seven planes per
+    block; the coarser levels, 48 points wide and less, fall back to the
+    colour launches) two steps take the same cycles and agree to rounding."""
+    rng = np.random.default_rng(17)
+    shape = (128, 64, 96)
+    rho = 0.8 + 0.05 * rng.uniform(-1, 1, shape)
+    vel = [0.03 * rng.standard_normal(shape) for _ in range(3)]
+    prm = dict(kind="pfc", dim=3, h=0.9, dt=0.02, alpha=0.6, tol=1e-11)
+    res = {}
+    for v in ("1", "3", "4"):
+        monkeypatch.setenv("FM_RB_VARIANT", v)
+        sol = gpu_solver(rho, prm, precision=precision, w_damp=0.0, tol=1e-11)
+        sol.set_fields(rho, vel)
+        cyc = [sol.step(prm["dt"]).cycles for _ in range(2)]
+        res[v] = (sol.get_fields(), cyc)
+        sol.close()
+    (ra, va), ca = res["1"]
+    for v in ("3", "4"):
+        (rb, vb), cb = res[v]
+        assert ca == cb, (v, ca, cb)
+        assert_parity(rb, vb, ra, va, 1e-12 if precision == fm.FM_FP64 else 1e-9)
 
 
 @functools.lru_cache(maxsize=1)

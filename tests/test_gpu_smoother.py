@@ -187,6 +187,45 @@ def test_tensor_copy_staging_equals_cp_async_staging(kind, shape, precision, mon
                 assert np.array_equal(a, b), (sweeps, vt, q, float(np.max(np.abs(a - b))))
 
 
+def _case3(kind, shape, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "cdft":
+        rho = 0.3 + 0.05 * rng.uniform(0, 1, shape)
+        prm = dict(kind="cdft", dim=3, h=17.0 / shape[2], dt=0.02, nu=2.362, delta=1e-10)
+    else:
+        rho = 0.8 + 0.05 * rng.uniform(-1, 1, shape)
+        prm = dict(kind="pfc", dim=3, h=0.9, dt=0.02, alpha=0.6)
+    vel = [0.05 * rng.standard_normal(shape) for _ in range(3)]
+    return rho, vel, prm
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+@pytest.mark.parametrize("kind,shape", [("pfc", (24, 48, 96)), ("pfc", (128, 64, 64)), ("pfc", (4, 16, 32)),
+                                        ("pfc", (2, 16, 64)), ("cdft", (16, 32, 32))])
+def test_3d_z_marching_sweeps_equal_colour_launches(kind, shape, precision, monkeypatch):
+    """The z-marching 3-D sweeps (variants 3 and 4: tiles of 32 x 8 and
+    32 x 16 points, planes staged in shared memory) run the point update of
+    the red and the black launch on the same values, so they agree with the
+    two-colour sweeps to the rounding of the compiled point update (the
+    tolerances of the 2-D variants; measured: float64 bit for bit, float32
+    within a few ulps): several tiles in x and y, the x rows of
+    the last tile wrapping around, blocks whose share of the planes is cut at
+    arbitrary planes and crosses tiles (64 x 64 x 128: about seven planes per
+    block), four and two planes (the staged planes wrap around z), and CDFT
+    (the coefficient density staged as well); 1 and 3 sweeps.  Where a tile
+    does not fit (32 x 16 float64) the variant falls back to the colour
+    launches."""
+    monkeypatch.setenv("FM_RB_VARIANT", "0")  # no autotuning at create
+    rho, vel, prm = _case3(kind, shape, 13)
+    f, _ = _oracle(rho, vel, prm, 0.0, 0)
+    tol = 1e-12 if precision == fm.FM_FP64 else 2e-5
+    for sweeps in (1, 3):
+        ref = _gpu(rho, vel, prm, f, precision, 0.0, sweeps, fm.FM_SWEEP_TWO_COLOUR)
+        assert max(float(np.max(np.abs(x))) for x in ref) > 0
+        for v in (3, 4):
+            _close(_gpu(rho, vel, prm, f, precision, 0.0, sweeps, v), ref, tol)
+
+
 def test_smooth_row_rejects_bad_arguments():
     rho, vel, prm = _case("cdft", (32, 32), 7)
     sol = gpu_solver(rho, prm)
