@@ -141,12 +141,21 @@ class ClockSampler:
 
 def sweeps_per_launch(variant):
     """Red-black sweeps one launch of fused-sweep variant `variant` runs."""
+    if variant >= 30:
+        return 1 + ((variant - 30) & 1)
     return 1 if variant == 28 else (2 if variant >= 18 else 1)
 
 
 def sweep_kernel(variant, batched):
     """Name of the fused-sweep kernel that variant `variant` launches."""
     pre = "kb_" if batched else "k_"
+    if variant >= 30:
+        if batched:  # the batch runs the small tiles as 0 and 24
+            variant = 24 if variant & 1 else 0
+        else:
+            tile = "16x16" if variant < 32 else "16x8"
+            return (f"k_smooth_rb2d<float,PFC,{tile}> ("
+                    + ("two sweeps per launch, halo 4)" if variant & 1 else "one sweep per launch)"))
     if variant >= 27 and not batched:
         tile, ns = [("32x16", 2), ("32x16", 1), ("32x32", 2)][variant - 27]
         return (f"k_smooth_rb2d_tma<float,PFC,{tile}> (tile staged by tensor copies, "

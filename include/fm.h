@@ -323,7 +323,7 @@ int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_
 /* ---- Measurement (no counterpart in the paper). ---- */
 
 /* Number of variants of the 2-D fused red-black sweep. */
-#define FM_SWEEP_VARIANTS 30
+#define FM_SWEEP_VARIANTS 34
 
 /* Variant of the 2-D fused red-black sweep the autotuner chose for `level`
  * at fm_create, and its timings of all FM_SWEEP_VARIANTS variants in ms per
@@ -338,7 +338,11 @@ int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_
  * memory); 27..29 the tile form with each tile staged by tensor copies (TMA)
  * instead of cp.async: 27 as 24, 28 as 0, 29 as 26 (the same updates; on a
  * level whose rows are not a whole number of 16 bytes they run the cp.async
- * staging; batches run them as 24, 0 and 26 and do not time them).  The time
+ * staging; batches run them as 24, 0 and 26 and do not time them); 30..33
+ * the tile form on small tiles, for the coarse levels: 30 one sweep and 31
+ * two sweeps per launch on 16 x 16 tiles, 32 and 33 the same on 16 x 8
+ * (single-instance solver; batches run them as 0, 24, 0, 24 and do not time
+ * them).  The time
  * per launch of a two-sweep variant is halved to give its time per sweep.  In 3-D the variants are 0 (a red and a black launch,
  * 256-thread blocks, the compiler's register count), 1 (the same bounded to
  * six resident blocks per multiprocessor) and 2 (the sweep in z-chunks sized

@@ -637,6 +637,11 @@ struct Batch {
       // solver): the same tiles staged by cp.async here
       case 27: return launch_v<32, 16, false, false, 2>(b, l, dir);
       case 28: return launch_v<32, 16, false, false>(b, l, dir);
+      // 30..33 (small tiles in the single-instance solver): the 32 x 16 tiles here
+      case 30: return launch_v<32, 16, false, false>(b, l, dir);
+      case 31: return launch_v<32, 16, false, false, 2>(b, l, dir);
+      case 32: return launch_v<32, 16, false, false>(b, l, dir);
+      case 33: return launch_v<32, 16, false, false, 2>(b, l, dir);
       default: return launch_v<32, 32, false, false, 2>(b, l, dir);
     }
   }

@@ -1200,9 +1200,13 @@ __global__ void __launch_bounds__(march_threads(TX), march2_minb<T>(TX)) k_smoot
 // the two-sweep tile form (tiles 32x16, 64x8, 32x32; f and omega from global
 // memory, one tile per block), 27..29 tiles staged by tensor copies (27: as
 // 24, 28: as 0, 29: as 26; single-instance solver only -- the batch runs
-// them as their cp.async twins).
+// them as their cp.async twins), 30..33 the tile form on small tiles for the
+// coarse levels (30: 16 x 16 one sweep, 31: 16 x 16 two sweeps, 32: 16 x 8
+// one sweep, 33: 16 x 8 two sweeps; single-instance solver only, the batch
+// runs them as 0 and 24).
 constexpr int RB_NVAR = FM_SWEEP_VARIANTS;
 constexpr int RB_TMA0 = 27;  // first variant staged by tensor copies
+constexpr int RB_SMALL0 = 30;  // first small-tile variant
 constexpr int TUNE_REPS = 10;  // timed launches per variant and level in the autotuners
 constexpr int RB_NTILE = 12;
 constexpr int RB_NMARCH = 6;
@@ -1210,11 +1214,14 @@ constexpr int RB_TWO = RB_NTILE + RB_NMARCH;  // first two-sweep variant
 constexpr int RB_TWO_TILE = RB_TWO + RB_NMARCH;  // first two-sweep tile variant
 __host__ __device__ constexpr int march_tx(int v) { return (v - RB_NTILE) % RB_NMARCH < 3 ? 64 : 128; }
 __host__ __device__ constexpr int march_ly(int v) { return 16 << ((v - RB_NTILE) % 3); }
-__host__ __device__ constexpr int sweeps_per_launch(int v) { return (v >= RB_TWO && v != RB_TMA0 + 1) ? 2 : 1; }
+__host__ __device__ constexpr int sweeps_per_launch(int v) {
+  return v >= RB_SMALL0 ? 1 + ((v - RB_SMALL0) & 1) : ((v >= RB_TWO && v != RB_TMA0 + 1) ? 2 : 1);
+}
 // The one-sweep variant with the same blocks as two-sweep variant v.
 __host__ __device__ constexpr int one_sweep_twin(int v) {
-  return v >= RB_TMA0 ? (v == RB_TMA0 ? RB_TMA0 + 1 : (v == RB_TMA0 + 2 ? 8 : v))
-                      : (v >= RB_TWO_TILE ? (v - RB_TWO_TILE) * 4 : (v >= RB_TWO ? v - RB_NMARCH : v));
+  return v >= RB_SMALL0 ? RB_SMALL0 + ((v - RB_SMALL0) & ~1)
+         : v >= RB_TMA0 ? (v == RB_TMA0 ? RB_TMA0 + 1 : (v == RB_TMA0 + 2 ? 8 : v))
+                        : (v >= RB_TWO_TILE ? (v - RB_TWO_TILE) * 4 : (v >= RB_TWO ? v - RB_NMARCH : v));
 }
 
 // The whole V-cycle of the small levels (each at most SMALL_N points) in one

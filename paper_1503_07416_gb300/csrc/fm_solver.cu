@@ -287,7 +287,11 @@ static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cud
     case 26: return launch_rb_v<T, KIND, 32, 32, false, false, 2>(st, L, P, s, dir);
     case 27: return launch_rb_tma<T, KIND, 32, 16, 2>(st, L, P, s, dir);
     case 28: return launch_rb_tma<T, KIND, 32, 16, 1>(st, L, P, s, dir);
-    default: return launch_rb_tma<T, KIND, 32, 32, 2>(st, L, P, s, dir);
+    case 29: return launch_rb_tma<T, KIND, 32, 32, 2>(st, L, P, s, dir);
+    case 30: return launch_rb_v<T, KIND, 16, 16, false, false>(st, L, P, s, dir);
+    case 31: return launch_rb_v<T, KIND, 16, 16, false, false, 2>(st, L, P, s, dir);
+    case 32: return launch_rb_v<T, KIND, 16, 8, false, false>(st, L, P, s, dir);
+    default: return launch_rb_v<T, KIND, 16, 8, false, false, 2>(st, L, P, s, dir);
   }
 }
 

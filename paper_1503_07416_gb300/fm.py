@@ -282,7 +282,7 @@ def fm_residual(st, g, r=None):
     return nrm.value
 
 
-FM_SWEEP_VARIANTS = 30
+FM_SWEEP_VARIANTS = 34
 FM_SWEEP_AUTO = -1
 FM_SWEEP_TWO_COLOUR = -2
 
