@@ -2067,6 +2067,40 @@ __global__ void __launch_bounds__(TPB) k_shared64(Fields64 F, Shared64 X, int N,
   if constexpr (KIND == KCDFT) X.x[4][idx] = log(r) + 2.0 * ce * r;
 }
 
+// After a cycle (3-D): the float64 update g += e of update64_point (with its
+// projection and non-positive-density flag) and then k_shared64's quantities
+// of the updated iterate, in one pass.  Each point reads and writes only its
+// own values, so the update can be in place.
+template <int KIND, int DIM, typename T>
+__global__ void __launch_bounds__(TPB) k_update_shared64(Fields64 F, Resid64Out O, Shared64 X, int N, double ce,
+                                                         double delta) {
+  using LY = Layout<KIND, DIM>;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N) return;
+  double gv[LY::NU];
+  T ev[LY::NU];  // all loads before the first store
+#pragma unroll
+  for (int q = 0; q < LY::NU; ++q) {
+    gv[q] = F.g[q][idx];
+    ev[q] = static_cast<const T*>(O.e0[q])[idx];
+  }
+  const double rk = F.rho[idx];
+#pragma unroll
+  for (int q = 0; q < LY::NU; ++q) gv[q] += from_t<T>(ev[q]);
+  gv[0] = (delta > 0.0) ? sqrt(gv[0] * gv[0] + delta * delta) : fabs(gv[0]);
+  if (F.nonpos && gv[0] <= 0.0) atomicOr(F.nonpos, 1);  // CDFT, delta = 0: ln 0 next
+#pragma unroll
+  for (int q = 0; q < LY::NU; ++q) F.g[q][idx] = gv[q];
+  double q2 = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    q2 += gv[1 + d] * gv[1 + d];
+    X.x[1 + d][idx] = rk * gv[1 + d];
+  }
+  X.x[0][idx] = q2;
+  if constexpr (KIND == KCDFT) X.x[4][idx] = log(gv[0]) + 2.0 * ce * gv[0];
+}
+
 // Float64 residual reading the shared quantities of k_shared64.
 template <int KIND, int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_resid64_x(Fields64 F, Shared64 X, Resid64Out O, Geo G, Step64 K,

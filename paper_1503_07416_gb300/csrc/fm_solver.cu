@@ -641,8 +641,10 @@ struct Solver {
   }
 
   // Float64 residual: 2-D tiled kernel; 3-D shared quantities then residual.
+  // update (3-D, after a cycle): the float64 update g += e is made by the
+  // shared-quantity pass (2-D makes it in k_update64 before this).
   static int launch_resid64(fm_state* st, const Fields64& F, const Resid64Out& O, const Geo& G, double h,
-                            const Phys<double>& P) {
+                            const Phys<double>& P, bool update = false) {
     cudaStream_t s = st->stream;
     if constexpr (DIM == 2) {
       k_resid64_tile<KIND, T><<<st->nblk, TPB, 0, s>>>(F, O, G, make_step64(P, 1.0 / h), P, st->partials);
@@ -650,7 +652,10 @@ struct Solver {
     } else {
       Shared64 X;
       for (int q = 0; q < 5; ++q) X.x[q] = st->x64[q];
-      k_shared64<KIND, DIM><<<nblocks(G.N), TPB, 0, s>>>(F, X, G.N, P.ce);
+      if (update)
+        k_update_shared64<KIND, DIM, T><<<nblocks(G.N), TPB, 0, s>>>(F, O, X, G.N, P.ce, st->prm.delta);
+      else
+        k_shared64<KIND, DIM><<<nblocks(G.N), TPB, 0, s>>>(F, X, G.N, P.ce);
       FM_LAUNCHED();
       k_resid64_x<KIND, DIM, T><<<st->nblk, TPB, 0, s>>>(F, X, O, G, make_step64(P, 1.0 / h), P,
                                                            st->partials);
@@ -668,7 +673,7 @@ struct Solver {
     cudaStream_t s = st->stream;
     Fields64 F = make_fields(st);
     Resid64Out O = resid_out(st, true, nullptr);
-    int rc = launch_resid64(st, F, O, G, h, P);
+    int rc = launch_resid64(st, F, O, G, h, P, DIM == 3 && in_body);
     if (rc) return rc;
     const double w = (DIM == 3) ? h * h * h : h * h;
     k_norm_ctl<LY::NU><<<1, TPB, 0, s>>>(st->partials, st->nblk, w, (Ctl*)st->ctl, st->prm.tol,
@@ -887,11 +892,13 @@ struct Solver {
       k_copy_back<T, LY::NU><<<nblocks(st->lv[0].g.N), TPB, 0, st->stream>>>(make_lvl<T>(st, 0));
       FM_LAUNCHED();
     }
-    const Geo G = st->lv[0].g;
-    Fields64 F = make_fields(st);
-    Resid64Out O = resid_out(st, true, nullptr);
-    k_update64<LY::NU, T><<<nblocks(G.N), TPB, 0, st->stream>>>(F, O, G.N, st->prm.delta);
-    FM_LAUNCHED();
+    if constexpr (DIM == 2) {  // (3-D: the residual's first pass makes the update)
+      const Geo G = st->lv[0].g;
+      Fields64 F = make_fields(st);
+      Resid64Out O = resid_out(st, true, nullptr);
+      k_update64<LY::NU, T><<<nblocks(G.N), TPB, 0, st->stream>>>(F, O, G.N, st->prm.delta);
+      FM_LAUNCHED();
+    }
     return enqueue_resid_norm(st, 1, hdl, use_handle);
   }
 
