@@ -133,8 +133,8 @@ __device__ __forceinline__ bool zm_point(int warp, int lane, int y0, int z, int&
 // the device runs side by side on one multiprocessor tend to pair a long
 // chunk with a short one), one block per chunk.  The blocks of all tiles start
 // together at the chunk boundaries and march up the planes side by side, so
-// the halos they share are read from L2.  Reads the correction from G.e (dir = 0) or G.r (dir = 1) and
-// writes it to the other.
+// the halos they share are read from L2.  Reads the correction from G.e
+// (dir = 0) or G.r (dir = 1) and writes it to the other.
 template <typename T, int KIND, int TY>
 __global__ void __launch_bounds__(ZmGeom<TY>::THREADS, zm_minb<T>(TY))
     k_smooth_zm3(const __grid_constant__ Lvl<T> G, Phys<T> P, int dir, int nchunks, int nlong) {
