@@ -141,6 +141,8 @@ class ClockSampler:
 
 def sweeps_per_launch(variant):
     """Red-black sweeps one launch of fused-sweep variant `variant` runs."""
+    if variant == 34:
+        return 2
     if variant >= 30:
         return 1 + ((variant - 30) & 1)
     return 1 if variant == 28 else (2 if variant >= 18 else 1)
@@ -149,6 +151,11 @@ def sweeps_per_launch(variant):
 def sweep_kernel(variant, batched):
     """Name of the fused-sweep kernel that variant `variant` launches."""
     pre = "kb_" if batched else "k_"
+    if variant == 34 and not batched:
+        return ("k_smooth_coop<float,PFC> (a smoothing step's red and black passes in one cooperative launch, "
+                "grid barriers between passes, in place)")
+    if variant == 34:
+        variant = 24
     if variant >= 30:
         if batched:  # the batch runs the small tiles as 0 and 24
             variant = 24 if variant & 1 else 0

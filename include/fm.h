@@ -323,7 +323,7 @@ int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_
 /* ---- Measurement (no counterpart in the paper). ---- */
 
 /* Number of variants of the 2-D fused red-black sweep. */
-#define FM_SWEEP_VARIANTS 34
+#define FM_SWEEP_VARIANTS 35
 
 /* Variant of the 2-D fused red-black sweep the autotuner chose for `level`
  * at fm_create, and its timings of all FM_SWEEP_VARIANTS variants in ms per
@@ -342,7 +342,10 @@ int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_
  * the tile form on small tiles, for the coarse levels: 30 one sweep and 31
  * two sweeps per launch on 16 x 16 tiles, 32 and 33 the same on 16 x 8
  * (single-instance solver; batches run them as 0, 24, 0, 24 and do not time
- * them).  The time
+ * them); 34 all the sweeps of a smoothing step (red and black passes over
+ * the whole level, in place) in one cooperative launch whose blocks meet at
+ * a grid-wide barrier between passes, timed with two sweeps per launch
+ * (single-instance solver; batches run it as 24).  The time
  * per launch of a two-sweep variant is halved to give its time per sweep.  In 3-D the variants are 0 (a red and a black launch,
  * 256-thread blocks, the compiler's register count), 1 (the same bounded to
  * six resident blocks per multiprocessor) and 2 (the sweep in z-chunks sized
@@ -390,6 +393,17 @@ int fm_widen(const float* in, double* out, long long n, void* stream);
  * stays usable), FM_EINVAL for a limit out of range.  Not reentrant: calls
  * that overlap on the GPU share one status word. */
 int fm_wait_selftest(int complete, int limit_us, void* stream);
+
+/* Measurement (no counterpart in the paper): the bounded wait of the
+ * grid-wide barrier of the cooperative sweep (fused-sweep variant 34), on
+ * `stream`: a cooperative launch of all the blocks the device holds at once,
+ * each arriving once and then waiting for every block (complete = 1) or for
+ * an arrival count nothing reaches (complete = 0), giving up after limit_us
+ * microseconds (1 .. 1000000), and synchronises.  FM_OK when every block
+ * passed, FM_ETIMEOUT when the limit ran out (every block then returns and
+ * the device stays usable), FM_EINVAL for a limit out of range.  Not
+ * reentrant: calls share one barrier and status word. */
+int fm_grid_barrier_selftest(int complete, int limit_us, void* stream);
 
 /* ---- Allocation-free entry point (the paper has no counterpart). ---- */
 

@@ -642,6 +642,7 @@ struct Batch {
       case 31: return launch_v<32, 16, false, false, 2>(b, l, dir);
       case 32: return launch_v<32, 16, false, false>(b, l, dir);
       case 33: return launch_v<32, 16, false, false, 2>(b, l, dir);
+      case 34: return launch_v<32, 16, false, false, 2>(b, l, dir);  // (cooperative in the single solver)
       default: return launch_v<32, 32, false, false, 2>(b, l, dir);
     }
   }

@@ -1203,10 +1203,13 @@ __global__ void __launch_bounds__(march_threads(TX), march2_minb<T>(TX)) k_smoot
 // them as their cp.async twins), 30..33 the tile form on small tiles for the
 // coarse levels (30: 16 x 16 one sweep, 31: 16 x 16 two sweeps, 32: 16 x 8
 // one sweep, 33: 16 x 8 two sweeps; single-instance solver only, the batch
-// runs them as 0 and 24).
+// runs them as 0 and 24), 34 all sweeps of a smoothing step in one
+// cooperative launch with grid barriers between the colour passes
+// (fm_coop.cuh; single-instance solver only, the batch runs it as 24).
 constexpr int RB_NVAR = FM_SWEEP_VARIANTS;
 constexpr int RB_TMA0 = 27;  // first variant staged by tensor copies
 constexpr int RB_SMALL0 = 30;  // first small-tile variant
+constexpr int RB_COOP = 34;  // a level's sweeps in one cooperative launch (in place; single-instance solver)
 constexpr int TUNE_REPS = 10;  // timed launches per variant and level in the autotuners
 constexpr int RB_NTILE = 12;
 constexpr int RB_NMARCH = 6;
@@ -1214,12 +1217,16 @@ constexpr int RB_TWO = RB_NTILE + RB_NMARCH;  // first two-sweep variant
 constexpr int RB_TWO_TILE = RB_TWO + RB_NMARCH;  // first two-sweep tile variant
 __host__ __device__ constexpr int march_tx(int v) { return (v - RB_NTILE) % RB_NMARCH < 3 ? 64 : 128; }
 __host__ __device__ constexpr int march_ly(int v) { return 16 << ((v - RB_NTILE) % 3); }
+// (variant 34 runs all the sweeps of a smoothing step in one launch; it is
+// timed and reported with two, the pre- and post-smoothing count.)
 __host__ __device__ constexpr int sweeps_per_launch(int v) {
-  return v >= RB_SMALL0 ? 1 + ((v - RB_SMALL0) & 1) : ((v >= RB_TWO && v != RB_TMA0 + 1) ? 2 : 1);
+  return v == RB_COOP ? 2
+                      : v >= RB_SMALL0 ? 1 + ((v - RB_SMALL0) & 1) : ((v >= RB_TWO && v != RB_TMA0 + 1) ? 2 : 1);
 }
 // The one-sweep variant with the same blocks as two-sweep variant v.
 __host__ __device__ constexpr int one_sweep_twin(int v) {
-  return v >= RB_SMALL0 ? RB_SMALL0 + ((v - RB_SMALL0) & ~1)
+  return v == RB_COOP ? 0
+         : v >= RB_SMALL0 ? RB_SMALL0 + ((v - RB_SMALL0) & ~1)
          : v >= RB_TMA0 ? (v == RB_TMA0 ? RB_TMA0 + 1 : (v == RB_TMA0 + 2 ? 8 : v))
                         : (v >= RB_TWO_TILE ? (v - RB_TWO_TILE) * 4 : (v >= RB_TWO ? v - RB_NMARCH : v));
 }
@@ -2210,7 +2217,9 @@ struct Ctl {
   int nonpos;   // CDFT: a density <= 0 reached ln this step (FM_ENONPOS)
   int hist;     // converged iterates kept for the extrapolated initial iterate (0, 1 or 2)
   int fault;    // a bounded wait inside a kernel ran out (FM_ETIMEOUT; never cleared)
+  unsigned gbar[2];  // grid barrier of the cooperative sweep: arrivals, blocks that left (zero between launches)
 };
+static_assert(sizeof(Ctl) <= 64, "the control block's slot in the arena and its host mirror hold 64 bytes");
 
 // Initial iterate extrapolated in time (fm_params.init = FM_INIT_EXTRAPOLATE),
 // before the prepare of a step: with the converged iterate g^k of the last

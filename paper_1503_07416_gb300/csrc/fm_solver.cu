@@ -32,6 +32,7 @@
 #include "fm_device.cuh"
 #include "fm_stepper.cuh"
 #include "fm_zmarch.cuh"
+#include "fm_coop.cuh"
 
 namespace fm {
 
@@ -256,6 +257,9 @@ static int launch_march2(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaSt
 // sweeps, the correction read from L.e and written to L.r (dir = 0) or the
 // reverse (dir = 1).
 template <typename T, int KIND>
+static int launch_coop(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int nsweeps);
+
+template <typename T, int KIND>
 static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int dir = 0) {
   switch (v) {
     case 0: return launch_rb_v<T, KIND, 32, 16, false, false>(st, L, P, s, dir);
@@ -291,7 +295,8 @@ static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cud
     case 30: return launch_rb_v<T, KIND, 16, 16, false, false>(st, L, P, s, dir);
     case 31: return launch_rb_v<T, KIND, 16, 16, false, false, 2>(st, L, P, s, dir);
     case 32: return launch_rb_v<T, KIND, 16, 8, false, false>(st, L, P, s, dir);
-    default: return launch_rb_v<T, KIND, 16, 8, false, false, 2>(st, L, P, s, dir);
+    case 33: return launch_rb_v<T, KIND, 16, 8, false, false, 2>(st, L, P, s, dir);
+    default: return launch_coop<T, KIND>(st, L, P, s, 2);  // in place (dir does not apply)
   }
 }
 
@@ -340,6 +345,48 @@ static int launch_zm3_v(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStr
   k_smooth_zm3<T, KIND, TY><<<(int)nblk, ZmGeom<TY>::THREADS, smem, s>>>(L, P, dir, nchunks, nlong);
   return FM_OK;
   }
+}
+
+// Launch nsweeps red-black sweeps of 2-D level L in place as one cooperative
+// launch (variant 34): as many blocks as are resident at once, at most one
+// thread per point of a colour.  FM_EINVAL where it does not apply (odd
+// rows, 3-D).
+template <typename T, int KIND>
+static bool coop_applies(const Lvl<T>& L) {
+  return L.g.nz == 1 && (L.g.nx & 1) == 0 && L.g.N >= 2;
+}
+
+template <typename T, int KIND>
+static int launch_coop(fm_state* st, const Lvl<T>& L, const Phys<T>& P, cudaStream_t s, int nsweeps) {
+  if (!coop_applies<T, KIND>(L) || nsweeps < 1) return FM_EINVAL;
+  static int per_sm = 0;
+  if (!per_sm) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_smooth_coop<T, KIND>, TPB, 0) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 0;
+      return FM_ECUDA;
+    }
+    if (per_sm < 1) return FM_EINVAL;
+  }
+  const int half = L.g.N / 2;
+  int grid = per_sm * st->sms;
+  if (grid > (half + TPB - 1) / TPB) grid = (half + TPB - 1) / TPB;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(TPB);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  Ctl* ctl = static_cast<Ctl*>(st->ctl);
+  if (cudaLaunchKernelEx(&cfg, k_smooth_coop<T, KIND>, L, P, nsweeps, &ctl->gbar[0], &ctl->fault) != cudaSuccess) {
+    cudaGetLastError();
+    return FM_ECUDA;
+  }
+  return FM_OK;
 }
 
 template <typename T, int KIND>
@@ -751,6 +798,22 @@ struct Solver {
     const int half = L.g.N / 2;
     const int nfused = (DIM == 2 && v >= 0) ? (iters & ~1) : 0;
     const int per = v >= 0 ? sweeps_per_launch(v) : 1;
+    if (DIM == 2 && v == RB_COOP && !coop_applies<T, KIND>(L)) v = -1;  // odd rows: two-colour launches
+    if (DIM == 2 && v == RB_COOP) {  // all sweeps in one cooperative launch, in place
+      if (prof && st->npev + 2 <= MAXEV) FM_CUDA(cudaEventRecord(st->pev[st->npev], s));
+      if (iters > 0) {
+        if constexpr (DIM == 2) {
+          const int rc = launch_coop<T, KIND>(st, *in_r ? swap_er(L) : L, P, s, iters);
+          if (rc) return rc;
+        }
+        FM_LAUNCHED();
+      }
+      if (prof && st->npev + 2 <= MAXEV) {
+        FM_CUDA(cudaEventRecord(st->pev[st->npev + 1], s));
+        st->npev += 2;
+      }
+      return FM_OK;
+    }
     if (DIM == 3 && v >= SM3_ZM && !zm3_applies<T, KIND>(st, v, L)) v = 1;  // not at this level's size
     if (DIM == 3 && v >= SM3_ZM) {  // fused z-marching sweeps, one launch each, e and r alternating
       for (int it = 0; it < iters; ++it) {
@@ -1496,6 +1559,61 @@ int fm_wait_selftest(int complete, int limit_us, void* stream) {
   if (cudaGetLastError() != cudaSuccess) return FM_ECUDA;
   int status = FM_ECUDA;
   if (cudaMemcpyFromSymbolAsync(&status, g_wait_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FM_ECUDA;
+  return status;
+}
+
+// Grid barrier of fm_grid_barrier_selftest: counters, fault flag and status.
+__device__ unsigned g_gbar_test[2];
+__device__ int g_gbar_fault;
+__device__ int g_gbar_status;
+
+// A cooperative launch of every resident block of k_smooth_coop's size; each
+// arrives once at the barrier of the cooperative sweep and waits for one
+// arrival of every block (complete = 1, reached) or for two (never reached).
+__global__ void __launch_bounds__(TPB) k_grid_barrier_selftest(int complete, unsigned long long limit_ns) {
+  const bool ok = grid_barrier(g_gbar_test, complete ? 1u : 2u, &g_gbar_fault, limit_ns);
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(&g_gbar_status, FM_ETIMEOUT);
+    return;
+  }
+  grid_barrier_leave(g_gbar_test);
+}
+
+int fm_grid_barrier_selftest(int complete, int limit_us, void* stream) {
+  if (limit_us < 1 || limit_us > 1000000) return FM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_barrier_selftest, TPB, 0) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return FM_ECUDA;
+  }
+  const unsigned zero2[2] = {0u, 0u};
+  const int zero = 0, ok = FM_OK;
+  if (cudaMemcpyToSymbolAsync(g_gbar_test, zero2, sizeof(zero2), 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyToSymbolAsync(g_gbar_fault, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyToSymbolAsync(g_gbar_status, &ok, sizeof(int), 0, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return FM_ECUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(per_sm * sms);
+  cfg.blockDim = dim3(TPB);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_grid_barrier_selftest, complete ? 1 : 0, 1000ull * (unsigned long long)limit_us) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return FM_ECUDA;
+  }
+  int status = FM_ECUDA;
+  if (cudaMemcpyFromSymbolAsync(&status, g_gbar_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return FM_ECUDA;
   return status;

@@ -96,6 +96,7 @@ _SIGS = {
     "fm_narrow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "fm_widen": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "fm_wait_selftest": (C.c_int, [C.c_int, C.c_int, C.c_void_p]),
+    "fm_grid_barrier_selftest": (C.c_int, [C.c_int, C.c_int, C.c_void_p]),
     "fm_smooth": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int]),
     "fm_create_batch": (C.c_int, [C.c_int, C.POINTER(fm_grid), C.POINTER(fm_params), C.POINTER(fm_functional),
                                   C.POINTER(C.c_void_p)]),
@@ -282,7 +283,7 @@ def fm_residual(st, g, r=None):
     return nrm.value
 
 
-FM_SWEEP_VARIANTS = 34
+FM_SWEEP_VARIANTS = 35
 FM_SWEEP_AUTO = -1
 FM_SWEEP_TWO_COLOUR = -2
 
@@ -305,6 +306,13 @@ def fm_wait_selftest(complete, limit_us, stream=None):
     """Status (FM_OK or FM_ETIMEOUT) of the smoother's bounded mbarrier wait
     on a barrier that is completed (complete=True) or that nothing completes."""
     return lib().fm_wait_selftest(1 if complete else 0, int(limit_us), C.c_void_p(stream))
+
+
+def fm_grid_barrier_selftest(complete, limit_us, stream=None):
+    """Status (FM_OK or FM_ETIMEOUT) of the cooperative sweep's bounded grid
+    barrier wait, on a count every block reaches (complete=True) or one that
+    nothing reaches."""
+    return lib().fm_grid_barrier_selftest(1 if complete else 0, int(limit_us), C.c_void_p(stream))
 
 
 def fm_widen(inp, out, stream=None):

@@ -106,6 +106,12 @@ def test_mass_noalloc_wrapper_checks_its_arguments(lib):
         fm.fm_mass_noalloc(torch.zeros((8, 8), dtype=torch.float32), 1.0, out_cpu)
 
 
+def test_grid_barrier_selftest_rejects_limits_out_of_range(lib):
+    """Checked before any device work (no GPU needed)."""
+    for limit in (0, -5, 1000001):
+        assert fm.fm_grid_barrier_selftest(True, limit) == fm.FM_EINVAL
+
+
 def test_wait_selftest_rejects_limits_out_of_range(lib):
     """Checked before any device work (no GPU needed)."""
     for limit in (0, -5, 1000001):

@@ -433,6 +433,25 @@ def test_bounded_wait_runs_out_with_etimeout_and_the_device_stays_usable():
     assert code == fm.FM_OK and info.res <= prm["tol"]
 
 
+def test_grid_barrier_wait_runs_out_with_etimeout_and_the_device_stays_usable(monkeypatch):
+    """The cooperative sweep's blocks meet at a grid barrier whose wait has a
+    time limit: an arrival count every block reaches passes; one that nothing
+    reaches gives up after the limit (2 ms) in every block and reports
+    FM_ETIMEOUT instead of hanging; a step with the cooperative sweep on the
+    same device afterwards is normal."""
+    assert fm.fm_grid_barrier_selftest(True, 2000) == fm.FM_OK
+    t0 = time.perf_counter()
+    assert fm.fm_grid_barrier_selftest(False, 2000) == fm.FM_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert fm.fm_grid_barrier_selftest(True, 2000) == fm.FM_OK
+    rho, vel, prm = inputs.pfc64()
+    monkeypatch.setenv("FM_RB_VARIANT", "34")
+    sol = gpu_solver(rho, prm)
+    sol.set_fields(rho, vel)
+    code, info = fm.fm_step_raw(sol.handle, prm["dt"])
+    assert code == fm.FM_OK and info.res <= prm["tol"]
+
+
 def test_nan_input_reports_enan():
     rho, vel, prm = inputs.pfc64()
     rho = rho.copy()
