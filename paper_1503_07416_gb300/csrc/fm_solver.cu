@@ -1113,6 +1113,7 @@ static size_t carve(fm_state* st, char* base) {
     st->fft.Jhat = (double2*)C.take(N0 * sizeof(double2));
     st->fft.work = (double2*)C.take(N0 * sizeof(double2));
     const int ns[3] = {st->lv[0].g.nx, st->lv[0].g.ny, st->lv[0].g.nz};
+    st->fft.Jr = (double*)C.take((size_t)(ns[0] / 2 + 1) * ns[1] * ns[2] * sizeof(double));
     for (int d = 0; d < 3; ++d)
       st->fft.tw[d] = d < st->dim ? (double2*)C.take((size_t)(ns[d] / 2 + 1) * sizeof(double2)) : nullptr;
   }

@@ -26,6 +26,7 @@ struct LevelBufs {
 
 struct FFTBufs {
   double2* Jhat;       // transform of h^d J / N (scaled so that the inverse needs no scale)
+  double* Jr;          // its real part at kx = 0 .. nx/2 (the real-input convolution; rows of nx/2 + 1)
   double2* work;       // complex work array, N values
   double2* tw[3];      // twiddles exp(-2 pi i k / n_d), k < n_d / 2
 };
