@@ -356,7 +356,9 @@ int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_
  * shared memory by bulk copies; levels whose sides are not multiples of the
  * tile report 0 for them and sweep with variant 1); their times are per
  * sweep.  Setting the environment variable
- * FM_RB_VARIANT=v before fm_create fixes the variant (no timing). */
+ * FM_RB_VARIANT=v before fm_create fixes the variant (no timing); a
+ * comma-separated list fixes one per level from the finest (the last one
+ * repeats; batches take the first). */
 int fm_tuning(const fm_state* st, int level, int* variant, float* ms_per_variant);
 
 /* Enable (1) or disable (0) CUDA-event timing of every finest-level smoother

@@ -394,6 +394,23 @@ static int launch_zm3(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cu
   return v == SM3_ZM ? launch_zm3_v<T, KIND, 8>(st, L, P, s, dir) : launch_zm3_v<T, KIND, 16>(st, L, P, s, dir);
 }
 
+// The sweep variants FM_RB_VARIANT fixes (a measurement switch): one number
+// for every level, or a comma-separated list, one per level from the finest
+// (the last one repeats); numbers outside 0 .. nvar - 1 give 0.
+static void fixed_variants(fm_state* st, const char* spec, int nvar) {
+  const char* p = spec;
+  int v = 0;
+  for (int l = 0; l < MAXLEV; ++l) {
+    if (*p) {
+      v = atoi(p);
+      if (v < 0 || v >= nvar) v = 0;
+      while (*p && *p != ',') ++p;
+      if (*p == ',') ++p;
+    }
+    st->rbv[l] = v;
+  }
+}
+
 // e = r on every point of a level (the correction back in e).
 template <typename T, int NU>
 __global__ void __launch_bounds__(TPB) k_copy_back(Lvl<T> L) {
@@ -539,8 +556,7 @@ struct Solver {
     const char* fixed = getenv("FM_RB_VARIANT");
     for (int l = 0; l < MAXLEV; ++l) st->rbv[l] = 0;
     if (fixed && fixed[0]) {
-      const int v = atoi(fixed);
-      for (int l = 0; l < MAXLEV; ++l) st->rbv[l] = (v >= 0 && v < SM3_NVAR) ? v : 0;
+      fixed_variants(st, fixed, SM3_NVAR);
       return FM_OK;
     }
     Phys<T> P = make_phys<T>(st);
@@ -588,8 +604,7 @@ struct Solver {
       const char* fixed = getenv("FM_RB_VARIANT");
       for (int l = 0; l < MAXLEV; ++l) st->rbv[l] = 0;
       if (fixed && fixed[0]) {
-        const int v = atoi(fixed);
-        for (int l = 0; l < MAXLEV; ++l) st->rbv[l] = (v >= 0 && v < RB_NVAR) ? v : 0;
+        fixed_variants(st, fixed, RB_NVAR);
         return FM_OK;
       }
       if (!st->fused_rb) return FM_OK;
