@@ -26,11 +26,12 @@ namespace fm {
 //
 // The arrays the point update reads at neighbours -- e (NU), rho^k, the
 // coefficient velocity (3) and, for CDFT, the coefficient density -- are
-// staged plane by plane into a ring of six slots (planes p - 1 .. p + 4 are
-// live in step p) by 16-byte cp.async chunks: thread t below SR * SW / V owns
-// one chunk position of the plane and copies it for every array.  The copies
-// of plane p + 4 are issued at the start of step p and waited for at its
-// end.  (Staging each row by one bulk copy through the tensor memory
+// staged plane by plane into a ring of 5 + D slots (planes p - 1 .. p + 3 + D
+// are live in step p) by 16-byte cp.async chunks: thread t below SR * SW / V
+// owns one chunk position of the plane and copies it for every array.  The
+// copies of plane p + 3 + D are issued at the start of step p, and at its end
+// the step waits for those of plane p + 4 (D = 1: issued by this step; D = 2:
+// by the step before).  (Staging each row by one bulk copy through the tensor memory
 // accelerator, 120 copies of 144 bytes per plane, measured three times
 // slower: the per-copy cost of the unit, not the bytes, set the pace.)  The
 // right-hand side, omega^k and (PFC) the coefficient density are read only
@@ -47,7 +48,13 @@ struct ZmGeom {
   static constexpr int SW = TX + 4;  // staged columns x0 - 2 .. x0 + 33
   static constexpr int SR = TY + 4;  // staged rows y0 - 2 .. y0 + TY + 1
   static constexpr int PS = SW * SR;  // values of one array in one plane
+  // ring slots and copy distance D = NSLOT - 5 (planes issued D steps before
+  // the step that first reads them).  Six slots, D = 1: a seventh slot for
+  // D = 2 on 32 x 16 tiles (202 KB of shared memory) measured slower, 0.093
+  // against 0.072 ms per sweep at 128^3 -- it leaves too little L1 for the
+  // point values that a red and a black point of one sector load in turn.
   static constexpr int NSLOT = 6;
+  static constexpr int D = NSLOT - 5;
   static constexpr int WARPS = TY + 2;
   static constexpr int THREADS = 32 * WARPS;
 };
@@ -230,14 +237,15 @@ __global__ void __launch_bounds__(ZmGeom<TY>::THREADS, zm_minb<T>(TY))
     wb_s = (ty + 2) * SW + 2 + 2 * i;
     wb_g = wrapi(y0 + ty, ny) * nx + wrapi(x0 + 2 * i, nx);
   }
-  // step p: issue plane p + 4; write plane p - 1 out; this lane's update
-  // with its point values `cur`; load the next step's into `nxt`
+  // step p: issue plane p + 3 + D; write plane p - 1 out; this lane's update
+  // with its point values `cur`; load the next step's into `nxt`; wait for
+  // plane p + 4 (every step commits one copy group, empty at the end)
   auto step = [&](int p, const ZmPt<T, KIND>& cur, ZmPt<T, KIND>& nxt) {
     // slots of the planes z - 1, z, z + 1 around this warp's role plane z
     // (red: p + 2, black: p)
     const int sbm = slot_base(red ? p + 1 : p - 1);
     const int sbc = next_slot(sbm), sbp = next_slot(sbc);
-    if (p + 4 <= z1 + 1) issue(p + 4);
+    if (p + 3 + Gm::D <= z1 + 1) issue(p + 3 + Gm::D);
     cp_async_commit();
     if (p - 1 >= z0 && p - 1 < z1 && wb >= 0) {
       const int si = slot_base(p - 1) + wb_s;
@@ -266,19 +274,24 @@ __global__ void __launch_bounds__(ZmGeom<TY>::THREADS, zm_minb<T>(TY))
       smooth_point_a<T, KIND, 3>(acc, P, K, n, 0);
     }
     if (role_z(p + 1, z)) zm_load_pt<T, KIND>(G, wrapz(z) * plane + gxy(z), nxt);
-    cp_async_wait_all();
+    cp_async_wait_n<Gm::D - 1>();
     __syncthreads();
   };
 
-  // prologue: planes z0 - 2 .. z0 (step z0 - 3 reads them)
+  // prologue: planes z0 - 2 .. z0 (step z0 - 3 reads them) in one group,
+  // then z0 + 1 .. z0 + D - 1 one group each (left in flight)
   for (int z = z0 - 2; z <= z0; ++z) issue(z);
   cp_async_commit();
+  for (int z = z0 + 1; z <= z0 + Gm::D - 1; ++z) {
+    if (z <= z1 + 1) issue(z);
+    cp_async_commit();
+  }
   ZmPt<T, KIND> pa, pb;
   {
     int z;
     if (role_z(z0 - 3, z)) zm_load_pt<T, KIND>(G, wrapz(z) * plane + gxy(z), pa);
   }
-  cp_async_wait_all();
+  cp_async_wait_n<Gm::D - 1>();
   __syncthreads();
   // steps z0 - 3 .. z1, two per iteration (the point values alternate
   // between pa and pb)
