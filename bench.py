@@ -210,12 +210,13 @@ def load_peaks():
 INIT = {"previous": 0, "extrapolate": 1}
 
 
-def make_solver(fm, rho_shape, prm, precision, stream, init="previous"):
+def make_solver(fm, rho_shape, prm, precision, stream, init="previous", coarse=None):
     n = list(reversed(rho_shape))
     from paper_1503_07416_gb300 import inputs
+    kw = {} if coarse is None else {"coarse_precision": coarse}
     return fm.Solver("pfc", n, prm["h"], alpha=prm["alpha"], precision=precision, tol=prm["tol"],
                      w_damp=0.0, gamma=prm["gamma"], delta=0.0, stream=stream, init=INIT[init],
-                     **inputs.BENCH_MG_2D)
+                     **inputs.BENCH_MG_2D, **kw)
 
 
 def time_device_steps(torch, fm, sol, rho_d, vel_d, dt, steps, warmup, flush):
@@ -283,13 +284,15 @@ def run_ours(args):
 
     results = {}
     tuning = {}
-    arms = [("mixed", fm.FM_MIXED, args.init), ("fp64", fm.FM_FP64, args.init)]
-    if args.init != "previous":
-        arms.append(("mixed_previous", fm.FM_MIXED, "previous"))  # the same arm from the previous time level
+    arms = [("mixed", fm.FM_MIXED, args.init, None), ("fp64", fm.FM_FP64, args.init, None)]
+    if args.init != "previous":  # the same arm from the previous time level
+        arms.append(("mixed_previous", fm.FM_MIXED, "previous", None))
+    # the mixed arm with the coarsest-grid solve in float32 instead of float64
+    arms.append(("mixed_coarse32", fm.FM_MIXED, args.init, fm.FM_MIXED))
     if args.only:
         arms = [a for a in arms if a[0] == args.only]
-    for name, prec, init in arms:
-        sol = make_solver(fm, rho.shape, prm, prec, stream, init)
+    for name, prec, init, coarse in arms:
+        sol = make_solver(fm, rho.shape, prm, prec, stream, init, coarse)
         tuning[name] = [fm.fm_tuning(sol.handle, l) for l in range(3)]
         if world > 1:
             dist.barrier()
@@ -401,7 +404,7 @@ def run_ours(args):
             "cycles_per_step_mean": round(statistics.mean(mix["cycles"]), 3),
             "multigrid": {"cycle": "V(2,2)", "levels": "512^2 .. 64^2 (4)", "coarsest_sweeps": 2,
                           "coarse_solve": "2 fused red-black sweeps of the 64^2 grid (multi-block, two sweeps "
-                                          "per launch)"},
+                                          "per launch), in float64 on float64 copies of the level"},
             "parallelism": f"{world} independent instance(s), one per GPU",
             "initial_iterate": {"previous": "previous time level (rho^k, u^k, mu^0, kappa^0)",
                                 "extrapolate": "linear extrapolation in time of the last two converged iterates "
@@ -416,6 +419,11 @@ def run_ours(args):
                 "smoother_gbs": round(words * 8 * N / (f64_avg * 1e-3) / 1e9, 1) if f64_sm_n else None,
             },
             "speedup_mixed_over_fp64": round(f64["total_ms"] / mix["total_ms"], 3),
+            "coarse_solve_precision": "float64 (fm_params.coarse_precision = FM_FP64)",
+            "mixed_coarse_solve_float32": (
+                {"value": round(world * steps / (results["mixed_coarse32"]["total_ms"] / 1e3), 3),
+                 "cycles_per_step_mean": round(statistics.mean(results["mixed_coarse32"]["cycles"]), 3)}
+                if "mixed_coarse32" in results else None),
             "mixed_from_previous_time_level": (
                 {"value": round(world * steps / (results["mixed_previous"]["total_ms"] / 1e3), 3),
                  "cycles_per_step_mean": round(statistics.mean(results["mixed_previous"]["cycles"]), 3)}
@@ -795,7 +803,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["mixed", "fp64", "mixed_previous"], default=None,
+    ap.add_argument("--only", choices=["mixed", "fp64", "mixed_previous", "mixed_coarse32"], default=None,
                     help="time one arm only and print a short diagnostic line (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-single", choices=["pfc512", "cdft256", "pfc3d128", "pfc64", "gradflow512",

@@ -136,6 +136,14 @@ typedef struct {
                        fm_set_fields, fm_prepare, fm_residual, a change of
                        the step size and a failed step; the converged
                        solution is the same either way (to the tolerance). */
+    int coarse_precision; /* precision of the coarsest-grid solve when
+                       precision = FM_MIXED [FM_FP64]: FM_FP64 solves it in
+                       float64 (the levels the single-block V-cycle or the
+                       coarsest multi-block sweeps handle, on float64 copies
+                       of their data), FM_MIXED in the cycle's float32.  The
+                       periodic hydrodynamic solver; the gradient flow, the
+                       channel and batches solve it in the cycle's
+                       precision. */
 } fm_params;
 
 typedef struct {

@@ -1024,8 +1024,16 @@ int fm_create_batch(int count, const fm_grid* grids, const fm_params* prm, const
     delete b;
     return FM_ENOMEM;
   }
+  // the batch runs its coarse levels in the cycle's precision (its own
+  // per-instance kernels): no float64 copies of them in the instances
+  fm_params iprm = *prm;
+  if (iprm.coarse_precision != FM_FP64 && iprm.coarse_precision != FM_MIXED) {
+    fm_destroy_batch(b);
+    return FM_EINVAL;
+  }
+  iprm.coarse_precision = FM_MIXED;
   for (int i = 0; i < count; ++i) {
-    const int rc = fm_create(&grids[i], prm, fn, &b->inst[i]);
+    const int rc = fm_create(&grids[i], &iprm, fn, &b->inst[i]);
     if (rc) {
       fm_destroy_batch(b);
       return rc;

@@ -2424,8 +2424,7 @@ static size_t small_layout(const SmallLv<T>& S, SmallSmem<T>& M, size_t limit) {
 // Host-side builders of the kernel argument structs from a state
 // --------------------------------------------------------------------------
 template <typename T>
-static Lvl<T> make_lvl(const fm_state* st, int l) {
-  const LevelBufs& B = st->lv[l];
+static Lvl<T> make_lvl_bufs(const LevelBufs& B) {
   Lvl<T> L;
   L.g = B.g;
   L.h = (T)B.h;
@@ -2442,6 +2441,11 @@ static Lvl<T> make_lvl(const fm_state* st, int l) {
     L.cv[d] = (const T*)B.cv[d];
   }
   return L;
+}
+
+template <typename T>
+static Lvl<T> make_lvl(const fm_state* st, int l) {
+  return make_lvl_bufs<T>(st->lv[l]);
 }
 
 template <typename T>

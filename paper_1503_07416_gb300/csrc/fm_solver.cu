@@ -411,6 +411,24 @@ static void fixed_variants(fm_state* st, const char* spec, int nvar) {
   }
 }
 
+// Element-wise conversions of up to CONV_MAX arrays in one launch: array a
+// (n[a] values) from src[a] to dst[a], block row blockIdx.y taking array a.
+constexpr int CONV_MAX = 96;
+template <typename A, typename B>
+struct ConvSet {
+  const A* src[CONV_MAX];
+  B* dst[CONV_MAX];
+  int n[CONV_MAX];
+  int count;
+  int maxn;
+};
+template <typename A, typename B>
+__global__ void __launch_bounds__(TPB) k_convert_set(const __grid_constant__ ConvSet<A, B> C) {
+  const int a = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < C.n[a]) C.dst[a][i] = static_cast<B>(C.src[a][i]);
+}
+
 // e = r on every point of a level (the correction back in e).
 template <typename T, int NU>
 __global__ void __launch_bounds__(TPB) k_copy_back(Lvl<T> L) {
@@ -902,9 +920,110 @@ struct Solver {
 
   // One V-cycle from level l down; *out_in_r: on return the correction of
   // level l is in its r buffer (1) or in e (0).
+  // The V-cycle of the small levels S (each of at most SMALL_N points) in
+  // one block: shared memory when they fit, else global memory.
+  static int small_cycle(fm_state* st, const SmallLv<T>& S, const Phys<T>& P) {
+    cudaStream_t s = st->stream;
+    SmallSmem<T> M;
+    const size_t smem = small_layout<T, KIND, DIM>(S, M, SMALL_SMEM_MAX);
+    if (smem <= SMALL_SMEM_MAX && S.lv[0].g.N <= SMALL_SMEM_N) {
+      static bool attr = false;
+      if (!attr) {
+        FM_CUDA(cudaFuncSetAttribute(k_vcycle_small_smem<T, KIND, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMALL_SMEM_MAX));
+        attr = true;
+      }
+      k_vcycle_small_smem<T, KIND, DIM><<<1, SMALL_TPB, smem, s>>>(S, M, P, st->prm.nu1, st->prm.nu2,
+                                                                    st->prm.ncoarse);
+    } else {
+      k_vcycle_small<T, KIND, DIM><<<1, SMALL_TPB, 0, s>>>(S, P, st->prm.nu1, st->prm.nu2, st->prm.ncoarse);
+    }
+    FM_LAUNCHED();
+    return FM_OK;
+  }
+
+  // Conversions between the coarse levels and their float64 copies (lv64):
+  // to64 copies the entry level l's right-hand side and correction and the
+  // coefficients of levels l .. nlev - 1; from64 copies the entry level's
+  // float64 correction (in r when in_r) back.  One launch each.
+  static int coarse_to64(fm_state* st, int l) {
+    ConvSet<T, double> C{};
+    auto add = [&](const void* src, void* dst, int n) {
+      if (src && dst && C.count < CONV_MAX) {
+        C.src[C.count] = static_cast<const T*>(src);
+        C.dst[C.count] = static_cast<double*>(dst);
+        C.n[C.count] = n;
+        C.count++;
+        if (n > C.maxn) C.maxn = n;
+      }
+    };
+    const int n0 = st->lv[l].g.N;
+    for (int q = 0; q < LY::NU; ++q) {
+      add(st->lv[l].f[q], st->lv64[l].f[q], n0);
+      add(st->lv[l].e[q], st->lv64[l].e[q], n0);
+    }
+    for (int k = l; k < st->nlev; ++k) {
+      const int n = st->lv[k].g.N;
+      add(st->lv[k].rk, st->lv64[k].rk, n);
+      add(st->lv[k].cr, st->lv64[k].cr, n);
+      for (int d = 0; d < LY::NOM; ++d) add(st->lv[k].om[d], st->lv64[k].om[d], n);
+      for (int d = 0; d < DIM; ++d) add(st->lv[k].cv[d], st->lv64[k].cv[d], n);
+    }
+    k_convert_set<T, double><<<dim3((C.maxn + TPB - 1) / TPB, C.count), TPB, 0, st->stream>>>(C);
+    FM_LAUNCHED();
+    return FM_OK;
+  }
+  static int coarse_from64(fm_state* st, int l, int in_r) {
+    ConvSet<double, T> C{};
+    const int n0 = st->lv[l].g.N;
+    for (int q = 0; q < LY::NU; ++q) {
+      C.src[q] = static_cast<const double*>(in_r ? st->lv64[l].r[q] : st->lv64[l].e[q]);
+      C.dst[q] = static_cast<T*>(st->lv[l].e[q]);
+      C.n[q] = n0;
+    }
+    C.count = LY::NU;
+    C.maxn = n0;
+    k_convert_set<double, T><<<dim3((n0 + TPB - 1) / TPB, C.count), TPB, 0, st->stream>>>(C);
+    FM_LAUNCHED();
+    return FM_OK;
+  }
+
+  // The coarsest-grid solve in float64 (mixed path): the coarse levels from
+  // l down on their float64 copies -- the single-block V-cycle, or the
+  // coarsest level's ncoarse sweeps as colour launches -- between the two
+  // conversions.
+  static int coarse_solve64(fm_state* st, int l) {
+    int rc = coarse_to64(st, l);
+    if (rc) return rc;
+    const Phys<double> P64 = make_phys<double>(st);
+    int in_r = 0;
+    if (st->coarse_fused) {
+      // colour launches of 32-thread blocks: the float64 point updates of a
+      // small level spread over all multiprocessors (GB300 issues few float64
+      // operations per multiprocessor and clock)
+      const Lvl<double> L64 = make_lvl_bufs<double>(st->lv64[l]);
+      const int half = L64.g.N / 2;
+      for (int it = 0; it < st->prm.ncoarse; ++it)
+        for (int color = 0; color < 2; ++color) {
+          k_smooth<double, KIND, DIM><<<(half + 31) / 32, 32, 0, st->stream>>>(L64, P64, color);
+          FM_LAUNCHED();
+        }
+    } else {
+      SmallLv<double> S;
+      S.count = st->nlev - l;
+      for (int q = 0; q < S.count; ++q) S.lv[q] = make_lvl_bufs<double>(st->lv64[l + q]);
+      rc = Solver<double, KIND, DIM>::small_cycle(st, S, P64);
+    }
+    if (rc) return rc;
+    return coarse_from64(st, l, in_r);
+  }
+
   static int vcycle(fm_state* st, int l, const Phys<T>& P, int* out_in_r) {
     cudaStream_t s = st->stream;
     *out_in_r = 0;
+    if constexpr (sizeof(T) == 4) {
+      if (l >= st->small_from && st->coarse64) return coarse_solve64(st, l);
+    }
     if (l >= st->small_from && st->coarse_fused) {  // the coarsest level: ncoarse fused sweeps
       return smooth(st, l, P, st->prm.ncoarse, out_in_r);
     }
@@ -912,22 +1031,7 @@ struct Solver {
       SmallLv<T> S;
       S.count = st->nlev - l;
       for (int q = 0; q < S.count; ++q) S.lv[q] = make_lvl<T>(st, l + q);
-      SmallSmem<T> M;
-      const size_t smem = small_layout<T, KIND, DIM>(S, M, SMALL_SMEM_MAX);
-      if (smem <= SMALL_SMEM_MAX && S.lv[0].g.N <= SMALL_SMEM_N) {
-        static bool attr = false;
-        if (!attr) {
-          FM_CUDA(cudaFuncSetAttribute(k_vcycle_small_smem<T, KIND, DIM>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_SMEM_MAX));
-          attr = true;
-        }
-        k_vcycle_small_smem<T, KIND, DIM><<<1, SMALL_TPB, smem, s>>>(S, M, P, st->prm.nu1, st->prm.nu2,
-                                                                      st->prm.ncoarse);
-      } else {
-        k_vcycle_small<T, KIND, DIM><<<1, SMALL_TPB, 0, s>>>(S, P, st->prm.nu1, st->prm.nu2, st->prm.ncoarse);
-      }
-      FM_LAUNCHED();
-      return FM_OK;
+      return small_cycle(st, S, P);
     }
     // The correction of level l may sit in its r buffer between the pre- and
     // the post-smoothing (after an odd number of fused launches); the
@@ -1124,6 +1228,31 @@ static size_t carve(fm_state* st, char* base) {
       }
     }
   }
+  // float64 copies of the coarse levels (mixed path, coarsest solve in
+  // float64): e, f, r, eh and the coefficients of levels small_from ..
+  // nlev - 1 (the entry level's eh stays in the float32 level: the
+  // prolongation reads it)
+  for (int l = 0; l < MAXLEV; ++l) st->lv64[l] = LevelBufs{};
+  if (st->coarse64) {
+    for (int l = st->small_from; l < st->nlev; ++l) {
+      LevelBufs& B = st->lv64[l];
+      B.g = st->lv[l].g;
+      B.h = st->lv[l].h;
+      const size_t N = B.g.N;
+      for (int q = 0; q < MAXU; ++q) {
+        B.e[q] = q < st->nu ? C.take(N * d8) : nullptr;
+        B.f[q] = q < st->nu ? C.take(N * d8) : nullptr;
+        B.r[q] = q < st->nu ? C.take(N * d8) : nullptr;
+        B.eh[q] = (q < st->nu && l > st->small_from) ? C.take(N * d8) : nullptr;
+      }
+      B.rk = C.take(N * d8);
+      B.cr = C.take(N * d8);
+      for (int d = 0; d < 3; ++d) {
+        B.om[d] = d < st->nom ? C.take(N * d8) : nullptr;
+        B.cv[d] = d < st->dim ? C.take(N * d8) : nullptr;
+      }
+    }
+  }
   if (st->kind == FM_CDFT) {
     st->fft.Jhat = (double2*)C.take(N0 * sizeof(double2));
     st->fft.work = (double2*)C.take(N0 * sizeof(double2));
@@ -1172,6 +1301,7 @@ void fm_default_params(fm_params* p) {
   p->walls = FM_WALLS_NONE;
   p->u_wall[0] = p->u_wall[1] = 0.0;
   p->init = FM_INIT_PREVIOUS;
+  p->coarse_precision = FM_FP64;
 }
 
 const char* fm_strerror(int code) {
@@ -1203,6 +1333,7 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
        !(prm->u_wall[0] == prm->u_wall[0]) || !(prm->u_wall[1] == prm->u_wall[1])))
     return FM_EINVAL;  // walls: the 2-D hydrodynamic PFC channel only
   if (prm->init != FM_INIT_PREVIOUS && prm->init != FM_INIT_EXTRAPOLATE) return FM_EINVAL;
+  if (prm->coarse_precision != FM_FP64 && prm->coarse_precision != FM_MIXED) return FM_EINVAL;
   if (prm->init == FM_INIT_EXTRAPOLATE && (prm->model != FM_HYDRO || prm->walls != FM_WALLS_NONE))
     return FM_EINVAL;  // the periodic hydrodynamic solver only
   if (prm->nu1 < 0 || prm->nu2 < 0 || prm->nu1 + prm->nu2 < 1 || prm->ncoarse < 1 || prm->max_cycles < 0)
@@ -1279,6 +1410,8 @@ int fm_create(const fm_grid* grid, const fm_params* prm, const fm_functional* fn
   // fused sweeps in 2-D, a red and a black launch per sweep in 3-D or without
   // fusion); one block would run its points serially.
   st->coarse_fused = st->small_from == nlev - 1 && st->lv[nlev - 1].g.N > SMALL_N;
+  st->coarse64 = st->prm.precision == FM_MIXED && st->prm.coarse_precision == FM_FP64 &&
+                 st->model == FM_HYDRO && st->prm.walls == FM_WALLS_NONE;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {

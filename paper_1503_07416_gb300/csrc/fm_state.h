@@ -41,6 +41,8 @@ struct fm_state {
   int kind, dim, nu, nom, nlev;
   int elem;                       // sizeof(T) of the hierarchy
   fm::LevelBufs lv[fm::MAXLEV];
+  fm::LevelBufs lv64[fm::MAXLEV];  // mixed path, coarse_precision FM_FP64: float64 copies of the coarse levels
+  bool coarse64;                   // the coarsest-grid solve runs on lv64 (levels small_from .. nlev - 1)
   // float64 finest-level fields
   double* rho;
   double* vel[3];

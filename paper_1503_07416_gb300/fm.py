@@ -54,7 +54,7 @@ class fm_params(C.Structure):
                 ("tol", C.c_double), ("sigma", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("max_cycles", C.c_int), ("coarsest", C.c_int), ("ncoarse", C.c_int),
                 ("precision", C.c_int), ("model", C.c_int), ("walls", C.c_int), ("u_wall", C.c_double * 2),
-                ("init", C.c_int)]
+                ("init", C.c_int), ("coarse_precision", C.c_int)]
 
 
 class fm_step_info(C.Structure):

@@ -60,6 +60,18 @@ def test_pfc64_steps(precision):
     _compare_step(rho, vel, prm, precision, steps=prm["steps"])
 
 
+@pytest.mark.parametrize("coarse", [fm.FM_FP64, fm.FM_MIXED])
+@pytest.mark.parametrize("mg", [{}, {"coarsest": 64, "ncoarse": 2}])
+def test_mixed_path_coarsest_solve_in_either_precision(coarse, mg):
+    """The mixed path with the coarsest-grid solve in float64 (the default,
+    on float64 copies of the coarse levels) and in float32: per-step parity
+    with the oracle both ways, with the single-block V-cycle of the small
+    levels (default hierarchy) and with a multi-block coarsest level (the
+    benchmark's 64^2 coarsest grid of a 256^2 problem), 2 steps each."""
+    rho, vel, prm = inputs.pfc_supercooled(256 if mg else 128, seed=22)
+    _compare_step(rho, vel, prm, fm.FM_MIXED, w_damp=0.0, steps=2, coarse_precision=coarse, **mg)
+
+
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
 def test_pfc_supercooled_with_velocity(precision):
     """PFC eps = 0.4 supercooled liquid with nuclei, non-zero velocity and
@@ -277,13 +289,15 @@ def test_full_size_cdft256_two_steps(precision):
 
 
 def test_mixed_coarsest_solve_costs_no_cycles_at_512():
-    """The mixed path runs its whole cycle, the coarsest-grid sweeps
-    included, in float32 inside the float64 residual loop.  At the benchmark's
-    512^2 configuration it takes the same V-cycles per step as the float64
-    path over five steps, and its fields stay within 1e-8 (per field, 2-norm
-    and element-wise) of the float64 path's."""
+    """The mixed path with its whole cycle, the coarsest-grid sweeps included,
+    in float32 inside the float64 residual loop (coarse_precision = FM_MIXED,
+    the faster choice on GB300; the default solves the coarsest grid in
+    float64).  At the benchmark's 512^2 configuration it takes the same
+    V-cycles per step as the float64 path over five steps, and its fields stay
+    within 1e-8 (per field, 2-norm and element-wise) of the float64 path's."""
     rho, vel, prm = inputs.pfc512()
-    sols = {p: gpu_solver(rho, prm, precision=p, w_damp=0.0, tol=1e-10, **inputs.BENCH_MG_2D)
+    sols = {p: gpu_solver(rho, prm, precision=p, w_damp=0.0, tol=1e-10, coarse_precision=fm.FM_MIXED,
+                          **inputs.BENCH_MG_2D)
             for p in (fm.FM_FP64, fm.FM_MIXED)}
     for sol in sols.values():
         sol.set_fields(rho, vel)
