@@ -31,8 +31,8 @@ namespace fm {
 // owns one chunk position of the plane and copies it for every array.  The
 // copies of plane p + 3 + D are issued at the start of step p, and at its end
 // the step waits for those of plane p + 4 (D = 1: issued by this step; D = 2:
-// by the step before).  (Staging each row by one bulk copy through the tensor memory
-// accelerator, 120 copies of 144 bytes per plane, measured three times
+// by the step before).  (Staging each row by one bulk copy through the tensor
+// memory accelerator, 120 copies of 144 bytes per plane, measured three times
 // slower: the per-copy cost of the unit, not the bytes, set the pace.)  The
 // right-hand side, omega^k and (PFC) the coefficient density are read only
 // at the point itself: each thread loads them into registers one step ahead.
