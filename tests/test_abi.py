@@ -37,6 +37,7 @@ def test_default_params_and_strerror(lib):
     p = fm.fm_default_params()
     assert p.gamma == 2.0 and p.nu1 == 2 and p.nu2 == 2 and p.sigma == 1.0
     assert p.precision == fm.FM_FP64 and p.tol == 1e-10
+    assert p.coarse_precision == fm.FM_FP64  # the coarsest-grid solve of the mixed path in float64
     codes = (fm.FM_OK, fm.FM_EINVAL, fm.FM_ENOMEM, fm.FM_ECUDA, fm.FM_ENOCONV, fm.FM_ENONPOS, fm.FM_ENAN,
              fm.FM_ETIMEOUT)
     msgs = [fm.strerror(code) for code in codes]
@@ -67,7 +68,7 @@ def _create(dim=2, n=(8, 8, 1), h=0.5, kind=fm.FM_PFC, nu=1.0, **kw):
     dict(w_damp=1.0), dict(nu1=0, nu2=0), dict(ncoarse=0), dict(precision=7), dict(coarsest=1),
     dict(dim=3, n=(8, 8, 5)), dict(model=7), dict(walls=3), dict(init=5),
     dict(walls=1, kind=fm.FM_CDFT, n=(8, 8, 1)), dict(walls=1, dim=3, n=(8, 8, 8)),
-    dict(init=1, model=1),
+    dict(init=1, model=1), dict(coarse_precision=3), dict(coarse_precision=-1),
 ])
 def test_create_rejects_invalid_arguments(lib, bad):
     assert _create(**bad) == fm.FM_EINVAL
