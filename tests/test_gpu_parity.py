@@ -731,6 +731,42 @@ def test_step_host_equals_set_step_get(precision):
     b.close()
 
 
+@pytest.mark.parametrize("pinned", ["all", "inputs"])
+def test_step_host_with_pinned_buffers_equals_set_step_get(pinned):
+    """fm_step_host with pinned host fields (the benchmark's end-to-end
+    buffers; the copies then run asynchronously), and with pinned inputs and
+    pageable outputs: the same bits as fm_set_fields + fm_step +
+    fm_get_fields, three steps in a row (the outputs fed back as inputs), and
+    the inputs in the outputs when a step fails."""
+    torch = pytest.importorskip("torch")
+    rho, vel, prm = inputs.pfc_supercooled(128, seed=31)
+    a = gpu_solver(rho, prm, precision=fm.FM_MIXED, w_damp=0.0)
+    b = gpu_solver(rho, prm, precision=fm.FM_MIXED, w_damp=0.0)
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    ri, vi = pin(rho), [pin(v) for v in vel]
+    if pinned == "all":
+        ro, vo = torch.empty_like(ri).pin_memory(), [torch.empty_like(v).pin_memory() for v in vi]
+    else:
+        ro, vo = torch.empty_like(ri), [torch.empty_like(v) for v in vi]
+    ra, va = rho.copy(), [v.copy() for v in vel]
+    for _ in range(3):
+        a.set_fields(ra, va)
+        ia = a.step(prm["dt"])
+        ra, va = a.get_fields()
+        ib = b.step_host(prm["dt"], ri, vi, ro, vo)
+        assert ia.cycles == ib.cycles
+        assert np.array_equal(ra, ro.numpy()) and all(np.array_equal(x, y.numpy()) for x, y in zip(va, vo))
+        ri.copy_(ro)
+        for x, y in zip(vi, vo):
+            x.copy_(y)
+    ri[5, 7] = math.nan
+    code, _ = fm.fm_step_host(b.handle, prm["dt"], ri, vi, ro, vo)
+    assert code == fm.FM_ENAN
+    assert math.isnan(float(ro[5, 7])) and torch.equal(vo[0], vi[0])
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
 def test_host_stepper_equals_step_host(precision):
     """Solver.host_stepper (buffers checked and marshalled once, one C call
