@@ -414,6 +414,9 @@ static void fixed_variants(fm_state* st, const char* spec, int nvar) {
 // Element-wise conversions of up to CONV_MAX arrays in one launch: array a
 // (n[a] values) from src[a] to dst[a], block row blockIdx.y taking array a.
 constexpr int CONV_MAX = 96;
+// the coarse solve's conversions: the entry level's f and e, and rk, cr, omega
+// (3) and the coefficient velocity (3) of up to MAXSMALL levels
+static_assert(CONV_MAX >= 2 * MAXU + MAXSMALL * 8, "room for every array the coarse-solve conversions copy");
 template <typename A, typename B>
 struct ConvSet {
   const A* src[CONV_MAX];
