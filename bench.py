@@ -394,7 +394,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 smoothing / f64 residual",
+        "dtype": "f32 smoothing and transfers / f64 residual, coarsest solve, norms",
         "data": "synthetic (seeded)",
         "config": {
             "workload": WORKLOAD,
