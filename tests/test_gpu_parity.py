@@ -844,6 +844,51 @@ def test_extrapolated_initial_iterate_same_solutions_fewer_cycles(precision):
     prev.close()
 
 
+@pytest.mark.parametrize("case", ["pfc3d", "cdft2d"])
+def test_extrapolated_initial_iterate_in_3d_and_cdft(case):
+    """FM_INIT_EXTRAPOLATE on the mixed path of the two other functionals'
+    workloads: 32^3 PFC with random velocity (the z-marching sweep on its
+    finest level, a multi-block float64 coarsest grid) and 64^2 CDFT with the
+    256^2 physics; six steps each match the oracle's step from the previous
+    time level within the mixed tolerance.  In 3-D they take no more
+    V-cycles in total than the previous-time-level start; the CDFT case's
+    random velocity decays within a step, the extrapolation overshoots it and
+    costs a cycle on most steps (41 against 37 measured), so there only the
+    parity is asserted."""
+    if case == "pfc3d":
+        rng = np.random.default_rng(16)
+        n = 32
+        rho = 0.8 + 0.05 * rng.uniform(-1, 1, (n, n, n))
+        vel = [0.03 * rng.standard_normal((n, n, n)) for _ in range(3)]
+        prm = dict(kind="pfc", dim=3, h=0.9, dt=0.02, alpha=0.6)
+        tol = 1e-11
+    else:
+        rho, vel, prm = inputs.cdft256(n=64)
+        prm = dict(prm, h=17.0 / 128)
+        rng = np.random.default_rng(17)
+        vel = [0.02 * rng.standard_normal(rho.shape) for _ in range(2)]
+        tol = 1e-11
+    P, opts, J = oracle_setup(rho, prm, w_damp=0.0, tol=tol)
+    ext = gpu_solver(rho, prm, precision=fm.FM_MIXED, w_damp=0.0, tol=tol, init=fm.FM_INIT_EXTRAPOLATE)
+    prev = gpu_solver(rho, prm, precision=fm.FM_MIXED, w_damp=0.0, tol=tol)
+    ext.set_fields(rho, vel)
+    prev.set_fields(rho, vel)
+    ce, cp = [], []
+    for _ in range(6):
+        ie = ext.step(prm["dt"])
+        ce.append(ie.cycles)
+        cp.append(prev.step(prm["dt"]).cycles)
+        assert ie.res <= tol
+        rg, vg = ext.get_fields()
+        ro, vo, _ = S.step(rho, vel, P, opts, J=J)
+        assert_parity(rg, vg, ro, vo, TOLMIX, (ce, cp))
+        rho, vel = ro, vo
+    if case == "pfc3d":
+        assert sum(ce) <= sum(cp), (ce, cp)
+    ext.close()
+    prev.close()
+
+
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
 def test_extrapolation_history_is_cleared_and_graph_modes_agree(precision):
     """fm_set_fields clears the history (the next step is bit for bit a fresh
