@@ -141,7 +141,7 @@ class ClockSampler:
 
 def sweeps_per_launch(variant):
     """Red-black sweeps one launch of fused-sweep variant `variant` runs."""
-    if variant == 34:
+    if variant in (34, 35):
         return 2
     if variant >= 30:
         return 1 + ((variant - 30) & 1)
@@ -154,7 +154,9 @@ def sweep_kernel(variant, batched):
     if variant == 34 and not batched:
         return ("k_smooth_coop<float,PFC> (a smoothing step's red and black passes in one cooperative launch, "
                 "grid barriers between passes, in place)")
-    if variant == 34:
+    if variant == 35 and not batched:
+        return "k_smooth_rb2d<float,PFC,32x14> (two sweeps per launch, halo 4)"
+    if variant in (34, 35):
         variant = 24
     if variant >= 30:
         if batched:  # the batch runs the small tiles as 0 and 24

@@ -331,7 +331,7 @@ int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_
 /* ---- Measurement (no counterpart in the paper). ---- */
 
 /* Number of variants of the 2-D fused red-black sweep. */
-#define FM_SWEEP_VARIANTS 35
+#define FM_SWEEP_VARIANTS 36
 
 /* Variant of the 2-D fused red-black sweep the autotuner chose for `level`
  * at fm_create, and its timings of all FM_SWEEP_VARIANTS variants in ms per
@@ -353,8 +353,11 @@ int fm_batch_time_sweep_variant(fm_batch* b, int variant, int iters, double* ms_
  * them); 34 all the sweeps of a smoothing step (red and black passes over
  * the whole level, in place) in one cooperative launch whose blocks meet at
  * a grid-wide barrier between passes, timed with two sweeps per launch
- * (single-instance solver; batches run it as 24).  The time
- * per launch of a two-sweep variant is halved to give its time per sweep.  In 3-D the variants are 0 (a red and a black launch,
+ * (single-instance solver; batches run it as 24); 35 as 24 on 32 x 14 tiles
+ * (592 tiles at 512^2, so that four blocks on each of 152 multiprocessors
+ * take nearly all of them in one wave; single-instance solver, batches run
+ * it as 24).  The time per launch of a two-sweep variant is halved to give
+ * its time per sweep.  In 3-D the variants are 0 (a red and a black launch,
  * 256-thread blocks, the compiler's register count), 1 (the same bounded to
  * six resident blocks per multiprocessor) and 2 (the sweep in z-chunks sized
  * to stay in L2: red over a chunk, then black over the planes whose

@@ -643,6 +643,7 @@ struct Batch {
       case 32: return launch_v<32, 16, false, false>(b, l, dir);
       case 33: return launch_v<32, 16, false, false, 2>(b, l, dir);
       case 34: return launch_v<32, 16, false, false, 2>(b, l, dir);  // (cooperative in the single solver)
+      case 35: return launch_v<32, 16, false, false, 2>(b, l, dir);  // (32 x 14 tiles in the single solver)
       default: return launch_v<32, 32, false, false, 2>(b, l, dir);
     }
   }

@@ -1208,11 +1208,14 @@ __global__ void __launch_bounds__(march_threads(TX), march2_minb<T>(TX)) k_smoot
 // one sweep, 33: 16 x 8 two sweeps; single-instance solver only, the batch
 // runs them as 0 and 24), 34 all sweeps of a smoothing step in one
 // cooperative launch with grid barriers between the colour passes
-// (fm_coop.cuh; single-instance solver only, the batch runs it as 24).
+// (fm_coop.cuh; single-instance solver only, the batch runs it as 24), 35
+// the two-sweep tile form on 32 x 14 tiles (single-instance solver only, the
+// batch runs it as 24).
 constexpr int RB_NVAR = FM_SWEEP_VARIANTS;
 constexpr int RB_TMA0 = 27;  // first variant staged by tensor copies
 constexpr int RB_SMALL0 = 30;  // first small-tile variant
 constexpr int RB_COOP = 34;  // a level's sweeps in one cooperative launch (in place; single-instance solver)
+constexpr int RB_T14 = 35;   // two-sweep tiles of 32 x 14 (single-instance solver)
 constexpr int TUNE_REPS = 10;  // timed launches per variant and level in the autotuners
 constexpr int RB_NTILE = 12;
 constexpr int RB_NMARCH = 6;
@@ -1223,12 +1226,13 @@ __host__ __device__ constexpr int march_ly(int v) { return 16 << ((v - RB_NTILE)
 // (variant 34 runs all the sweeps of a smoothing step in one launch; it is
 // timed and reported with two, the pre- and post-smoothing count.)
 __host__ __device__ constexpr int sweeps_per_launch(int v) {
-  return v == RB_COOP ? 2
-                      : v >= RB_SMALL0 ? 1 + ((v - RB_SMALL0) & 1) : ((v >= RB_TWO && v != RB_TMA0 + 1) ? 2 : 1);
+  return (v == RB_COOP || v == RB_T14) ? 2
+         : v >= RB_SMALL0              ? 1 + ((v - RB_SMALL0) & 1)
+                                       : ((v >= RB_TWO && v != RB_TMA0 + 1) ? 2 : 1);
 }
 // The one-sweep variant with the same blocks as two-sweep variant v.
 __host__ __device__ constexpr int one_sweep_twin(int v) {
-  return v == RB_COOP ? 0
+  return (v == RB_COOP || v == RB_T14) ? 0
          : v >= RB_SMALL0 ? RB_SMALL0 + ((v - RB_SMALL0) & ~1)
          : v >= RB_TMA0 ? (v == RB_TMA0 ? RB_TMA0 + 1 : (v == RB_TMA0 + 2 ? 8 : v))
                         : (v >= RB_TWO_TILE ? (v - RB_TWO_TILE) * 4 : (v >= RB_TWO ? v - RB_NMARCH : v));

@@ -296,6 +296,7 @@ static int launch_rb(fm_state* st, int v, const Lvl<T>& L, const Phys<T>& P, cud
     case 31: return launch_rb_v<T, KIND, 16, 16, false, false, 2>(st, L, P, s, dir);
     case 32: return launch_rb_v<T, KIND, 16, 8, false, false>(st, L, P, s, dir);
     case 33: return launch_rb_v<T, KIND, 16, 8, false, false, 2>(st, L, P, s, dir);
+    case 35: return launch_rb_v<T, KIND, 32, 14, false, false, 2>(st, L, P, s, dir);
     default: return launch_coop<T, KIND>(st, L, P, s, 2);  // in place (dir does not apply)
   }
 }

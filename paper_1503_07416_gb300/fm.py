@@ -283,7 +283,7 @@ def fm_residual(st, g, r=None):
     return nrm.value
 
 
-FM_SWEEP_VARIANTS = 35
+FM_SWEEP_VARIANTS = 36
 FM_SWEEP_AUTO = -1
 FM_SWEEP_TWO_COLOUR = -2
 

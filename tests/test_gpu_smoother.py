@@ -143,14 +143,15 @@ def test_two_sweep_pass_equals_one_sweep_passes(kind, shape, precision, monkeypa
     """The two-sweep variants run the same point update on the same values
     as the one-sweep variants with the same blocks -- marching 18..23 against
     12..17, tiles 24..26 against 0, 4, 8, small tiles 31 and 33 against 30
-    and 32 -- only in another order of
+    and 32, the 32 x 14 tiles of 35 against the 32 x 16 ones of 0 -- only in
+    another order of
     independent points, so the results agree bit for bit: 2 sweeps (one pass)
     and 5 (two passes and a two-colour sweep), on grids with ragged strips
     and tiles, fewer rows than a block and fewer columns than a strip."""
     monkeypatch.setenv("FM_RB_VARIANT", "0")  # no autotuning at create
     rho, vel, prm = _case(kind, shape, 9)
     f, _ = _oracle(rho, vel, prm, 0.0, 0)
-    pairs = [(18 + m, 12 + m) for m in range(6)] + [(24 + k, 4 * k) for k in range(3)] + [(31, 30), (33, 32)]
+    pairs = [(18 + m, 12 + m) for m in range(6)] + [(24 + k, 4 * k) for k in range(3)] + [(31, 30), (33, 32), (35, 0)]
     for sweeps in (2, 5):
         for v2, v1 in pairs:
             try:
