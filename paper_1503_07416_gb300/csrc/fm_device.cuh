@@ -10,6 +10,8 @@
 #include <cmath>
 #include <cstring>
 #include <cstdlib>
+#include <type_traits>
+#include <utility>
 
 #include "fm_state.h"
 
@@ -66,11 +68,27 @@ __device__ __forceinline__ PtK<T> make_ptk(const Phys<T>& P, T h) {
 __device__ __forceinline__ float rcp_blk(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rcp_blk(double x) { return 1.0 / x; }
 
+// CDFT chemical-potential part of the correction form at a point with
+// correction e and coefficient density cr: ln(1 + e / cr) + 2 c_e e (the
+// change of ln rho + 2 c_e rho from rho = cr to cr + e).
+template <typename T>
+__device__ __forceinline__ T cdft_mc(T e, T cr, T ce) {
+  return log1p_t(e / cr) + T(2) * ce * e;
+}
+
+// An accessor that also provides mcv(i), cdft_mc of point i's current
+// correction kept by the launch that last changed it.
+template <class A, class = void>
+struct HasMcv : std::false_type {};
+template <class A>
+struct HasMcv<A, std::void_t<decltype(std::declval<const A&>().mcv(0))>> : std::true_type {};
+
 // Point-block update of one point, written against an accessor A that
 // provides e(q, i) / set_e(q, i, v), rk(i), cr(i), cv(d, i), f(q, fc) and
 // om(d, fc) (A is a level descriptor in any memory, or a shared-memory tile
-// with compile-time strides); K holds the level constants.  Neighbours are
-// at n.m / n.p; the right-hand side and omega^k are read at index fc.
+// with compile-time strides), and optionally mcv(i); K holds the level
+// constants.  Neighbours are at n.m / n.p; the right-hand side and omega^k
+// are read at index fc.
 template <typename T, int KIND, int DIM, class A>
 __device__ __forceinline__ void smooth_point_a(const A& a, const Phys<T>& P, const PtK<T>& K, const Nb& n,
                                                int fc) {
@@ -113,9 +131,10 @@ __device__ __forceinline__ void smooth_point_a(const A& a, const Phys<T>& P, con
   auto mc = [&](int idx) {
     if constexpr (KIND == KPFC) {
       return a.e(LY::IMU, idx);
+    } else if constexpr (HasMcv<A>::value) {
+      return a.mcv(idx);
     } else {
-      const T e = a.e(0, idx);
-      return log1p_t(e / a.cr(idx)) + T(2) * P.ce * e;
+      return cdft_mc<T>(a.e(0, idx), a.cr(idx), P.ce);
     }
   };
 
@@ -428,6 +447,44 @@ __global__ void __launch_bounds__(TPB) k_smooth(Lvl<T> L, Phys<T> P, int color) 
   if (!colour_point(t, color, L.g, i, j, k)) return;
   const Nb n = neighbours(i, j, k, L.g);
   smooth_point<T, KIND, DIM>(L, P, make_ptk<T, DIM>(P, L.h), n);
+}
+
+// Level accessor whose neighbours' CDFT chemical-potential parts come from M.
+struct McAcc64 {
+  const Lvl<double>& L;
+  const double* M;
+  __device__ __forceinline__ double e(int q, int i) const { return L.e[q][i]; }
+  __device__ __forceinline__ void set_e(int q, int i, double v) const { L.e[q][i] = v; }
+  __device__ __forceinline__ double rk(int i) const { return L.rk[i]; }
+  __device__ __forceinline__ double cr(int i) const { return L.cr[i]; }
+  __device__ __forceinline__ double cv(int d, int i) const { return L.cv[d][i]; }
+  __device__ __forceinline__ double f(int q, int i) const { return L.f[q][i]; }
+  __device__ __forceinline__ double om(int d, int i) const { return L.om[d][i]; }
+  __device__ __forceinline__ double mcv(int i) const { return M[i]; }
+};
+
+// A CDFT colour launch of the float64 coarsest-level sweeps that keeps
+// M[i] = cdft_mc of every point it updates: the next launch (the other
+// colour) reads its neighbours' values from M instead of evaluating the
+// logarithm at each of them (2 DIM evaluations a point on GB300's slow
+// float64 pipe become one).  The first launch of a solve (USE_M false)
+// evaluates its neighbours' values itself, as k_smooth does; M of a colour is
+// read only by the launch after the one that wrote it, so values and order
+// are those of k_smooth.
+template <int DIM, bool USE_M>
+__global__ void __launch_bounds__(TPB) k_smooth_cdft64_mc(Lvl<double> L, Phys<double> P, int color, double* M) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (!colour_point(t, color, L.g, i, j, k)) return;
+  const Nb n = neighbours(i, j, k, L.g);
+  const PtK<double> K = make_ptk<double, DIM>(P, L.h);
+  if constexpr (USE_M) {
+    const McAcc64 a{L, M};
+    smooth_point_a<double, KCDFT, DIM>(a, P, K, n, n.c);
+  } else {
+    smooth_point<double, KCDFT, DIM>(L, P, K, n);
+  }
+  M[n.c] = cdft_mc<double>(L.e[0][n.c], L.cr[n.c], P.ce);
 }
 
 // The same colour sweep compiled for six resident blocks per SM (at most 40

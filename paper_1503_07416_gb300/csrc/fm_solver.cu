@@ -1007,9 +1007,20 @@ struct Solver {
       // operations per multiprocessor and clock)
       const Lvl<double> L64 = make_lvl_bufs<double>(st->lv64[l]);
       const int half = L64.g.N / 2;
+      // CDFT: the chemical-potential part of the points a launch updates is
+      // kept in M (the level's float64 r[0], unused by these sweeps) for the
+      // next launch
+      double* M = static_cast<double*>(st->lv64[l].r[0]);
       for (int it = 0; it < st->prm.ncoarse; ++it)
         for (int color = 0; color < 2; ++color) {
-          k_smooth<double, KIND, DIM><<<(half + 31) / 32, 32, 0, st->stream>>>(L64, P64, color);
+          if constexpr (KIND == KCDFT) {
+            if (it == 0 && color == 0)
+              k_smooth_cdft64_mc<DIM, false><<<(half + 31) / 32, 32, 0, st->stream>>>(L64, P64, color, M);
+            else
+              k_smooth_cdft64_mc<DIM, true><<<(half + 31) / 32, 32, 0, st->stream>>>(L64, P64, color, M);
+          } else {
+            k_smooth<double, KIND, DIM><<<(half + 31) / 32, 32, 0, st->stream>>>(L64, P64, color);
+          }
           FM_LAUNCHED();
         }
     } else {
@@ -1235,7 +1246,8 @@ static size_t carve(fm_state* st, char* base) {
   // float64 copies of the coarse levels (mixed path, coarsest solve in
   // float64): e, f, r, eh and the coefficients of levels small_from ..
   // nlev - 1 (the entry level's eh stays in the float32 level: the
-  // prolongation reads it)
+  // prolongation reads it; a multi-block coarsest level's r[0] holds the
+  // CDFT chemical-potential parts of its colour launches)
   for (int l = 0; l < MAXLEV; ++l) st->lv64[l] = LevelBufs{};
   if (st->coarse64) {
     for (int l = st->small_from; l < st->nlev; ++l) {

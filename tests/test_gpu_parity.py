@@ -72,6 +72,19 @@ def test_mixed_path_coarsest_solve_in_either_precision(coarse, mg):
     _compare_step(rho, vel, prm, fm.FM_MIXED, w_damp=0.0, steps=2, coarse_precision=coarse, **mg)
 
 
+@pytest.mark.parametrize("coarse", [fm.FM_FP64, fm.FM_MIXED])
+def test_cdft_with_a_multi_block_coarsest_level(coarse):
+    """CDFT, the 256^2 physics on a 128^2 box with a 64^2 coarsest grid: in
+    float64 its sweeps are colour launches that keep the chemical-potential
+    parts of the points they update for the next launch; per-step parity with
+    the oracle over 3 steps, with the coarsest solve in either precision."""
+    rho, vel, prm = inputs.cdft256(n=128)
+    prm = dict(prm, h=17.0 / 128)
+    rng = np.random.default_rng(12)
+    vel = [0.02 * rng.standard_normal(rho.shape) for _ in range(2)]
+    _compare_step(rho, vel, prm, fm.FM_MIXED, steps=3, coarse_precision=coarse, coarsest=64, ncoarse=2)
+
+
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
 def test_pfc_supercooled_with_velocity(precision):
     """PFC eps = 0.4 supercooled liquid with nuclei, non-zero velocity and
