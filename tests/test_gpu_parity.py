@@ -86,6 +86,20 @@ def test_cdft_with_a_multi_block_coarsest_level(coarse):
 
 
 @pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
+def test_3d_cdft_steps(precision):
+    """3-D CDFT, 32^3 with random velocity: two levels, the 16^3 coarsest grid
+    swept by multi-block launches (in the mixed path in float64, keeping the
+    chemical-potential parts between colour launches); the convolution by the
+    3-D FFT; per-step parity over 2 steps."""
+    rng = np.random.default_rng(18)
+    n = 32
+    rho = 0.1 * np.pi * (1 + 0.1 * rng.uniform(0, 1, (n, n, n)))
+    vel = [0.02 * rng.standard_normal((n, n, n)) for _ in range(3)]
+    prm = dict(kind="cdft", dim=3, h=17.0 / 32, dt=0.02, nu=2.362, delta=1e-10)
+    _compare_step(rho, vel, prm, precision, tol=1e-11, w_damp=0.0, steps=2)
+
+
+@pytest.mark.parametrize("precision", [fm.FM_FP64, fm.FM_MIXED])
 def test_pfc_supercooled_with_velocity(precision):
     """PFC eps = 0.4 supercooled liquid with nuclei, non-zero velocity and
     vorticity, 128x128, undamped smoother."""
