@@ -405,8 +405,10 @@ def run_ours(args):
             "l2": "flushed (256 MiB write) between timed steps, flush untimed",
             "cycles_per_step_mean": round(statistics.mean(mix["cycles"]), 3),
             "multigrid": {"cycle": "V(2,2)", "levels": "512^2 .. 64^2 (4)", "coarsest_sweeps": 2,
-                          "coarse_solve": "2 fused red-black sweeps of the 64^2 grid (multi-block, two sweeps "
-                                          "per launch), in float64 on float64 copies of the level"},
+                          "coarse_solve": "2 red-black sweeps of the 64^2 grid in float64 on float64 copies of "
+                                          "the level: a conversion launch in, 4 colour launches of 32-thread "
+                                          "blocks, a conversion launch out (the float32-coarse arm: one fused "
+                                          "two-sweep launch)"},
             "parallelism": f"{world} independent instance(s), one per GPU",
             "initial_iterate": {"previous": "previous time level (rho^k, u^k, mu^0, kappa^0)",
                                 "extrapolate": "linear extrapolation in time of the last two converged iterates "
